@@ -1,0 +1,46 @@
+"""Dense characteristic-mode eigensolve.  Test infrastructure.
+
+Section II, Eq. (GEP): X J_n = lambda_n R J_n with Z = R + iX (Eq. (6)).
+Sign reading: taken literally with exp(ikR)/R and the prefactor +ik eta,
+Re Z is negative semidefinite and the literal pencil gives characteristic
+values of the opposite sign to Table I and to the physical reading of
+Section II (lambda < 0 stores electric energy).  This oracle therefore
+uses R := -Re Z (positive semidefinite) and X := +Im Z.  Characteristic
+values do not depend on the overall scale of Z.
+
+Solved as the pencil (R, X): R J = mu X J, mu = 1 / lambda, so the values
+nearest zero are those with the largest |mu| (the same selection the paper
+makes with IRA on Eq. (SEP)).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+
+
+def cm_values(Z: np.ndarray, nev: int = 10) -> np.ndarray:
+    """The nev characteristic values nearest zero, sorted by magnitude."""
+    R = -Z.real
+    X = Z.imag
+    mu = scipy.linalg.eigvals(R, X)
+    mu = mu[np.isfinite(mu)]
+    idx = np.argsort(-np.abs(mu))[:nev]
+    lam = 1.0 / mu[idx]
+    return lam.real[np.argsort(np.abs(lam.real))]
+
+
+def cm_values_arnoldi(Z: np.ndarray, nev: int = 10, seed: int = 0) -> np.ndarray:
+    """Same selection as ``cm_values`` through a dense LU of X and Arnoldi
+    iteration (ARPACK, as in Section IV) on X^-1 R, largest |1/lambda|."""
+    import scipy.sparse.linalg as sla
+
+    R = -Z.real
+    X = Z.imag
+    lu = scipy.linalg.lu_factor(X)
+    n = Z.shape[0]
+    op = sla.LinearOperator((n, n), matvec=lambda v: scipy.linalg.lu_solve(lu, R @ v), dtype=np.float64)
+    v0 = np.random.Generator(np.random.PCG64(seed)).standard_normal(n)
+    mu = sla.eigs(op, k=nev, which="LM", v0=v0, ncv=max(2 * nev + 1, 40), tol=1e-12,
+                  return_eigenvectors=False)
+    lam = (1.0 / mu).real
+    return lam[np.argsort(np.abs(lam))]
