@@ -1,0 +1,207 @@
+/*
+ * mlfma.h - C ABI of the GB300 (sm_103a) multilevel fast multipole matrix-
+ * vector product for the Galerkin EFIE with RWG basis functions on a
+ * triangulated PEC surface.
+ *
+ * The product is y = Z x with Z_ij = i k eta < f_i, G, f_j > (Section II,
+ * Eq. (5)), G = [I - grad grad'/k^2] exp(ikR)/R (Eqs. (2)-(3)): no 1/(4 pi),
+ * time convention exp(-i w t).  Characteristic-mode analysis uses
+ * R = -Re Z (positive semidefinite) and X = Im Z; for a real x these are
+ * -Re(Z x) and Im(Z x).
+ *
+ * Z x is split as in the two-level formula (Section III-B, Eq. (ZI)): an
+ * explicitly stored near-field part over each leaf group's neighbours B_m,
+ * and a far part evaluated by aggregation, translation (Section III-A,
+ * Eqs. (7)-(8)) and disaggregation, extended over an oct-tree with
+ * interpolation and anterpolation between levels (Section III-C).
+ *
+ * Conventions for every entry point
+ * - Every function returns an mlfma_status; none aborts, traps or exits.  On
+ *   failure a message is kept per thread and returned by mlfma_last_error().
+ * - Mesh arrays are host memory, read during mlfma_plan() only.
+ * - Vector arguments of mlfma_matvec*() are DEVICE pointers on the plan's
+ *   device, row-major [N][B] with the batch index innermost, in canonical
+ *   RWG order (below).  mlfma_matvec_host() takes HOST pointers instead.
+ * - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *   void*, NULL = legacy default stream); device-side failures surface at the
+ *   next call on the plan or at mlfma_sync().
+ * - A plan is not thread-safe: serialise calls on one plan; calls on
+ *   different plans may run concurrently.
+ *
+ * Canonical RWG order: one basis function per edge shared by exactly two
+ * triangles, edges sorted by (smaller vertex index, larger vertex index).
+ * T+ is the triangle whose vertex cycle runs along the edge from the smaller
+ * to the larger index; f = +l/(2A+) (r - v+) on T+ and -l/(2A-) (r - v-) on
+ * T-.  Boundary edges carry no function; an edge on three or more triangles,
+ * or with both triangles running the same way along it, is MLFMA_EINVAL.
+ */
+#ifndef MLFMA_H
+#define MLFMA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mlfma_plan_s *mlfma_plan_t;   /* opaque; owns all memory it allocates */
+
+typedef enum {
+    MLFMA_OK = 0,
+    MLFMA_EINVAL = 1,    /* bad argument, mesh or size */
+    MLFMA_ENOMEM = 2,    /* host or device allocation failed */
+    MLFMA_ECUDA = 3,     /* a CUDA runtime call failed; message has the CUDA error */
+    MLFMA_ENOTCONV = 4,  /* reserved for iterative solvers */
+    MLFMA_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    MLFMA_ENOTSUP = 6    /* valid request this build does not support */
+} mlfma_status;
+
+/* Arithmetic of a product.  MLFMA_FP64: complex FP64 everywhere (near field,
+ * radiation patterns, translations, interpolation, accumulation).
+ * MLFMA_FP32: complex FP32 near field, patterns, translation tables and
+ * fields, FP32 interpolation coefficients, FP32 accumulation; the tables are
+ * built in FP64 and rounded once. */
+typedef enum { MLFMA_FP64 = 0, MLFMA_FP32 = 1 } mlfma_prec;
+
+typedef struct {
+    int interp_order;   /* points per dimension of the local Lagrange
+                           interpolation between levels (Section III-C);
+                           even, 4..12; default 6 */
+    int max_batch;      /* largest B (real columns; a complex column counts
+                           two) a product may use; fields are sized for it;
+                           default 64 */
+    int precisions;     /* bit mask (1 << mlfma_prec) of arithmetic to set up;
+                           default both */
+    int host_only;      /* 1: build the host tables only and never touch a
+                           GPU (for inspection with mlfma_export); products
+                           are refused with MLFMA_EINVAL */
+    int device;         /* CUDA device ordinal; -1 = the current device */
+    double eta;         /* wave impedance eta in Eq. (1); default 376.730313668 */
+} mlfma_opts;
+
+/* Fill *opts with the defaults above.  Always MLFMA_OK unless opts is NULL. */
+mlfma_status mlfma_default_opts(mlfma_opts *opts);
+
+/*
+ * Build a plan: RWG list, oct-tree (Section III-C: level 0 is the cube
+ * enclosing the mesh, each level halves the box side; `levels` counts level
+ * 0, like Table II's nlv), near lists, sampling grids, interpolation
+ * stencils, translation tables (Eq. (8)), and on the GPU the FP64 near-field
+ * blocks (with singularity extraction) and leaf radiation patterns.
+ *
+ *  verts  [nv][3] float64, metres            tris  [nt][3] int32, 0-based
+ *  k      wavenumber (rad/m), > 0            levels  2..21
+ *  digits d0 of the truncation number L = ceil(k d + 1.8 d0^(2/3) (k d)^(1/3)),
+ *         d = sqrt(3) a for box side a (Section V, Eq. (9)); 1..15
+ *  opts   NULL for defaults
+ *  out    receives the plan; untouched on failure
+ * Far interactions start at level 2 (Section III-C).  The root cube's side is
+ * the mesh's largest bounding-box extent; an RWG belongs to the leaf box
+ * holding its edge midpoint (faces belong to the upper box).
+ * Errors: EINVAL (arguments, mesh), ENOMEM, ECUDA.
+ */
+mlfma_status mlfma_plan(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                        double k, int levels, double digits, const mlfma_opts *opts,
+                        mlfma_plan_t *out);
+
+/* Number of unknowns N (RWG functions). */
+mlfma_status mlfma_num_unknowns(mlfma_plan_t plan, int64_t *n);
+
+/* Canonical RWG list: edge_v [N][2] (smaller, larger vertex index) and
+ * tri_pm [N][2] (T+, T-), both host int32 arrays of the caller. Either may be
+ * NULL. */
+mlfma_status mlfma_rwg_edges(mlfma_plan_t plan, int32_t *edge_v, int32_t *tri_pm);
+
+/*
+ * y = Z x on the GPU (Eq. (ZI), multilevel).
+ *  x      device, [N][B]: float (FP32) or double (FP64) real values; or, when
+ *         x_is_complex, interleaved complex [N][B] of that real type
+ *  y      device, [N][B] interleaved complex of the same real type; must not
+ *         overlap x
+ *  B      columns, 1..max_batch (complex x: 1..max_batch/2)
+ *  prec   an mlfma_prec set up in the plan
+ *  stream cudaStream_t or NULL
+ * Asynchronous.  Errors: EINVAL (sizes, precision not set up, host-only
+ * plan), ECUDA.
+ */
+mlfma_status mlfma_matvec(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
+                          int64_t B, int prec, void *stream);
+
+/*
+ * y = Z^H x.  Z is symmetric (Z = Z^T, Section II; the near blocks are
+ * symmetrised explicitly), so Z^H x = conj(Z conj(x)): the same pass with
+ * the input and output conjugated.  Arguments as mlfma_matvec.
+ */
+mlfma_status mlfma_matvec_adjoint(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
+                                  int64_t B, int prec, void *stream);
+
+/*
+ * y = Z x with HOST x and y (same layouts and types as mlfma_matvec): copies
+ * x to the device, runs the product on `stream`, copies y back and waits for
+ * the stream.  Uses the plan's own device staging buffers.
+ */
+mlfma_status mlfma_matvec_host(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
+                               int64_t B, int prec, void *stream);
+
+/* Wait for the plan's work on `stream` and report any pending device-side
+ * error. */
+mlfma_status mlfma_sync(mlfma_plan_t plan, void *stream);
+
+/* Summary of a plan (host copy; all fields filled). */
+#define MLFMA_MAX_LEVELS 22
+typedef struct {
+    int64_t n;                         /* unknowns */
+    int levels;                        /* incl. level 0 */
+    int leaf_level;                    /* levels - 1 */
+    double root_side;                  /* m */
+    double root_center[3];
+    int64_t near_nnz;                  /* stored near-field entries */
+    int64_t leaf_boxes;
+    int max_leaf_unknowns;
+    int box_count[MLFMA_MAX_LEVELS];   /* occupied boxes per level */
+    int trunc_L[MLFMA_MAX_LEVELS];     /* L per level (0 where no far work) */
+    int samples_K[MLFMA_MAX_LEVELS];   /* (L+1) * 2(L+1) */
+    int64_t translations[MLFMA_MAX_LEVELS];  /* interaction-list entries */
+    int64_t device_bytes;              /* device memory held by the plan */
+    double setup_seconds;              /* wall time of mlfma_plan */
+} mlfma_info;
+
+mlfma_status mlfma_plan_info(mlfma_plan_t plan, mlfma_info *info);
+
+/*
+ * Copy a host-side table of the plan into `dst` (host memory of `cap`
+ * bytes); *needed receives the size in bytes (call with dst = NULL to ask).
+ * Tables (level = the far level they belong to):
+ *   MLFMA_X_PERM       int64 [N]       leaf-order position -> canonical index
+ *   MLFMA_X_LEAF_BOX   int32 [N]       leaf box of each unknown, canonical order
+ *   MLFMA_X_GRID       float64 [K][4]  (cos theta, phi, weight, theta) per sample,
+ *                                      theta-major (q = it * 2(L+1) + ip)
+ *   MLFMA_X_ALPHA      float64 [T][K][2] translation table per offset type
+ *   MLFMA_X_ALPHA_OFFS int32 [T][3]    offset (in boxes) of each type
+ *   MLFMA_X_INTERP     float64 [K_parent][K_child]  dense form of the level+1 ->
+ *                                      level interpolation (applied to each tangential
+ *                                      component alike; pole reflection sign folded in)
+ *   MLFMA_X_BOX_CENTERS float64 [boxes][3]
+ *   MLFMA_X_NEAR_COUNT int64 [1]       near entries
+ *   MLFMA_X_ANTERP     float64 [K_child][K_parent]  dense form of the level ->
+ *                                      level+1 anterpolation, built from its own
+ *                                      (transposed, weighted) stencils
+ */
+enum {
+    MLFMA_X_PERM = 1, MLFMA_X_LEAF_BOX = 2, MLFMA_X_GRID = 3, MLFMA_X_ALPHA = 4,
+    MLFMA_X_ALPHA_OFFS = 5, MLFMA_X_INTERP = 6, MLFMA_X_BOX_CENTERS = 7, MLFMA_X_NEAR_COUNT = 8,
+    MLFMA_X_ANTERP = 9
+};
+mlfma_status mlfma_export(mlfma_plan_t plan, int what, int level, void *dst, int64_t cap,
+                          int64_t *needed);
+
+/* Release everything the plan owns (waits for its work).  NULL is a no-op. */
+void mlfma_destroy(mlfma_plan_t plan);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *mlfma_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLFMA_H */

@@ -1,0 +1,585 @@
+// C ABI (include/mlfma.h): plan construction, products, inspection.
+#include "../../include/mlfma.h"
+#include "device.h"
+#include "plan_host.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace mlfma;
+
+namespace {
+
+thread_local std::string g_err;
+
+mlfma_status fail(mlfma_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+mlfma_status cuda_fail(cudaError_t e, const char *where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? MLFMA_ENOMEM : MLFMA_ECUDA;
+}
+
+struct DevMem {
+    std::vector<void *> ptrs;
+    int64_t bytes = 0;
+    cudaError_t alloc(void **p, size_t n)
+    {
+        *p = nullptr;
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(p, n);
+        if (e == cudaSuccess) {
+            ptrs.push_back(*p);
+            bytes += (int64_t)n;
+        }
+        return e;
+    }
+    template <class T>
+    cudaError_t upload(const T *src, size_t count, const T **out)
+    {
+        void *p;
+        cudaError_t e = alloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) return e;
+        if (count) e = cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        *out = static_cast<const T *>(p);
+        return e;
+    }
+    template <class T>
+    cudaError_t upload(const std::vector<T> &v, const T **out) { return upload(v.data(), v.size(), out); }
+    void release(void *p)
+    {
+        for (auto &q : ptrs)
+            if (q == p) {
+                cudaFree(q);
+                q = nullptr;
+            }
+    }
+    void free_all()
+    {
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev_);
+        if (dev >= 0 && dev != prev_) {
+            cudaSetDevice(dev);
+            set_ = true;
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (set_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = 0;
+    bool set_ = false;
+};
+
+}  // namespace
+
+struct mlfma_plan_s {
+    PlanHost host;
+    mlfma_opts opts{};
+    int device = -1;
+    bool on_device = false;
+    DevMem mem;
+    ProductArgs<float> a32;
+    ProductArgs<double> a64;
+    bool has32 = false, has64 = false;
+    void *stage_x = nullptr, *stage_y = nullptr;   // host-API staging (largest type)
+    double setup_seconds = 0;
+};
+
+namespace {
+
+template <class R>
+cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *near64, const double2 *V64,
+                            const std::vector<const int32_t *> &dev_ints)
+{
+    PlanHost &H = p->host;
+    DevMem &M = p->mem;
+    const int Bmax = p->opts.max_batch;
+    cudaError_t e;
+    a.n = H.N;
+    a.leaf = H.leaf;
+    a.levels = H.levels;
+    // near values
+    if (sizeof(R) == 8) {
+        a.near_val = reinterpret_cast<const R *>(near64);
+    } else {
+        void *d;
+        if ((e = M.alloc(&d, (size_t)H.nnz * 8)) != cudaSuccess) return e;
+        if ((e = launch_cast_c64_to_c32(near64, static_cast<float2 *>(d), H.nnz, 0)) != cudaSuccess) return e;
+        a.near_val = static_cast<const R *>(d);
+    }
+    if (H.leaf >= 2) {
+        const int64_t nv = H.N * (int64_t)H.lv[H.leaf].K * 2;
+        if (sizeof(R) == 8) {
+            a.V = reinterpret_cast<const R *>(V64);
+        } else {
+            void *d;
+            if ((e = M.alloc(&d, (size_t)nv * 8)) != cudaSuccess) return e;
+            if ((e = launch_cast_c64_to_c32(V64, static_cast<float2 *>(d), nv, 0)) != cudaSuccess) return e;
+            a.V = static_cast<const R *>(d);
+        }
+    }
+    void *d;
+    if ((e = M.alloc(&d, (size_t)H.N * Bmax * sizeof(R))) != cudaSuccess) return e;
+    a.xp = static_cast<R *>(d);
+    if ((e = M.alloc(&d, (size_t)H.N * Bmax * 2 * sizeof(R))) != cudaSuccess) return e;
+    a.yp = static_cast<R *>(d);
+    int64_t scratch = 16;
+    const double cfar = -H.k * H.k * H.eta / (4.0 * M_PI);
+    for (int l = 2; l <= H.leaf; ++l) {
+        const Level &Lv = H.lv[l];
+        DevLevel<R> &D = a.lv[l];
+        D.nbox = Lv.nbox();
+        D.L = Lv.L; D.nth = Lv.nth; D.nph = Lv.nph; D.K = Lv.K; D.ntype = Lv.ntype;
+        const int32_t *const *ip = &dev_ints[(size_t)l * 16];
+        D.il_ptr = ip[0]; D.il_src = ip[1]; D.il_type = ip[2];
+        D.parent = ip[3]; D.octant = ip[4]; D.child_ptr = ip[5];
+        D.thu_ptr = ip[6]; D.thu_idx = ip[7]; D.thu_refl = ip[8];
+        D.phu_ptr = ip[9]; D.phu_idx = ip[10];
+        D.thd_ptr = ip[11]; D.thd_idx = ip[12]; D.thd_refl = ip[13];
+        D.phd_ptr = ip[14]; D.phd_idx = ip[15];
+        std::vector<R> tmp(2 * Lv.alpha.size());
+        for (size_t i = 0; i < Lv.alpha.size(); ++i) { tmp[2 * i] = (R)Lv.alpha[i].real(); tmp[2 * i + 1] = (R)Lv.alpha[i].imag(); }
+        if ((e = M.upload(tmp, &D.alpha)) != cudaSuccess) return e;
+        if (l < H.leaf) {
+            tmp.resize(2 * Lv.shift.size());
+            for (size_t i = 0; i < Lv.shift.size(); ++i) { tmp[2 * i] = (R)Lv.shift[i].real(); tmp[2 * i + 1] = (R)Lv.shift[i].imag(); }
+            if ((e = M.upload(tmp, &D.shift)) != cudaSuccess) return e;
+            auto cast = [](const std::vector<double> &v) { return std::vector<R>(v.begin(), v.end()); };
+            if ((e = M.upload(cast(Lv.th_up.coef), &D.thu_c)) != cudaSuccess) return e;
+            if ((e = M.upload(cast(Lv.ph_up.coef), &D.phu_c)) != cudaSuccess) return e;
+            if ((e = M.upload(cast(Lv.th_dn.coef), &D.thd_c)) != cudaSuccess) return e;
+            if ((e = M.upload(cast(Lv.ph_dn.coef), &D.phd_c)) != cudaSuccess) return e;
+            const Level &C = H.lv[l + 1];
+            scratch = std::max<int64_t>(scratch, (int64_t)C.nbox() * 2 * Lv.nth * C.nph * Bmax);
+        }
+        std::vector<R> w(Lv.K);
+        for (int q = 0; q < Lv.K; ++q)
+            w[q] = (R)((l == H.leaf ? cfar : 1.0) * Lv.wt[q / Lv.nph] * 2.0 * M_PI / Lv.nph);
+        if ((e = M.upload(w, &D.wq)) != cudaSuccess) return e;
+        const size_t fsz = (size_t)D.nbox * 2 * Lv.K * Bmax * 2 * sizeof(R);
+        if ((e = M.alloc(&d, fsz)) != cudaSuccess) return e;
+        D.S = static_cast<R *>(d);
+        if ((e = M.alloc(&d, fsz)) != cudaSuccess) return e;
+        D.G = static_cast<R *>(d);
+    }
+    if ((e = M.alloc(&d, (size_t)scratch * 2 * sizeof(R))) != cudaSuccess) return e;
+    a.scratch = static_cast<R *>(d);
+    return cudaSuccess;
+}
+
+mlfma_status setup_device(mlfma_plan_t p)
+{
+    PlanHost &H = p->host;
+    DevMem &M = p->mem;
+    cudaError_t e;
+#define CK(x, where) do { if ((e = (x)) != cudaSuccess) return cuda_fail(e, where); } while (0)
+    const int nt = (int)(H.T.size() / 3);
+    const double *dV;
+    const int32_t *dT;
+    CK(M.upload(H.V, &dV), "upload vertices");
+    CK(M.upload(H.T, &dT), "upload triangles");
+    void *tq, *tv, *area, *cen, *hmax;
+    CK(M.alloc(&tq, sizeof(double) * 21 * nt), "alloc geometry");
+    CK(M.alloc(&tv, sizeof(double) * 9 * nt), "alloc geometry");
+    CK(M.alloc(&area, sizeof(double) * nt), "alloc geometry");
+    CK(M.alloc(&cen, sizeof(double) * 3 * nt), "alloc geometry");
+    CK(M.alloc(&hmax, sizeof(double) * nt), "alloc geometry");
+    CK(launch_mesh_geometry(dV, dT, nt, (double *)tq, (double *)tv, (double *)area, (double *)cen, (double *)hmax, 0),
+       "mesh geometry");
+    // RWG data in leaf order
+    std::vector<int32_t> rtri(2 * H.N);
+    std::vector<double> rvf(6 * H.N), rlen(H.N);
+    std::vector<int32_t> ubox(H.N);
+    for (int64_t i = 0; i < H.N; ++i) {
+        const int64_t c = H.perm[i];
+        rtri[2 * i] = H.rwg.tri[2 * c];
+        rtri[2 * i + 1] = H.rwg.tri[2 * c + 1];
+        for (int s = 0; s < 2; ++s)
+            for (int d = 0; d < 3; ++d) rvf[6 * i + 3 * s + d] = H.V[3 * H.rwg.vfree[2 * c + s] + d];
+        rlen[i] = H.rwg.len[c];
+        ubox[i] = H.leaf_box[c];
+    }
+    DevMesh dm;
+    dm.nt = nt;
+    dm.tq = (const double *)tq; dm.tv = (const double *)tv; dm.tvi = dT;
+    dm.area = (const double *)area; dm.cen = (const double *)cen; dm.hmax = (const double *)hmax;
+    dm.n = H.N;
+    CK(M.upload(rtri, &dm.rtri), "upload rwg");
+    CK(M.upload(rvf, &dm.rvf), "upload rwg");
+    CK(M.upload(rlen, &dm.rlen), "upload rwg");
+    const int32_t *d_ubox;
+    CK(M.upload(ubox, &d_ubox), "upload rwg");
+    const int64_t *d_perm;
+    CK(M.upload(H.perm, &d_perm), "upload perm");
+    DevNear nr;
+    nr.nleaf = H.lv[H.leaf].nbox();
+    CK(M.upload(H.box_ptr, &nr.box_ptr), "upload near");
+    CK(M.upload(H.strip_off, &nr.strip_off), "upload near");
+    CK(M.upload(H.col_ptr, &nr.col_ptr), "upload near");
+    CK(M.upload(H.strip_col, &nr.strip_col), "upload near");
+    void *near64;
+    CK(M.alloc(&near64, (size_t)H.nnz * 16), "alloc near field");
+    CK(launch_near_fill(dm, nr, H.k, H.eta, (double2 *)near64, 0), "near fill");
+    void *V64 = nullptr;
+    if (H.leaf >= 2) {
+        const Level &Lf = H.lv[H.leaf];
+        std::vector<double> grid(9 * (size_t)Lf.K);
+        for (int q = 0; q < Lf.K; ++q) {
+            const int it = q / Lf.nph, ip = q % Lf.nph;
+            const double ct = Lf.ct[it], st = std::sqrt(std::max(0.0, 1 - ct * ct));
+            const double cp = std::cos(Lf.ph[ip]), sp = std::sin(Lf.ph[ip]);
+            const double g[9] = {st * cp, st * sp, ct, ct * cp, ct * sp, -st, -sp, cp, 0.0};
+            std::memcpy(&grid[9 * (size_t)q], g, sizeof(g));
+        }
+        const double *d_grid, *d_bc;
+        CK(M.upload(grid, &d_grid), "upload grid");
+        CK(M.upload(Lf.center, &d_bc), "upload centers");
+        CK(M.alloc(&V64, (size_t)H.N * Lf.K * 2 * 16), "alloc patterns");
+        CK(launch_leaf_patterns(dm, d_ubox, d_bc, Lf.K, d_grid, H.k, (double2 *)V64, 0), "leaf patterns");
+    }
+    // integer tables shared by both precisions: 16 slots per level
+    std::vector<const int32_t *> ints((size_t)H.levels * 16, nullptr);
+    for (int l = 2; l <= H.leaf; ++l) {
+        const Level &Lv = H.lv[l];
+        const int32_t **ip = &ints[(size_t)l * 16];
+        CK(M.upload(Lv.il_ptr, &ip[0]), "upload lists");
+        CK(M.upload(Lv.il_src, &ip[1]), "upload lists");
+        CK(M.upload(Lv.il_type, &ip[2]), "upload lists");
+        CK(M.upload(Lv.parent, &ip[3]), "upload lists");
+        CK(M.upload(Lv.octant, &ip[4]), "upload lists");
+        if (l < H.leaf) {
+            CK(M.upload(Lv.child_ptr, &ip[5]), "upload lists");
+            CK(M.upload(Lv.th_up.ptr, &ip[6]), "upload stencils");
+            CK(M.upload(Lv.th_up.idx, &ip[7]), "upload stencils");
+            CK(M.upload(Lv.th_up.refl, &ip[8]), "upload stencils");
+            CK(M.upload(Lv.ph_up.ptr, &ip[9]), "upload stencils");
+            CK(M.upload(Lv.ph_up.idx, &ip[10]), "upload stencils");
+            CK(M.upload(Lv.th_dn.ptr, &ip[11]), "upload stencils");
+            CK(M.upload(Lv.th_dn.idx, &ip[12]), "upload stencils");
+            CK(M.upload(Lv.th_dn.refl, &ip[13]), "upload stencils");
+            CK(M.upload(Lv.ph_dn.ptr, &ip[14]), "upload stencils");
+            CK(M.upload(Lv.ph_dn.idx, &ip[15]), "upload stencils");
+        }
+    }
+    const int prec = p->opts.precisions;
+    if (prec & (1 << MLFMA_FP32)) {
+        p->a32.nr = nr; p->a32.ubox = d_ubox; p->a32.perm = d_perm;
+        CK(setup_precision<float>(p, p->a32, (const double2 *)near64, (const double2 *)V64, ints), "setup FP32");
+        p->has32 = true;
+    }
+    if (prec & (1 << MLFMA_FP64)) {
+        p->a64.nr = nr; p->a64.ubox = d_ubox; p->a64.perm = d_perm;
+        CK(setup_precision<double>(p, p->a64, (const double2 *)near64, (const double2 *)V64, ints), "setup FP64");
+        p->has64 = true;
+    }
+    const size_t stage = (size_t)H.N * p->opts.max_batch * 2 * sizeof(double);
+    CK(M.alloc(&p->stage_x, stage), "alloc staging");
+    CK(M.alloc(&p->stage_y, stage), "alloc staging");
+    CK(cudaDeviceSynchronize(), "plan setup");
+    if (!p->has64) {
+        M.release(near64);
+        if (V64) M.release(V64);
+    }
+#undef CK
+    return MLFMA_OK;
+}
+
+mlfma_status check_plan(mlfma_plan_t p)
+{
+    if (!p) return fail(MLFMA_EINVAL, "plan is NULL");
+    return MLFMA_OK;
+}
+
+mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream, int adjoint,
+                     bool host)
+{
+    if (check_plan(p)) return MLFMA_EINVAL;
+    if (!p->on_device) return fail(MLFMA_EINVAL, "plan was built host-only; products need a device plan");
+    if (!x || !y) return fail(MLFMA_EINVAL, "x or y is NULL");
+    if (x == y) return fail(MLFMA_EINVAL, "x and y must not overlap");
+    if (B < 1) return fail(MLFMA_EINVAL, "B must be >= 1");
+    const int64_t Bi = B * (xc ? 2 : 1);
+    if (Bi > p->opts.max_batch) return fail(MLFMA_EINVAL, "B exceeds the plan's max_batch");
+    if (prec == MLFMA_FP32 && !p->has32) return fail(MLFMA_EINVAL, "FP32 was not set up in this plan");
+    if (prec == MLFMA_FP64 && !p->has64) return fail(MLFMA_EINVAL, "FP64 was not set up in this plan");
+    if (prec != MLFMA_FP32 && prec != MLFMA_FP64) return fail(MLFMA_EINVAL, "unknown precision");
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t rsz = prec == MLFMA_FP64 ? 8 : 4;
+    const size_t xbytes = (size_t)p->host.N * B * (xc ? 2 : 1) * rsz;
+    const size_t ybytes = (size_t)p->host.N * B * 2 * rsz;
+    cudaError_t e;
+    const void *xd = x;
+    void *yd = y;
+    if (host) {
+        if ((e = cudaMemcpyAsync(p->stage_x, x, xbytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "copy x to device");
+        xd = p->stage_x;
+        yd = p->stage_y;
+    }
+    if (prec == MLFMA_FP64) {
+        ProductArgs<double> a = p->a64;
+        a.B = (int)Bi;
+        e = run_product<double>(a, xd, xc, yd, (int)B, adjoint, s);
+    } else {
+        ProductArgs<float> a = p->a32;
+        a.B = (int)Bi;
+        e = run_product<float>(a, xd, xc, yd, (int)B, adjoint, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "product launch");
+    if (host) {
+        if ((e = cudaMemcpyAsync(y, p->stage_y, ybytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "copy y to host");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "product");
+    }
+    return MLFMA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mlfma_status mlfma_default_opts(mlfma_opts *o)
+{
+    if (!o) return fail(MLFMA_EINVAL, "opts is NULL");
+    o->interp_order = 6;
+    o->max_batch = 64;
+    o->precisions = (1 << MLFMA_FP32) | (1 << MLFMA_FP64);
+    o->host_only = 0;
+    o->device = -1;
+    o->eta = 376.730313668;
+    return MLFMA_OK;
+}
+
+mlfma_status mlfma_plan(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, double k, int levels,
+                        double digits, const mlfma_opts *opts, mlfma_plan_t *out)
+{
+    g_err.clear();
+    if (!out) return fail(MLFMA_EINVAL, "out is NULL");
+    auto t0 = std::chrono::steady_clock::now();
+    std::unique_ptr<mlfma_plan_s> p(new (std::nothrow) mlfma_plan_s());
+    if (!p) return fail(MLFMA_ENOMEM, "host allocation failed");
+    if (opts) p->opts = *opts; else mlfma_default_opts(&p->opts);
+    if (p->opts.max_batch < 1 || p->opts.max_batch > 4096) return fail(MLFMA_EINVAL, "max_batch must be in 1..4096");
+    if (!(p->opts.eta > 0)) return fail(MLFMA_EINVAL, "eta must be positive");
+    std::string err;
+    try {
+        err = build_plan_host(p->host, verts, nv, tris, nt, k, levels, digits, p->opts.interp_order, p->opts.eta);
+    } catch (const std::bad_alloc &) {
+        return fail(MLFMA_ENOMEM, "host allocation failed while building the plan");
+    }
+    if (!err.empty()) return fail(MLFMA_EINVAL, err);
+    if (!p->opts.host_only) {
+        if ((p->opts.precisions & 3) == 0) return fail(MLFMA_EINVAL, "no precision requested");
+        int dev = p->opts.device;
+        if (dev < 0) {
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        }
+        p->device = dev;
+        DeviceGuard g(dev);
+        mlfma_status st;
+        try {
+            st = setup_device(p.get());
+        } catch (const std::bad_alloc &) {
+            st = fail(MLFMA_ENOMEM, "host allocation failed during device setup");
+        }
+        if (st != MLFMA_OK) {
+            p->mem.free_all();
+            return st;
+        }
+        p->on_device = true;
+    }
+    p->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = p.release();
+    return MLFMA_OK;
+}
+
+mlfma_status mlfma_num_unknowns(mlfma_plan_t p, int64_t *n)
+{
+    if (check_plan(p)) return MLFMA_EINVAL;
+    if (!n) return fail(MLFMA_EINVAL, "n is NULL");
+    *n = p->host.N;
+    return MLFMA_OK;
+}
+
+mlfma_status mlfma_rwg_edges(mlfma_plan_t p, int32_t *edge_v, int32_t *tri_pm)
+{
+    if (check_plan(p)) return MLFMA_EINVAL;
+    if (edge_v) std::memcpy(edge_v, p->host.rwg.edge_v.data(), p->host.rwg.edge_v.size() * sizeof(int32_t));
+    if (tri_pm) std::memcpy(tri_pm, p->host.rwg.tri.data(), p->host.rwg.tri.size() * sizeof(int32_t));
+    return MLFMA_OK;
+}
+
+mlfma_status mlfma_matvec(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)
+{
+    return product(p, x, xc, y, B, prec, stream, 0, false);
+}
+
+mlfma_status mlfma_matvec_adjoint(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)
+{
+    return product(p, x, xc, y, B, prec, stream, 1, false);
+}
+
+mlfma_status mlfma_matvec_host(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)
+{
+    return product(p, x, xc, y, B, prec, stream, 0, true);
+}
+
+mlfma_status mlfma_sync(mlfma_plan_t p, void *stream)
+{
+    if (check_plan(p)) return MLFMA_EINVAL;
+    if (!p->on_device) return MLFMA_OK;
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "mlfma_sync");
+    return MLFMA_OK;
+}
+
+mlfma_status mlfma_plan_info(mlfma_plan_t p, mlfma_info *info)
+{
+    if (check_plan(p)) return MLFMA_EINVAL;
+    if (!info) return fail(MLFMA_EINVAL, "info is NULL");
+    std::memset(info, 0, sizeof(*info));
+    const PlanHost &H = p->host;
+    info->n = H.N;
+    info->levels = H.levels;
+    info->leaf_level = H.leaf;
+    info->root_side = H.root_side;
+    for (int d = 0; d < 3; ++d) info->root_center[d] = H.root_center[d];
+    info->near_nnz = H.nnz;
+    info->leaf_boxes = H.lv[H.leaf].nbox();
+    info->max_leaf_unknowns = H.max_leaf;
+    for (int l = 0; l < H.levels && l < MLFMA_MAX_LEVELS; ++l) {
+        info->box_count[l] = H.lv[l].nbox();
+        info->trunc_L[l] = H.lv[l].L;
+        info->samples_K[l] = H.lv[l].K;
+        info->translations[l] = (int64_t)H.lv[l].il_src.size();
+    }
+    info->device_bytes = p->mem.bytes;
+    info->setup_seconds = p->setup_seconds;
+    return MLFMA_OK;
+}
+
+mlfma_status mlfma_export(mlfma_plan_t p, int what, int level, void *dst, int64_t cap, int64_t *needed)
+{
+    if (check_plan(p)) return MLFMA_EINVAL;
+    const PlanHost &H = p->host;
+    std::vector<char> buf;
+    auto put = [&](const void *src, size_t n) { buf.assign((const char *)src, (const char *)src + n); };
+    const bool far_level = level >= 2 && level <= H.leaf;
+    switch (what) {
+    case MLFMA_X_PERM:
+        put(H.perm.data(), H.perm.size() * sizeof(int64_t));
+        break;
+    case MLFMA_X_LEAF_BOX:
+        put(H.leaf_box.data(), H.leaf_box.size() * sizeof(int32_t));
+        break;
+    case MLFMA_X_NEAR_COUNT:
+        put(&H.nnz, sizeof(int64_t));
+        break;
+    case MLFMA_X_BOX_CENTERS:
+        if (level < 0 || level > H.leaf) return fail(MLFMA_EINVAL, "level out of range");
+        put(H.lv[level].center.data(), H.lv[level].center.size() * sizeof(double));
+        break;
+    case MLFMA_X_GRID: {
+        if (!far_level) return fail(MLFMA_EINVAL, "level has no far work");
+        const Level &Lv = H.lv[level];
+        std::vector<double> g(4 * (size_t)Lv.K);
+        for (int q = 0; q < Lv.K; ++q) {
+            g[4 * q] = Lv.ct[q / Lv.nph];
+            g[4 * q + 1] = Lv.ph[q % Lv.nph];
+            g[4 * q + 2] = Lv.wt[q / Lv.nph] * 2.0 * M_PI / Lv.nph;
+            g[4 * q + 3] = Lv.th[q / Lv.nph];
+        }
+        put(g.data(), g.size() * sizeof(double));
+        break;
+    }
+    case MLFMA_X_ALPHA:
+        if (!far_level) return fail(MLFMA_EINVAL, "level has no far work");
+        put(H.lv[level].alpha.data(), H.lv[level].alpha.size() * sizeof(cd));
+        break;
+    case MLFMA_X_ALPHA_OFFS:
+        if (!far_level) return fail(MLFMA_EINVAL, "level has no far work");
+        put(H.lv[level].type_off.data(), H.lv[level].type_off.size() * sizeof(int32_t));
+        break;
+    case MLFMA_X_INTERP: {
+        if (!(level >= 2 && level < H.leaf)) return fail(MLFMA_EINVAL, "no interpolation into this level");
+        const Level &Pa = H.lv[level], &C = H.lv[level + 1];
+        std::vector<double> Mx((size_t)Pa.K * C.K, 0.0);
+        for (int t = 0; t < Pa.nth; ++t)
+            for (int u = 0; u < Pa.nph; ++u)
+                for (int e = Pa.ph_up.ptr[u]; e < Pa.ph_up.ptr[u + 1]; ++e) {
+                    const int v0 = Pa.ph_up.idx[e];
+                    for (int f = Pa.th_up.ptr[t]; f < Pa.th_up.ptr[t + 1]; ++f) {
+                        const int j = Pa.th_up.idx[f];
+                        const int v = Pa.th_up.refl[f] ? (v0 + C.nph / 2) % C.nph : v0;
+                        Mx[(size_t)(t * Pa.nph + u) * C.K + j * C.nph + v] += Pa.ph_up.coef[e] * Pa.th_up.coef[f];
+                    }
+                }
+        put(Mx.data(), Mx.size() * sizeof(double));
+        break;
+    }
+    case MLFMA_X_ANTERP: {
+        if (!(level >= 2 && level < H.leaf)) return fail(MLFMA_EINVAL, "no anterpolation from this level");
+        const Level &Pa = H.lv[level], &C = H.lv[level + 1];
+        std::vector<double> Ax((size_t)C.K * Pa.K, 0.0);
+        // child (j, v') <- theta rows (t, refl) of U(t, v), U(t, v) <- phi rows u of the parent
+        for (int j = 0; j < C.nth; ++j)
+            for (int vp = 0; vp < C.nph; ++vp)
+                for (int f = Pa.th_dn.ptr[j]; f < Pa.th_dn.ptr[j + 1]; ++f) {
+                    const int t = Pa.th_dn.idx[f];
+                    const int v = Pa.th_dn.refl[f] ? (vp + C.nph / 2) % C.nph : vp;
+                    for (int e = Pa.ph_dn.ptr[v]; e < Pa.ph_dn.ptr[v + 1]; ++e)
+                        Ax[(size_t)(j * C.nph + vp) * Pa.K + t * Pa.nph + Pa.ph_dn.idx[e]] +=
+                            Pa.th_dn.coef[f] * Pa.ph_dn.coef[e];
+                }
+        put(Ax.data(), Ax.size() * sizeof(double));
+        break;
+    }
+    default:
+        return fail(MLFMA_EINVAL, "unknown table");
+    }
+    if (needed) *needed = (int64_t)buf.size();
+    if (dst) {
+        if (cap < (int64_t)buf.size()) return fail(MLFMA_EINVAL, "destination too small");
+        std::memcpy(dst, buf.data(), buf.size());
+    }
+    return MLFMA_OK;
+}
+
+void mlfma_destroy(mlfma_plan_t p)
+{
+    if (!p) return;
+    if (p->on_device) {
+        DeviceGuard g(p->device);
+        cudaDeviceSynchronize();
+        p->mem.free_all();
+    }
+    delete p;
+}
+
+const char *mlfma_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

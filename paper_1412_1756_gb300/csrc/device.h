@@ -1,0 +1,89 @@
+// Device-side data of a plan and the launchers of its kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace mlfma {
+
+// Mesh and RWG data used by the FP64 setup kernels (leaf order for RWGs).
+struct DevMesh {
+    int nt = 0;
+    const double *tq = nullptr;     // [nt][7][3] quadrature points
+    const double *tv = nullptr;     // [nt][9]    vertices of each triangle
+    const int32_t *tvi = nullptr;   // [nt][3]    vertex indices
+    const double *area = nullptr;   // [nt]
+    const double *cen = nullptr;    // [nt][3]
+    const double *hmax = nullptr;   // [nt]
+    int64_t n = 0;
+    const int32_t *rtri = nullptr;  // [N][2] leaf order
+    const double *rvf = nullptr;    // [N][2][3] free vertex coordinates
+    const double *rlen = nullptr;   // [N]
+};
+
+struct DevNear {
+    int nleaf = 0;
+    const int32_t *box_ptr = nullptr;    // [nleaf+1]
+    const int64_t *strip_off = nullptr;  // [nleaf+1]
+    const int32_t *col_ptr = nullptr;    // [nleaf+1]
+    const int32_t *strip_col = nullptr;  // columns (leaf-order unknowns)
+};
+
+// One far level's tables in arithmetic type R (complex values as R pairs).
+template <class R>
+struct DevLevel {
+    int nbox = 0, L = 0, nth = 0, nph = 0, K = 0, ntype = 0;
+    const int32_t *il_ptr = nullptr, *il_src = nullptr, *il_type = nullptr;
+    const R *alpha = nullptr;            // [ntype][K][2]
+    const int32_t *parent = nullptr;     // [nbox] into level l-1
+    const int32_t *octant = nullptr;     // [nbox]
+    const int32_t *child_ptr = nullptr;  // [nbox+1] into level l+1
+    const R *shift = nullptr;            // [8][K][2] (parents only)
+    // to children (parents only): up stencils rows = this level's nth / nph;
+    // down stencils rows = child nth / nph
+    const int32_t *thu_ptr = nullptr, *thu_idx = nullptr, *thu_refl = nullptr;
+    const R *thu_c = nullptr;
+    const int32_t *phu_ptr = nullptr, *phu_idx = nullptr;
+    const R *phu_c = nullptr;
+    const int32_t *thd_ptr = nullptr, *thd_idx = nullptr, *thd_refl = nullptr;
+    const R *thd_c = nullptr;
+    const int32_t *phd_ptr = nullptr, *phd_idx = nullptr;
+    const R *phd_c = nullptr;
+    const R *wq = nullptr;               // [K] quadrature weight (leaf: times -k^2 eta / 4 pi)
+    R *S = nullptr;                      // outgoing field [nbox][2][K][B]
+    R *G = nullptr;                      // incoming field [nbox][2][K][B]
+};
+
+// ------------------------------------------------------------ setup ---
+cudaError_t launch_mesh_geometry(const double *V, const int32_t *T, int nt, double *tq, double *tv, double *area,
+                                 double *cen, double *hmax, cudaStream_t s);
+cudaError_t launch_near_fill(const DevMesh &m, const DevNear &nr, double k, double eta, double2 *val,
+                             cudaStream_t s);
+cudaError_t launch_leaf_patterns(const DevMesh &m, const int32_t *ubox, const double *box_center, int K,
+                                 const double *grid /* [K][9]: khat, theta-hat, phi-hat */, double k, double2 *V, cudaStream_t s);
+cudaError_t launch_cast_c64_to_c32(const double2 *src, float2 *dst, int64_t n, cudaStream_t s);
+
+// ------------------------------------------------------------ product ---
+template <class R>
+struct ProductArgs {
+    int64_t n = 0;
+    int B = 0;                 // internal real columns
+    int leaf = 0, levels = 0;  // levels with far work: 2..leaf
+    DevNear nr;
+    const R *near_val = nullptr;    // complex, strip layout
+    const R *V = nullptr;           // leaf patterns [N][K][2] complex
+    const int32_t *ubox = nullptr;  // [N] leaf box of each leaf-order unknown
+    const int64_t *perm = nullptr;  // [N]
+    R *xp = nullptr;                // [N][B] real
+    R *yp = nullptr;                // [N][B] complex
+    R *scratch = nullptr;           // interpolation scratch
+    DevLevel<R> lv[22];
+};
+
+// Runs y_user = Z x_user (or its adjoint) on stream s.  x_user / y_user in
+// the caller's layout ([N][Bu], complex or real x, complex y).
+template <class R>
+cudaError_t run_product(const ProductArgs<R> &a, const void *x_user, int x_complex, void *y_user, int Bu,
+                        int adjoint, cudaStream_t s);
+
+}  // namespace mlfma

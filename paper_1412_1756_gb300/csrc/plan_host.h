@@ -1,0 +1,91 @@
+// Host-side plan of the multilevel fast multipole product (FP64 tables).
+// Section III-C: oct-tree with level 0 the enclosing cube; far work from
+// level 2 to the leaf level; uniform phi / Gauss-Legendre theta sampling;
+// local Lagrange interpolation between levels.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace mlfma {
+
+using cd = std::complex<double>;
+
+struct RwgList {
+    std::vector<int32_t> edge_v;  // [N][2]  smaller, larger vertex index
+    std::vector<int32_t> tri;     // [N][2]  T+, T-
+    std::vector<int32_t> vfree;   // [N][2]  free vertex of T+, of T-
+    std::vector<double> len;      // [N]
+};
+
+// Row-wise sparse stencil: row r uses entries ptr[r] .. ptr[r+1]-1.
+struct Stencil {
+    std::vector<int32_t> ptr;
+    std::vector<int32_t> idx;
+    std::vector<int32_t> refl;    // theta stencils: 1 = sample taken at phi + pi
+    std::vector<double> coef;     // pole reflection sign folded in
+};
+
+struct Level {
+    int l = 0;
+    double a = 0.0;                 // box side
+    // sampling grid (levels with far work)
+    int L = 0, nth = 0, nph = 0, K = 0;
+    std::vector<double> ct, th, wt, ph;   // cos theta, theta, GL weight, phi
+    // boxes
+    std::vector<uint64_t> code;     // occupied boxes, Morton order
+    std::vector<double> center;     // [nbox][3]
+    std::vector<int32_t> parent;    // index into level l-1
+    std::vector<int32_t> octant;    // position within the parent (x<<2 | y<<1 | z)
+    std::vector<int32_t> child_ptr; // [nbox+1] range in level l+1
+    // translation (l >= 2)
+    std::vector<int32_t> il_ptr, il_src, il_type;
+    std::vector<int32_t> type_off;  // [ntype][3]
+    int ntype = 0;
+    std::vector<cd> alpha;          // [ntype][K]
+    // to/from children (2 <= l < leaf)
+    std::vector<cd> shift;          // [8][K]: exp(i k khat.(r_parent - r_child))
+    Stencil th_up, ph_up;           // child grid -> this grid (rows: nth / nph of this level)
+    Stencil ph_dn, th_dn;           // weighted transposes (rows: child nph / child nth)
+    int nbox() const { return (int)code.size(); }
+};
+
+struct PlanHost {
+    // inputs
+    std::vector<double> V;          // [nv][3]
+    std::vector<int32_t> T;         // [nt][3]
+    double k = 0, digits = 3, eta = 376.730313668;
+    int levels = 0, leaf = 0, order = 6;
+    // derived
+    RwgList rwg;
+    int64_t N = 0;
+    double root_side = 0, root_center[3] = {0, 0, 0}, origin[3] = {0, 0, 0};
+    std::vector<int64_t> perm;      // leaf-order position -> canonical index
+    std::vector<int32_t> leaf_box;  // canonical index -> leaf box
+    std::vector<int32_t> box_ptr;   // [nleaf+1] positions in leaf order
+    std::vector<Level> lv;          // [levels]
+    // near field: per leaf box, a dense strip [rows of the box] x
+    // [columns of all neighbour boxes], column-major
+    std::vector<int32_t> nb_ptr, nb_box;
+    std::vector<int64_t> strip_off; // [nleaf+1] element offsets
+    std::vector<int32_t> col_ptr;   // [nleaf+1] into strip_col
+    std::vector<int32_t> strip_col; // leaf-order unknown of each strip column
+    int64_t nnz = 0;
+    int max_leaf = 0;
+};
+
+// Builds everything above from (verts, tris).  Returns "" or an error text.
+std::string build_plan_host(PlanHost &P, const double *verts, int64_t nv, const int32_t *tris,
+                            int64_t nt, double k, int levels, double digits, int order, double eta);
+
+// Truncation number of Section V, Eq. (9), d = sqrt(3) a.
+int truncation_number(double k, double a, double digits);
+
+// Special functions (FP64), exported for the plan's own use.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
+void sph_bessel_j(int nmax, double x, std::vector<double> &j);
+void sph_bessel_y(int nmax, double x, std::vector<double> &y);
+
+}  // namespace mlfma

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of the C ABI in include/mlfma.h.
+
+Argument marshalling only: every step of the product runs in the CUDA
+library.  PyTorch supplies device memory and the current stream.  If the
+compiled library is missing this module raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+FP64 = 0
+FP32 = 1
+MAX_LEVELS = 22
+
+X_PERM, X_LEAF_BOX, X_GRID, X_ALPHA, X_ALPHA_OFFS, X_INTERP, X_BOX_CENTERS, X_NEAR_COUNT, X_ANTERP = range(1, 10)
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ENOTSUP"}
+
+EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg_edges", "mlfma_matvec",
+            "mlfma_matvec_adjoint", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
+            "mlfma_destroy", "mlfma_last_error"]
+
+
+class MlfmaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("interp_order", ctypes.c_int), ("max_batch", ctypes.c_int), ("precisions", ctypes.c_int),
+                ("host_only", ctypes.c_int), ("device", ctypes.c_int), ("eta", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("levels", ctypes.c_int), ("leaf_level", ctypes.c_int),
+                ("root_side", ctypes.c_double), ("root_center", ctypes.c_double * 3),
+                ("near_nnz", ctypes.c_int64), ("leaf_boxes", ctypes.c_int64), ("max_leaf_unknowns", ctypes.c_int),
+                ("box_count", ctypes.c_int * MAX_LEVELS), ("trunc_L", ctypes.c_int * MAX_LEVELS),
+                ("samples_K", ctypes.c_int * MAX_LEVELS), ("translations", ctypes.c_int64 * MAX_LEVELS),
+                ("device_bytes", ctypes.c_int64), ("setup_seconds", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the compiled library (build it first when asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("MLFMA CUDA library not built (%s); call __graft_entry__.build() or "
+                               "paper_1412_1756_gb300._build.build()" % path)
+        _build.build()
+    L = ctypes.CDLL(path)
+    P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.mlfma_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.mlfma_plan.argtypes = [P, I64, P, I64, ctypes.c_double, I, ctypes.c_double, ctypes.POINTER(Opts),
+                             ctypes.POINTER(P)]
+    L.mlfma_num_unknowns.argtypes = [P, ctypes.POINTER(I64)]
+    L.mlfma_rwg_edges.argtypes = [P, P, P]
+    for f in ("mlfma_matvec", "mlfma_matvec_adjoint", "mlfma_matvec_host"):
+        getattr(L, f).argtypes = [P, P, I, P, I64, I, P]
+    L.mlfma_sync.argtypes = [P, P]
+    L.mlfma_plan_info.argtypes = [P, ctypes.POINTER(Info)]
+    L.mlfma_export.argtypes = [P, I, I, P, I64, ctypes.POINTER(I64)]
+    L.mlfma_destroy.argtypes = [P]
+    L.mlfma_destroy.restype = None
+    L.mlfma_last_error.argtypes = []
+    L.mlfma_last_error.restype = ctypes.c_char_p
+    for f in EXPORTED:
+        if f not in ("mlfma_destroy", "mlfma_last_error"):
+            getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise MlfmaError(status, load().mlfma_last_error().decode())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class MlfmaPlan:
+    """A plan for y = Z x on one mesh at one wavenumber (include/mlfma.h)."""
+
+    def __init__(self, verts, tris, k, levels, digits=3.0, interp_order=6, max_batch=64,
+                 precisions=(FP32, FP64), host_only=False, device=None, eta=None):
+        L = load()
+        self._lib = L
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tris, dtype=np.int32)
+        o = Opts()
+        _check(L.mlfma_default_opts(ctypes.byref(o)))
+        o.interp_order = int(interp_order)
+        o.max_batch = int(max_batch)
+        o.precisions = sum(1 << p for p in precisions)
+        o.host_only = 1 if host_only else 0
+        if device is not None:
+            o.device = int(device)
+        elif not host_only:
+            import torch
+            o.device = torch.cuda.current_device()
+        if eta is not None:
+            o.eta = float(eta)
+        h = ctypes.c_void_p()
+        _check(L.mlfma_plan(_np_ptr(v), v.shape[0], _np_ptr(t), t.shape[0], float(k), int(levels),
+                            float(digits), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.k = float(k)
+        self.max_batch = int(max_batch)
+        self.host_only = bool(host_only)
+        n = ctypes.c_int64()
+        _check(L.mlfma_num_unknowns(h, ctypes.byref(n)))
+        self.n = int(n.value)
+
+    # ------------------------------------------------------------ queries
+    def info(self) -> dict:
+        inf = Info()
+        _check(self._lib.mlfma_plan_info(self._h, ctypes.byref(inf)))
+        nl = inf.levels
+        return {
+            "n": inf.n, "levels": nl, "leaf_level": inf.leaf_level, "root_side": inf.root_side,
+            "root_center": list(inf.root_center), "near_nnz": inf.near_nnz, "leaf_boxes": inf.leaf_boxes,
+            "max_leaf_unknowns": inf.max_leaf_unknowns, "box_count": list(inf.box_count[:nl]),
+            "trunc_L": list(inf.trunc_L[:nl]), "samples_K": list(inf.samples_K[:nl]),
+            "translations": list(inf.translations[:nl]), "device_bytes": inf.device_bytes,
+            "setup_seconds": inf.setup_seconds,
+        }
+
+    def rwg_edges(self):
+        ev = np.zeros((self.n, 2), np.int32)
+        tp = np.zeros((self.n, 2), np.int32)
+        _check(self._lib.mlfma_rwg_edges(self._h, _np_ptr(ev), _np_ptr(tp)))
+        return ev, tp
+
+    def export(self, what: int, level: int = 0) -> np.ndarray:
+        need = ctypes.c_int64()
+        _check(self._lib.mlfma_export(self._h, what, level, None, 0, ctypes.byref(need)))
+        buf = np.zeros(need.value, np.uint8)
+        _check(self._lib.mlfma_export(self._h, what, level, _np_ptr(buf), need.value, ctypes.byref(need)))
+        if what == X_PERM:
+            return buf.view(np.int64)
+        if what in (X_LEAF_BOX,):
+            return buf.view(np.int32)
+        if what == X_NEAR_COUNT:
+            return buf.view(np.int64)
+        if what == X_ALPHA_OFFS:
+            return buf.view(np.int32).reshape(-1, 3)
+        if what == X_GRID:
+            return buf.view(np.float64).reshape(-1, 4)
+        if what == X_ALPHA:
+            return buf.view(np.complex128)
+        if what == X_BOX_CENTERS:
+            return buf.view(np.float64).reshape(-1, 3)
+        return buf.view(np.float64)
+
+    # ----------------------------------------------------------- products
+    @staticmethod
+    def _prec_of(dtype):
+        import torch
+        if dtype in (torch.float32, torch.complex64):
+            return FP32
+        if dtype in (torch.float64, torch.complex128):
+            return FP64
+        raise TypeError("x must be float32/float64/complex64/complex128, got %s" % dtype)
+
+    def _product(self, fn, x, y, stream):
+        import torch
+        if not x.is_cuda:
+            raise ValueError("x must be a CUDA tensor (use matvec_host for host arrays)")
+        squeeze = x.dim() == 1
+        x2 = x.reshape(self.n, -1) if squeeze else x
+        if x2.dim() != 2 or x2.shape[0] != self.n:
+            raise ValueError("x must be [N] or [N, B] with N = %d" % self.n)
+        x2 = x2.contiguous()
+        prec = self._prec_of(x2.dtype)
+        xc = 1 if x2.is_complex() else 0
+        cdt = torch.complex64 if prec == FP32 else torch.complex128
+        B = x2.shape[1]
+        if y is None:
+            y = torch.empty((self.n, B), dtype=cdt, device=x2.device)
+        if y.dtype != cdt or not y.is_contiguous() or y.numel() != self.n * B:
+            raise ValueError("y must be a contiguous %s tensor with N*B elements" % cdt)
+        s = torch.cuda.current_stream(x2.device).cuda_stream if stream is None else stream
+        _check(fn(self._h, ctypes.c_void_p(x2.data_ptr()), xc, ctypes.c_void_p(y.data_ptr()), B, prec,
+                  ctypes.c_void_p(s)))
+        return y.reshape(self.n) if squeeze else y.reshape(self.n, B)
+
+    def matvec(self, x, y=None, stream=None):
+        """y = Z x for a CUDA tensor x [N] or [N, B] (real or complex)."""
+        return self._product(self._lib.mlfma_matvec, x, y, stream)
+
+    def matvec_adjoint(self, x, y=None, stream=None):
+        """y = Z^H x."""
+        return self._product(self._lib.mlfma_matvec_adjoint, x, y, stream)
+
+    def matvec_host(self, x: np.ndarray, prec: int = FP32, y: np.ndarray = None, stream=None) -> np.ndarray:
+        """y = Z x for HOST arrays (copies inside the call; waits for completion)."""
+        rdt = np.float32 if prec == FP32 else np.float64
+        cdt = np.complex64 if prec == FP32 else np.complex128
+        squeeze = x.ndim == 1
+        x2 = x.reshape(self.n, -1)
+        xc = 1 if np.iscomplexobj(x2) else 0
+        x2 = np.ascontiguousarray(x2, dtype=cdt if xc else rdt)
+        B = x2.shape[1]
+        if y is None:
+            y = np.empty((self.n, B), dtype=cdt)
+        _check(self._lib.mlfma_matvec_host(self._h, _np_ptr(x2), xc, _np_ptr(y), B, prec,
+                                           ctypes.c_void_p(stream or 0)))
+        return y.reshape(self.n) if squeeze else y
+
+    def sync(self, stream=None):
+        _check(self._lib.mlfma_sync(self._h, ctypes.c_void_p(stream or 0)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mlfma_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

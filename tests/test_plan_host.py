@@ -1,0 +1,163 @@
+"""Host-side plan logic of the C-ABI library, on CPU (host_only plans: no GPU
+is touched).  Checked against the oracle's independent RWG list, against the
+addition theorem (Section III-A, Eqs. (7)-(8)) and the E1 point test of
+Section V, and against exactness properties of the interpolation and
+anterpolation (Section III-C)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle.rwg import rwg_list
+from paper_1412_1756_gb300 import mlfma as M
+
+
+def host_plan(name, **kw):
+    W = workloads.get(name)
+    v, t = W.mesh()
+    return W, v, t, M.MlfmaPlan(v, t, W.k, W.levels, W.digits, host_only=True, **kw)
+
+
+def test_library_exports_every_declared_symbol():
+    import ctypes
+    import re
+    import os
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "mlfma.h")).read()
+    declared = set(re.findall(r"^(?:mlfma_status|void|const char \*)\s*(mlfma_\w+)\(", hdr, re.M))
+    assert declared == set(M.EXPORTED)
+    lib = ctypes.CDLL(M.library_path())
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("name", ["sphere-r0.5m-ico3", "sphere-r2m-ico5", "plate6m-strips"])
+def test_rwg_list_matches_oracle(name):
+    W, v, t, P = host_plan(name)
+    ev, tp = P.rwg_edges()
+    r = rwg_list(v, t)
+    assert P.n == W.n_expected
+    assert np.array_equal(ev, r["edge_v"]) and np.array_equal(tp, r["tri"])
+
+
+def test_bad_meshes_rejected():
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1]], float)
+    for tris in ([[0, 1, 2], [1, 0, 3], [0, 1, 4]], [[0, 1, 2], [0, 1, 3]], [[0, 1, 7]], [[0, 1, 1]]):
+        with pytest.raises(M.MlfmaError) as e:
+            M.MlfmaPlan(v, np.array(tris), 2 * math.pi, 3, host_only=True)
+        assert e.value.status == 1
+    with pytest.raises(M.MlfmaError):
+        M.MlfmaPlan(v, np.array([[0, 1, 2], [1, 0, 3]]), -1.0, 3, host_only=True)
+    with pytest.raises(M.MlfmaError):
+        M.MlfmaPlan(v, np.array([[0, 1, 2], [1, 0, 3]]), 1.0, 1, host_only=True)
+    with pytest.raises(M.MlfmaError):
+        M.MlfmaPlan(v, np.array([[0, 1, 2], [1, 0, 3]]), 1.0, 3, interp_order=5, host_only=True)
+
+
+def test_tree_and_lists_sphere_r2():
+    """Sizes of the five-level tree on the 30,720-unknown sphere: every
+    unknown in exactly one leaf box, a box-pair near structure, and
+    interaction lists that, with the near lists, cover every leaf pair once."""
+    W, v, t, P = host_plan("sphere-r2m-ico5")
+    inf = P.info()
+    assert inf["box_count"] == [1, 8, 56, 272, 1160]
+    assert inf["trunc_L"][2:] == [20, 13, 8]
+    assert inf["samples_K"][2:] == [882, 392, 162]
+    assert inf["translations"][2:] == [2504, 12216, 54000]
+    perm = P.export(M.X_PERM)
+    assert np.array_equal(np.sort(perm), np.arange(P.n))
+    assert inf["near_nnz"] == P.export(M.X_NEAR_COUNT)[0]
+
+
+def test_truncation_number_eq9():
+    """L = ceil(kd + 1.8 d0^(2/3) (kd)^(1/3)), d = sqrt(3) a (Section V)."""
+    W, v, t, P = host_plan("cube8m")
+    inf = P.info()
+    for l in range(2, inf["levels"]):
+        a = inf["root_side"] / 2 ** l
+        kd = W.k * math.sqrt(3) * a
+        assert inf["trunc_L"][l] == math.ceil(kd + 1.8 * 3.0 ** (2 / 3) * kd ** (1 / 3))
+        assert inf["samples_K"][l] == 2 * (inf["trunc_L"][l] + 1) ** 2
+
+
+def _grid(P, l):
+    g = P.export(M.X_GRID, l)
+    st = np.sqrt(1 - g[:, 0] ** 2)
+    kh = np.stack([st * np.cos(g[:, 1]), st * np.sin(g[:, 1]), g[:, 0]], 1)
+    th = np.stack([g[:, 0] * np.cos(g[:, 1]), g[:, 0] * np.sin(g[:, 1]), -st], 1)
+    ph = np.stack([-np.sin(g[:, 1]), np.cos(g[:, 1]), 0 * st], 1)
+    return g, kh, th, ph
+
+
+def test_grid_integrates_band_limited_exactly():
+    """(L+1) Gauss-Legendre nodes in cos(theta) x 2(L+1) uniform phi integrate
+    spherical polynomials of degree <= 2L+1 exactly: int exp(i k k.d) = 4 pi j0(k|d|)
+    for small |d|, and sum of weights = 4 pi."""
+    W, v, t, P = host_plan("sphere-r2m-ico5")
+    g, kh, _, _ = _grid(P, 2)
+    assert abs(g[:, 2].sum() - 4 * math.pi) < 1e-12
+    d = np.array([0.1, -0.2, 0.15])
+    val = np.sum(g[:, 2] * np.exp(1j * W.k * (kh @ d)))
+    x = W.k * np.linalg.norm(d)
+    assert abs(val - 4 * math.pi * math.sin(x) / x) < 1e-12
+
+
+def _point_test(a, d0, ri, rm, rj, rmp, offset=(2, 0, 0)):
+    k = 2 * math.pi
+    v, t = workloads.cube(4 * a, 8)
+    P = M.MlfmaPlan(v, t, k, 3, d0, host_only=True)
+    g, kh, _, _ = _grid(P, 2)
+    al = P.export(M.X_ALPHA, 2).reshape(-1, g.shape[0])
+    offs = P.export(M.X_ALPHA_OFFS, 2)
+    ti = [i for i, o in enumerate(offs) if tuple(o) == offset][0]
+    ri, rm, rj, rmp = (np.asarray(z) * a for z in (ri, rm, rj, rmp))
+    assert np.allclose(rm - rmp, np.array(offset) * a)
+    r = np.linalg.norm(ri - rj)
+    exact = np.exp(1j * k * r) / r
+    approx = 1j * k / (4 * math.pi) * np.sum(g[:, 2] * np.exp(1j * k * (kh @ ((ri - rm) + (rmp - rj)))) * al[ti])
+    return abs(approx - exact) / abs(exact)
+
+
+def test_addition_theorem_benign_points():
+    """Points close to their group centres: the truncated Gegenbauer series
+    converges like (|d|/|r|)^L, so Eq. (7) with the table of Eq. (8) must
+    reproduce exp(ikr)/r to ~1e-10."""
+    for a in (0.5, 1.0, 2.0):
+        err = _point_test(a, 3.0, (2.55, 0.45, 0.52), (2.5, 0.5, 0.5), (0.47, 0.53, 0.5), (0.5, 0.5, 0.5))
+        assert err < 1e-9, (a, err)
+
+
+def test_e1_point_test_case1():
+    """Section V, Case 1 geometry: source (0.9999a, a, 0) in the group centred
+    at (a/2, a/2, a/2); observer (2.9999a, 0, a) in the group centred at
+    (2.5a, a/2, a/2); L from Eq. (9) with d0 = 3.  Error falls with a/lambda
+    and reaches the 3-digit level from a = lambda on."""
+    errs = []
+    for a in (0.25, 0.5, 1.0, 2.0, 4.0):
+        errs.append(_point_test(a, 3.0, (2.9999, 0, 1.0), (2.5, 0.5, 0.5), (0.9999, 1.0, 0.0), (0.5, 0.5, 0.5)))
+    assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:])), errs
+    assert errs[0] < 1e-2 and errs[1] < 3e-3 and max(errs[2:]) < 1e-3, errs
+
+
+@pytest.mark.parametrize("order,tol", [(6, 3e-3), (8, 1e-3), (10, 5e-4)])
+def test_interpolation_band_limited(order, tol):
+    """Local Lagrange interpolation (Section III-C) of the pattern of a point
+    current inside a child box to the parent grid, theta and phi components,
+    converging with the order; anterpolation is exactly
+    W_child^-1 Interp^T W_parent."""
+    W, v, t, P = host_plan("sphere-r2m-ico5", interp_order=order)
+    for l in (2, 3):
+        gp, khp, thp, php = _grid(P, l)
+        gc, khc, thc, phc = _grid(P, l + 1)
+        Mx = P.export(M.X_INTERP, l).reshape(gp.shape[0], gc.shape[0])
+        A = P.export(M.X_ANTERP, l).reshape(gc.shape[0], gp.shape[0])
+        assert np.abs(A - (Mx.T * gp[None, :, 2]) / gc[:, 2, None]).max() < 1e-14
+        ac = P.info()["root_side"] / 2 ** (l + 1)
+        rng = np.random.default_rng(l)
+        for _ in range(10):
+            d = rng.uniform(-0.5, 0.5, 3) * ac * 1.2
+            pol = rng.standard_normal(3)
+            for tc, tp in ((thc, thp), (phc, php)):
+                fc = (tc @ pol) * np.exp(1j * W.k * (khc @ d))
+                fp = (tp @ pol) * np.exp(1j * W.k * (khp @ d))
+                assert np.abs(Mx @ fc - fp).max() < tol * np.abs(fp).max()
