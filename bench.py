@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput of the MLFMA product y = Z x (Galerkin EFIE, RWG basis) on one
+GB300: matvecs/s of the mixed-precision (complex FP32) batched pass, with the
+plain FP64 single-vector pass on the same GPU and inputs beside it, the error
+against the FP64 oracle on the timed inputs, and the roofline fraction of the
+dominant kernel.
+
+Default workload: PEC sphere of radius 2 m at wavelength 1 m, icosphere
+subdivision 5 (20,480 triangles, 30,720 RWG unknowns), 5-level tree, d0 = 3,
+B = 64 real N(0,1) right-hand sides per pass (one matvec = one column).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  With N > 1 (torchrun) every rank runs an
+independent replica of the same workload (the product does not shard in one
+step); value is the sum over ranks, time the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "MLFMA Z·x matvecs/s (mixed+batched vs FP64, same GPU, err≤1e-3); %HBM roofline"
+UNIT = "matvec/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="sphere-r2m-ico5")
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def algorithmic(info, B, stage, rsz=4):
+    """Algorithmic bytes (and flops) of one launch of a stage at B columns:
+    every operand read once and every result written once (complex = 2 rsz)."""
+    n = info["n"]
+    csz = 2 * rsz
+    leaf = info["leaf_level"]
+    K = info["samples_K"]
+    nb = info["box_count"]
+    field = lambda l: nb[l] * 2 * K[l] * B * csz
+    if stage == "near":
+        return info["near_nnz"] * csz + n * B * rsz + n * B * csz, 8 * info["near_nnz"] * B
+    if stage == "radiate":
+        return n * K[leaf] * 2 * csz + n * B * rsz + field(leaf), 8 * n * K[leaf] * B
+    if stage == "receive":
+        return n * K[leaf] * 2 * csz + field(leaf) + 2 * n * B * csz, 16 * n * K[leaf] * B
+    if stage.startswith("up"):
+        l = int(stage[2:])
+        return field(l + 1) + field(l), 0
+    if stage.startswith("down"):
+        l = int(stage[4:])
+        return field(l) + 2 * field(l + 1), 0
+    if stage.startswith("translate"):
+        l = int(stage[9:])
+        return 2 * field(l), 2 * 8 * info["translations"][l] * K[l] * B
+    return 0, 0
+
+
+def oracle_rate(wl, v, t, B, seconds, seed=7):
+    """The FP64 CPU oracle as it stands: exact rows of Z x (each O(N)),
+    timed on this host's cores; returns (matvecs/s, rows, cores, seconds)."""
+    from oracle import efie
+    P = efie.Problem(v, t, wl.k)
+    x = workloads.rhs(P.n, B, wl.seed)
+    rng = np.random.default_rng(seed)
+    cores = efie.num_threads()
+    rows = max(cores, 8)
+    t0 = time.perf_counter()
+    P.matvec_rows(x, rng.choice(P.n, rows, replace=False))
+    dt = time.perf_counter() - t0
+    total_rows = rows
+    while dt < seconds:
+        more = int(max(cores, min(8 * rows, rows * (seconds - dt) / max(dt, 1e-3))))
+        t1 = time.perf_counter()
+        P.matvec_rows(x, rng.choice(P.n, more, replace=False))
+        dt += time.perf_counter() - t1
+        total_rows += more
+        if time.perf_counter() - t0 > 3 * seconds:
+            break
+    per_row = dt / total_rows
+    # one full product of B columns costs N rows; a column is one matvec
+    return B / (per_row * P.n), total_rows, cores, dt
+
+
+# --------------------------------------------------------------- reference
+def run_reference(a, rank):
+    if rank != 0:
+        return
+    wl = workloads.get(a.workload)
+    v, t = wl.mesh()
+    secs = max(10.0, min(60.0, a.cpu_seconds))
+    vals = []
+    rows_total, cores = 0, 1
+    t0 = time.perf_counter()
+    for step in range(a.warmup + a.steps):
+        # each step: a bounded sample of exact rows of the same product
+        rate, rows, cores, dt = oracle_rate(wl, v, t, a.batch, secs / max(1, a.steps + a.warmup), seed=step)
+        if step >= a.warmup:
+            vals.append(rate)
+            rows_total += rows
+    wall = time.perf_counter() - t0
+    value = float(np.median(vals))
+    n = 30720 if wl.n_expected == 0 else wl.n_expected
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * a.batch / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": {"workload": wl.name, "N": n, "levels": wl.levels, "digits": wl.digits,
+                                        "batch": a.batch},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d exact rows of Z x (FP64 CPU oracle, on-the-fly, O(N) each) over %d steps, "
+                                   "extrapolated to N rows; %.1f s wall" % (rows_total, a.steps, wall)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank)
+
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+
+    from paper_1412_1756_gb300 import FP32, FP64, MlfmaPlan
+
+    wl = workloads.get(a.workload)
+    v, t = wl.mesh()
+    B = a.batch
+    plan = MlfmaPlan(v, t, wl.k, wl.levels, wl.digits, max_batch=max(B, 1), device=local)
+    info = plan.info()
+    n = plan.n
+    x_np = workloads.rhs(n, B, wl.seed)
+    x32 = torch.from_numpy(x_np).to("cuda", torch.float32)
+    x64_1 = torch.from_numpy(x_np[:, :1].copy()).to("cuda", torch.float64)
+    y32 = torch.empty((n, B), dtype=torch.complex64, device="cuda")
+    y64 = torch.empty((n, 1), dtype=torch.complex128, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for s in range(steps):
+            flush.zero_()           # evict L2 between steps (outside the events)
+            ev[s][0].record(stream)
+            fn()
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        if dist:
+            tt = torch.tensor([ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms
+
+    # --- mixed precision, batched (the headline)
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: plan.matvec(x32, y32), a.steps, a.warmup)
+    clocks = clk.summary()
+    value_rank = B * a.steps / (ms / 1e3)
+    value = value_rank * world
+    # --- plain FP64 single vector on the same GPU and input column
+    steps64 = max(3, a.steps)
+    ms64 = timed(lambda: plan.matvec(x64_1, y64), steps64, a.warmup)
+    fp64_rate = steps64 / (ms64 / 1e3)
+
+    # --- error against the FP64 oracle on the timed inputs (sampled rows)
+    y32_np = y32.cpu().numpy()
+    y64_np = y64.cpu().numpy()
+    err = None
+    if rank == 0:
+        from oracle import efie
+        idx = np.random.default_rng(11).choice(n, 16, replace=False)
+        ref = efie.Problem(v, t, wl.k).matvec_rows(x_np, idx)
+        err = float(np.linalg.norm(y32_np[idx] - ref) / np.linalg.norm(ref))
+        err64 = float(np.linalg.norm(y64_np[idx, 0] - ref[:, 0]) / np.linalg.norm(ref[:, 0]))
+
+    # --- per-stage device times (serial pass) and roofline of the dominant kernel
+    stage_runs = [plan.profile_stages(x32, y32) for _ in range(3)]
+    stages = {k: float(np.median([r[k] for r in stage_runs])) for k in stage_runs[0]}
+    dom = max((k for k in stages if k not in ("prepare", "finalize")), key=lambda k: stages[k])
+    hbm_peak, peak_src = peaks()
+    abytes, aflops = algorithmic(info, B, dom)
+    dom_ms = stages[dom]
+    roof = {"kernel": dom, "bound": "hbm", "achieved": abytes / (dom_ms / 1e3) / 1e9, "peak": hbm_peak,
+            "unit": "GB/s", "frac": abytes / (dom_ms / 1e3) / 1e9 / hbm_peak, "traffic": None,
+            "algorithmic_bytes": abytes, "ms": dom_ms, "peak_source": peak_src,
+            "timing": "CUDA events around the kernel in a serial pass on the launching stream"}
+    hbm_stages = {}
+    for k, msk in stages.items():
+        b_, _ = algorithmic(info, B, k)
+        if b_ and msk > 0:
+            hbm_stages[k] = round(b_ / (msk / 1e3) / 1e9 / hbm_peak, 3)
+
+    # --- end to end through the public host-buffer entry point (pinned memory)
+    xh = torch.from_numpy(x_np.astype(np.float32)).pin_memory().numpy()
+    yh = torch.empty((n, B), dtype=torch.complex64).pin_memory().numpy()
+    for _ in range(a.warmup):
+        plan.matvec_host(xh, FP32, yh)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        plan.matvec_host(xh, FP32, yh)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": B * a.steps / e2e_s * world, "unit": UNIT, "h2d_bytes_per_step": int(xh.nbytes),
+           "d2h_bytes_per_step": int(yh.nbytes),
+           "how": "mlfma_matvec_host: pinned host x -> device, product, device -> pinned host y, stream sync"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        rate, rows, cores, secs = oracle_rate(wl, v, t, B, a.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d exact rows of Z x (FP64 CPU oracle, O(N) per row), %.1f s, extrapolated to "
+                         "N = %d rows for %d columns" % (rows, secs, n, B)}
+
+    nf = info["leaf_level"] - 2   # far levels beyond the coarsest
+    launches_per_step = 2 + 1 + (1 + nf) + nf + nf + 1 + 1   # prepare, near, radiate, translate, up, down, receive, finalize
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64", "data": "synthetic",
+            "config": {"workload": wl.name, "N": n, "levels": wl.levels, "digits": wl.digits, "batch": B,
+                       "interp_order": 6, "k": wl.k, "l2": "flushed between timed steps (256 MB write)",
+                       "mesh": "icosphere subdivision 5, radius 2 m"},
+            "fp64_single_vector": {"value": fp64_rate * world, "unit": UNIT, "ms_per_matvec": ms64 / steps64,
+                                   "speedup_of_mixed_batched": value / (fp64_rate * world)},
+            "err_vs_oracle": {"fp32_batched": err, "fp64_single": err64 if rank == 0 else None,
+                              "rows": 16, "bound": 1e-3},
+            "roofline": roof,
+            "hbm_frac_by_stage": hbm_stages,
+            "stage_ms": {k: round(vv, 4) for k, vv in stages.items()},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * a.steps,
+            "clocks": clocks,
+            "setup_s": info["setup_seconds"],
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

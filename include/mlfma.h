@@ -121,8 +121,12 @@ mlfma_status mlfma_rwg_edges(mlfma_plan_t plan, int32_t *edge_v, int32_t *tri_pm
  *  B      columns, 1..max_batch (complex x: 1..max_batch/2)
  *  prec   an mlfma_prec set up in the plan
  *  stream cudaStream_t or NULL
- * Asynchronous.  Errors: EINVAL (sizes, precision not set up, host-only
- * plan), ECUDA.
+ * Asynchronous.  The near field and the far pass are captured into a CUDA
+ * graph on the plan's own streams the first time a (precision, column
+ * count) pair is used and replayed afterwards; the graph's branches (near
+ * field, aggregation, per-level translations) run concurrently and join
+ * back into `stream`.  Errors: EINVAL (sizes, precision not set up,
+ * host-only plan), ECUDA.
  */
 mlfma_status mlfma_matvec(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
                           int64_t B, int prec, void *stream);
@@ -142,6 +146,19 @@ mlfma_status mlfma_matvec_adjoint(mlfma_plan_t plan, const void *x, int x_is_com
  */
 mlfma_status mlfma_matvec_host(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
                                int64_t B, int prec, void *stream);
+
+/*
+ * Measurement aid: the same product as mlfma_matvec, run serially on
+ * `stream` (no graph, no overlap) with a CUDA event after every stage, then
+ * waits for the stream.  stage_ms[MLFMA_STAGE_COUNT] receives the device
+ * time of each stage in ms: 0 prepare, 1 near field, 2 leaf radiation,
+ * 3 + l interpolation into level l, 25 + l translation at level l, 47 + l
+ * anterpolation from level l, 69 leaf reception, 70 finalize; stages that do
+ * not exist are 0.
+ */
+#define MLFMA_STAGE_COUNT 71
+mlfma_status mlfma_profile_stages(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
+                                  int64_t B, int prec, void *stream, double *stage_ms);
 
 /* Wait for the plan's work on `stream` and report any pending device-side
  * error. */

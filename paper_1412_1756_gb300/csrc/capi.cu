@@ -3,9 +3,11 @@
 #include "device.h"
 #include "plan_host.h"
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
 #include <string>
@@ -104,13 +106,19 @@ struct mlfma_plan_s {
     bool has32 = false, has64 = false;
     void *stage_x = nullptr, *stage_y = nullptr;   // host-API staging (largest type)
     double setup_seconds = 0;
+    CoreStreams cs;                                  // plan-owned streams/events of the core pass
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (precision, columns) -> captured core
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;   // caller stream <-> plan streams
+    StageClock clock;
 };
 
 namespace {
 
+constexpr int kIntSlots = 20;   // device integer tables per level
+
 template <class R>
 cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *near64, const double2 *V64,
-                            const std::vector<const int32_t *> &dev_ints)
+                            const std::vector<const int32_t *> &dev_ints, const std::vector<const int16_t *> &dev_ty)
 {
     PlanHost &H = p->host;
     DevMem &M = p->mem;
@@ -151,7 +159,11 @@ cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *ne
         DevLevel<R> &D = a.lv[l];
         D.nbox = Lv.nbox();
         D.L = Lv.L; D.nth = Lv.nth; D.nph = Lv.nph; D.K = Lv.K; D.ntype = Lv.ntype;
-        const int32_t *const *ip = &dev_ints[(size_t)l * 16];
+        const int32_t *const *ip = &dev_ints[(size_t)l * kIntSlots];
+        D.grp_ptr = ip[16]; D.grp_src = ip[17]; D.pchild_ptr = ip[18];
+        D.grp_ty = dev_ty[l];
+        D.nparent = H.lv[l - 1].nbox();
+        D.max_grp = Lv.max_grp;
         D.il_ptr = ip[0]; D.il_src = ip[1]; D.il_type = ip[2];
         D.parent = ip[3]; D.octant = ip[4]; D.child_ptr = ip[5];
         D.thu_ptr = ip[6]; D.thu_idx = ip[7]; D.thu_refl = ip[8];
@@ -238,6 +250,8 @@ mlfma_status setup_device(mlfma_plan_t p)
     CK(M.upload(H.strip_off, &nr.strip_off), "upload near");
     CK(M.upload(H.col_ptr, &nr.col_ptr), "upload near");
     CK(M.upload(H.strip_col, &nr.strip_col), "upload near");
+    for (int b = 0; b < nr.nleaf; ++b) nr.max_cols = std::max(nr.max_cols, H.col_ptr[b + 1] - H.col_ptr[b]);
+    nr.max_rows = H.max_leaf;
     void *near64;
     CK(M.alloc(&near64, (size_t)H.nnz * 16), "alloc near field");
     CK(launch_near_fill(dm, nr, H.k, H.eta, (double2 *)near64, 0), "near fill");
@@ -259,10 +273,15 @@ mlfma_status setup_device(mlfma_plan_t p)
         CK(launch_leaf_patterns(dm, d_ubox, d_bc, Lf.K, d_grid, H.k, (double2 *)V64, 0), "leaf patterns");
     }
     // integer tables shared by both precisions: 16 slots per level
-    std::vector<const int32_t *> ints((size_t)H.levels * 16, nullptr);
+    std::vector<const int32_t *> ints((size_t)H.levels * kIntSlots, nullptr);
+    std::vector<const int16_t *> tys((size_t)H.levels, nullptr);
     for (int l = 2; l <= H.leaf; ++l) {
         const Level &Lv = H.lv[l];
-        const int32_t **ip = &ints[(size_t)l * 16];
+        const int32_t **ip = &ints[(size_t)l * kIntSlots];
+        CK(M.upload(Lv.grp_ptr, &ip[16]), "upload lists");
+        CK(M.upload(Lv.grp_src, &ip[17]), "upload lists");
+        CK(M.upload(H.lv[l - 1].child_ptr, &ip[18]), "upload lists");
+        CK(M.upload(Lv.grp_ty, &tys[l]), "upload lists");
         CK(M.upload(Lv.il_ptr, &ip[0]), "upload lists");
         CK(M.upload(Lv.il_src, &ip[1]), "upload lists");
         CK(M.upload(Lv.il_type, &ip[2]), "upload lists");
@@ -285,17 +304,27 @@ mlfma_status setup_device(mlfma_plan_t p)
     const int prec = p->opts.precisions;
     if (prec & (1 << MLFMA_FP32)) {
         p->a32.nr = nr; p->a32.ubox = d_ubox; p->a32.perm = d_perm;
-        CK(setup_precision<float>(p, p->a32, (const double2 *)near64, (const double2 *)V64, ints), "setup FP32");
+        CK(setup_precision<float>(p, p->a32, (const double2 *)near64, (const double2 *)V64, ints, tys), "setup FP32");
         p->has32 = true;
     }
     if (prec & (1 << MLFMA_FP64)) {
         p->a64.nr = nr; p->a64.ubox = d_ubox; p->a64.perm = d_perm;
-        CK(setup_precision<double>(p, p->a64, (const double2 *)near64, (const double2 *)V64, ints), "setup FP64");
+        CK(setup_precision<double>(p, p->a64, (const double2 *)near64, (const double2 *)V64, ints, tys), "setup FP64");
         p->has64 = true;
     }
     const size_t stage = (size_t)H.N * p->opts.max_batch * 2 * sizeof(double);
     CK(M.alloc(&p->stage_x, stage), "alloc staging");
     CK(M.alloc(&p->stage_y, stage), "alloc staging");
+    if (prec & (1 << MLFMA_FP32)) CK(prime_kernels<float>(), "kernel attributes");
+    if (prec & (1 << MLFMA_FP64)) CK(prime_kernels<double>(), "kernel attributes");
+    CK(cudaStreamCreateWithFlags(&p->cs.main, cudaStreamNonBlocking), "create streams");
+    CK(cudaStreamCreateWithFlags(&p->cs.far, cudaStreamNonBlocking), "create streams");
+    CK(cudaStreamCreateWithFlags(&p->cs.tr, cudaStreamNonBlocking), "create streams");
+    for (auto &ev : p->cs.ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "create events");
+    CK(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming), "create events");
+    CK(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming), "create events");
+    CK(cudaEventCreate(&p->clock.start), "create events");
+    for (auto &ev : p->clock.ev) CK(cudaEventCreate(&ev), "create events");
     CK(cudaDeviceSynchronize(), "plan setup");
     if (!p->has64) {
         M.release(near64);
@@ -311,8 +340,90 @@ mlfma_status check_plan(mlfma_plan_t p)
     return MLFMA_OK;
 }
 
+void release_streams(mlfma_plan_t p)
+{
+    for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
+    p->graphs.clear();
+    for (cudaStream_t st : {p->cs.main, p->cs.far, p->cs.tr})
+        if (st) cudaStreamDestroy(st);
+    for (auto &ev : p->cs.ev)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : {p->ev_in, p->ev_out, p->clock.start})
+        if (ev) cudaEventDestroy(ev);
+    for (auto &ev : p->clock.ev)
+        if (ev) cudaEventDestroy(ev);
+}
+
+// The core pass (near field and far pass) for (precision, columns), captured
+// once into a CUDA graph on the plan's streams and replayed afterwards.
+template <class R>
+mlfma_status core_graph(mlfma_plan_t p, const ProductArgs<R> &a, int prec, cudaGraphExec_t *out)
+{
+    auto key = std::make_pair(prec, a.B);
+    auto it = p->graphs.find(key);
+    if (it != p->graphs.end()) {
+        *out = it->second;
+        return MLFMA_OK;
+    }
+    cudaError_t e = cudaStreamBeginCapture(p->cs.main, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    cudaError_t el = launch_core<R>(a, p->cs, nullptr);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(p->cs.main, &g);
+    if (el != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(el, "core pass launch");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    p->graphs[key] = ex;
+    *out = ex;
+    return MLFMA_OK;
+}
+
+template <class R>
+mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int xc, void *yd, int Bu, int adjoint,
+                 cudaStream_t s, double *stage_ms)
+{
+    cudaError_t e;
+    if (stage_ms) {
+        StageClock &clk = p->clock;
+        clk.n = 0;
+        CoreStreams serial{};
+        serial.main = s;
+        if ((e = cudaEventRecord(clk.start, s)) != cudaSuccess) return cuda_fail(e, "stage timer");
+        if ((e = launch_prepare<R>(a, xd, xc, Bu, adjoint, s)) != cudaSuccess) return cuda_fail(e, "prepare");
+        clk.stage[clk.n] = STAGE_PREPARE;
+        if ((e = cudaEventRecord(clk.ev[clk.n++], s)) != cudaSuccess) return cuda_fail(e, "stage timer");
+        if ((e = launch_core<R>(a, serial, &clk)) != cudaSuccess) return cuda_fail(e, "core pass");
+        if ((e = launch_finalize<R>(a, yd, xc, Bu, adjoint, s)) != cudaSuccess) return cuda_fail(e, "finalize");
+        clk.stage[clk.n] = STAGE_FINALIZE;
+        if ((e = cudaEventRecord(clk.ev[clk.n++], s)) != cudaSuccess) return cuda_fail(e, "stage timer");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stage timer");
+        for (int i = 0; i < STAGE_COUNT; ++i) stage_ms[i] = 0.0;
+        cudaEvent_t prev = clk.start;
+        for (int i = 0; i < clk.n; ++i) {
+            float ms = 0;
+            if ((e = cudaEventElapsedTime(&ms, prev, clk.ev[i])) != cudaSuccess) return cuda_fail(e, "stage timer");
+            stage_ms[clk.stage[i]] += ms;
+            prev = clk.ev[i];
+        }
+        return MLFMA_OK;
+    }
+    if ((e = launch_prepare<R>(a, xd, xc, Bu, adjoint, s)) != cudaSuccess) return cuda_fail(e, "prepare");
+    cudaGraphExec_t ex;
+    mlfma_status st = core_graph<R>(p, a, prec, &ex);
+    if (st != MLFMA_OK) return st;
+    if ((e = cudaGraphLaunch(ex, s)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    if ((e = launch_finalize<R>(a, yd, xc, Bu, adjoint, s)) != cudaSuccess) return cuda_fail(e, "finalize");
+    return MLFMA_OK;
+}
+
 mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream, int adjoint,
-                     bool host)
+                     bool host, double *stage_ms = nullptr)
 {
     if (check_plan(p)) return MLFMA_EINVAL;
     if (!p->on_device) return fail(MLFMA_EINVAL, "plan was built host-only; products need a device plan");
@@ -321,9 +432,9 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
     if (B < 1) return fail(MLFMA_EINVAL, "B must be >= 1");
     const int64_t Bi = B * (xc ? 2 : 1);
     if (Bi > p->opts.max_batch) return fail(MLFMA_EINVAL, "B exceeds the plan's max_batch");
+    if (prec != MLFMA_FP32 && prec != MLFMA_FP64) return fail(MLFMA_EINVAL, "unknown precision");
     if (prec == MLFMA_FP32 && !p->has32) return fail(MLFMA_EINVAL, "FP32 was not set up in this plan");
     if (prec == MLFMA_FP64 && !p->has64) return fail(MLFMA_EINVAL, "FP64 was not set up in this plan");
-    if (prec != MLFMA_FP32 && prec != MLFMA_FP64) return fail(MLFMA_EINVAL, "unknown precision");
     DeviceGuard g(p->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t rsz = prec == MLFMA_FP64 ? 8 : 4;
@@ -338,16 +449,17 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
         xd = p->stage_x;
         yd = p->stage_y;
     }
+    mlfma_status st;
     if (prec == MLFMA_FP64) {
         ProductArgs<double> a = p->a64;
         a.B = (int)Bi;
-        e = run_product<double>(a, xd, xc, yd, (int)B, adjoint, s);
+        st = run<double>(p, a, prec, xd, xc, yd, (int)B, adjoint, s, stage_ms);
     } else {
         ProductArgs<float> a = p->a32;
         a.B = (int)Bi;
-        e = run_product<float>(a, xd, xc, yd, (int)B, adjoint, s);
+        st = run<float>(p, a, prec, xd, xc, yd, (int)B, adjoint, s, stage_ms);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "product launch");
+    if (st != MLFMA_OK) return st;
     if (host) {
         if ((e = cudaMemcpyAsync(y, p->stage_y, ybytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return cuda_fail(e, "copy y to host");
@@ -406,6 +518,8 @@ mlfma_status mlfma_plan(const double *verts, int64_t nv, const int32_t *tris, in
             st = fail(MLFMA_ENOMEM, "host allocation failed during device setup");
         }
         if (st != MLFMA_OK) {
+            cudaDeviceSynchronize();
+            release_streams(p.get());
             p->mem.free_all();
             return st;
         }
@@ -445,6 +559,13 @@ mlfma_status mlfma_matvec_adjoint(mlfma_plan_t p, const void *x, int xc, void *y
 mlfma_status mlfma_matvec_host(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)
 {
     return product(p, x, xc, y, B, prec, stream, 0, true);
+}
+
+mlfma_status mlfma_profile_stages(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream,
+                                  double *stage_ms)
+{
+    if (!stage_ms) return fail(MLFMA_EINVAL, "stage_ms is NULL");
+    return product(p, x, xc, y, B, prec, stream, 0, false, stage_ms);
 }
 
 mlfma_status mlfma_sync(mlfma_plan_t p, void *stream)
@@ -572,9 +693,10 @@ mlfma_status mlfma_export(mlfma_plan_t p, int what, int level, void *dst, int64_
 void mlfma_destroy(mlfma_plan_t p)
 {
     if (!p) return;
-    if (p->on_device) {
+    if (p->on_device || p->cs.main) {
         DeviceGuard g(p->device);
         cudaDeviceSynchronize();
+        release_streams(p);
         p->mem.free_all();
     }
     delete p;

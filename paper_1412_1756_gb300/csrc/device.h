@@ -27,6 +27,8 @@ struct DevNear {
     const int64_t *strip_off = nullptr;  // [nleaf+1]
     const int32_t *col_ptr = nullptr;    // [nleaf+1]
     const int32_t *strip_col = nullptr;  // columns (leaf-order unknowns)
+    int max_cols = 0;                    // largest strip width
+    int max_rows = 0;                    // largest leaf box
 };
 
 // One far level's tables in arithmetic type R (complex values as R pairs).
@@ -34,6 +36,10 @@ template <class R>
 struct DevLevel {
     int nbox = 0, L = 0, nth = 0, nph = 0, K = 0, ntype = 0;
     const int32_t *il_ptr = nullptr, *il_src = nullptr, *il_type = nullptr;
+    int nparent = 0, max_grp = 0;        // translation grouped by parent (level l-1)
+    const int32_t *grp_ptr = nullptr, *grp_src = nullptr;
+    const int16_t *grp_ty = nullptr;     // [entries][8]
+    const int32_t *pchild_ptr = nullptr; // parent level's child ranges into this level
     const R *alpha = nullptr;            // [ntype][K][2]
     const int32_t *parent = nullptr;     // [nbox] into level l-1
     const int32_t *octant = nullptr;     // [nbox]
@@ -80,10 +86,43 @@ struct ProductArgs {
     DevLevel<R> lv[22];
 };
 
-// Runs y_user = Z x_user (or its adjoint) on stream s.  x_user / y_user in
-// the caller's layout ([N][Bu], complex or real x, complex y).
+// Stage numbering of the per-stage timer (level-indexed stages add l).
+enum {
+    STAGE_PREPARE = 0, STAGE_NEAR = 1, STAGE_RADIATE = 2, STAGE_UP = 3, STAGE_TRANSLATE = 25,
+    STAGE_DOWN = 47, STAGE_RECEIVE = 69, STAGE_FINALIZE = 70, STAGE_COUNT = 71
+};
+
+// Serial per-stage timing: an event recorded after every stage.
+struct StageClock {
+    cudaEvent_t start = nullptr;
+    cudaEvent_t ev[96] = {};
+    int stage[96] = {};
+    int n = 0;
+};
+
+// Streams and events of the concurrent core pass (near || far chain, and
+// each level's translation as soon as its outgoing field exists).
+struct CoreStreams {
+    cudaStream_t main = nullptr, far = nullptr, tr = nullptr;
+    cudaEvent_t ev[64] = {};
+};
+
+// Kernel attributes (dynamic shared memory); call before launching or capturing.
 template <class R>
-cudaError_t run_product(const ProductArgs<R> &a, const void *x_user, int x_complex, void *y_user, int Bu,
-                        int adjoint, cudaStream_t s);
+cudaError_t prime_kernels();
+
+// x (caller layout [N][Bu], real or complex) -> leaf-order real columns.
+template <class R>
+cudaError_t launch_prepare(const ProductArgs<R> &a, const void *x_user, int x_complex, int Bu, int adjoint,
+                           cudaStream_t s);
+// leaf-order complex columns -> y (caller layout [N][Bu]).
+template <class R>
+cudaError_t launch_finalize(const ProductArgs<R> &a, void *y_user, int x_complex, int Bu, int adjoint,
+                            cudaStream_t s);
+// near field and the whole far pass into a.yp.  With clk: everything on
+// cs.main in order, an event after each stage.  Without: concurrent
+// branches on the three streams, joined back into cs.main.
+template <class R>
+cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClock *clk);
 
 }  // namespace mlfma

@@ -495,6 +495,43 @@ std::string build_plan_host(PlanHost &P, const double *verts, int64_t nv, const 
             // neighbours that are not neighbours themselves
             if (Lv.il_ptr[b + 1] - Lv.il_ptr[b] > 189) return "interaction list longer than 189 (internal error)";
         }
+        // grouped form: sources shared by the children of one parent
+        {
+            const Level &Pa = P.lv[l - 1];
+            Lv.grp_ptr.assign(1, 0);
+            Lv.grp_src.clear();
+            Lv.grp_ty.clear();
+            Lv.max_grp = 0;
+            for (int pb = 0; pb < Pa.nbox(); ++pb) {
+                const int c0 = Pa.child_ptr[pb], nc = Pa.child_ptr[pb + 1] - c0;
+                neighbours(l - 1, pb, nbp);
+                for (int pn : nbp)
+                    for (int s = Pa.child_ptr[pn]; s < Pa.child_ptr[pn + 1]; ++s) {
+                        int64_t X, Y, Z;
+                        unmorton(Lv.code[s], X, Y, Z);
+                        int16_t ty[8];
+                        bool any = false;
+                        for (int c = 0; c < 8; ++c) {
+                            ty[c] = -1;
+                            if (c >= nc) continue;
+                            int64_t x, y, z;
+                            unmorton(Lv.code[c0 + c], x, y, z);
+                            int dx = (int)(x - X), dy = (int)(y - Y), dz = (int)(z - Z);
+                            if (std::abs(dx) <= 1 && std::abs(dy) <= 1 && std::abs(dz) <= 1) continue;
+                            int t = type_of[(dx + 3) * 49 + (dy + 3) * 7 + (dz + 3)];
+                            if (t < 0) return "grouped interaction list disagrees with the per-box list";
+                            ty[c] = (int16_t)t;
+                            any = true;
+                        }
+                        if (!any) continue;
+                        Lv.grp_src.push_back(s);
+                        for (int c = 0; c < 8; ++c) Lv.grp_ty.push_back(ty[c]);
+                    }
+                Lv.grp_ptr.push_back((int32_t)Lv.grp_src.size());
+                Lv.max_grp = std::max(Lv.max_grp, Lv.grp_ptr[pb + 1] - Lv.grp_ptr[pb]);
+            }
+            if (Lv.max_grp > 216) return "grouped source list longer than 216 (internal error)";
+        }
         translation_table(Lv, k);
     }
 

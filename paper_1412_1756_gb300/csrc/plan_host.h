@@ -42,6 +42,12 @@ struct Level {
     std::vector<int32_t> child_ptr; // [nbox+1] range in level l+1
     // translation (l >= 2)
     std::vector<int32_t> il_ptr, il_src, il_type;
+    // the same lists grouped by parent (level l-1): for parent P, entries
+    // grp_ptr[P] .. grp_ptr[P+1]-1 name a source box and, for each of P's
+    // children (slot 0..7 in child order), the translation type or -1
+    std::vector<int32_t> grp_ptr, grp_src;
+    std::vector<int16_t> grp_ty;    // [entries][8]
+    int max_grp = 0;
     std::vector<int32_t> type_off;  // [ntype][3]
     int ntype = 0;
     std::vector<cd> alpha;          // [ntype][K]

@@ -23,7 +23,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIM
 
 EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg_edges", "mlfma_matvec",
             "mlfma_matvec_adjoint", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
-            "mlfma_destroy", "mlfma_last_error"]
+            "mlfma_profile_stages", "mlfma_destroy", "mlfma_last_error"]
+STAGE_COUNT = 71
 
 
 class MlfmaError(RuntimeError):
@@ -74,6 +75,7 @@ def load(build_if_missing: bool = False):
     for f in ("mlfma_matvec", "mlfma_matvec_adjoint", "mlfma_matvec_host"):
         getattr(L, f).argtypes = [P, P, I, P, I64, I, P]
     L.mlfma_sync.argtypes = [P, P]
+    L.mlfma_profile_stages.argtypes = [P, P, I, P, I64, I, P, P]
     L.mlfma_plan_info.argtypes = [P, ctypes.POINTER(Info)]
     L.mlfma_export.argtypes = [P, I, I, P, I64, ctypes.POINTER(I64)]
     L.mlfma_destroy.argtypes = [P]
@@ -224,6 +226,22 @@ class MlfmaPlan:
         _check(self._lib.mlfma_matvec_host(self._h, _np_ptr(x2), xc, _np_ptr(y), B, prec,
                                            ctypes.c_void_p(stream or 0)))
         return y.reshape(self.n) if squeeze else y
+
+    def profile_stages(self, x, y=None, stream=None) -> dict:
+        """Serial per-stage device times (ms) of one product (measurement aid)."""
+        import torch
+        ms = np.zeros(STAGE_COUNT)
+        fn = lambda h, xp, xc, yp, B, prec, s: self._lib.mlfma_profile_stages(h, xp, xc, yp, B, prec, s, _np_ptr(ms))
+        self._product(fn, x, y, stream)
+        out = {"prepare": ms[0], "near": ms[1], "radiate": ms[2], "receive": ms[69], "finalize": ms[70]}
+        for l in range(22):
+            if ms[3 + l]:
+                out["up%d" % l] = ms[3 + l]
+            if ms[25 + l]:
+                out["translate%d" % l] = ms[25 + l]
+            if ms[47 + l]:
+                out["down%d" % l] = ms[47 + l]
+        return out
 
     def sync(self, stream=None):
         _check(self._lib.mlfma_sync(self._h, ctypes.c_void_p(stream or 0)))
