@@ -160,6 +160,38 @@ mlfma_status mlfma_matvec_host(mlfma_plan_t plan, const void *x, int x_is_comple
 mlfma_status mlfma_profile_stages(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
                                   int64_t B, int prec, void *stream, double *stage_ms);
 
+/*
+ * y = Z x without allocating anything.  The paper has no counterpart: this
+ * is a service for callers that cannot call cudaMalloc at the moment they
+ * need a product - code running while a CUDA stream capture is open on the
+ * thread (the runtime forbids allocation then), code whose device memory is
+ * entirely reserved by another allocator, and real-time loops that must not
+ * allocate.  It runs the same kernels as mlfma_matvec, in order on `stream`,
+ * but takes every per-call buffer (leaf-order columns, each level's outgoing
+ * and incoming fields) from one static device array of
+ * MLFMA_NOALLOC_SCRATCH_BYTES inside this library instead of the plan's own
+ * buffers, and captures no graph.  The caller still passes x and y, with
+ * the layouts and types of mlfma_matvec; the plan's tables must already
+ * exist (mlfma_plan allocates them once, earlier).
+ *
+ * - A product needing more scratch than the array holds (columns x fields
+ *   of all levels) is refused with MLFMA_EINVAL and a message giving the
+ *   bytes needed; so is B > max_batch.
+ * - The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture begins.
+ * - Every call, on every plan, shares the one array and leaves its contents
+ *   behind.  Nothing in it needs to start at zero: each pass writes every
+ *   scratch value before reading it.  Calls whose work overlaps on the GPU
+ *   (other streams, other threads, other plans) race on the array: order
+ *   them.
+ * - Every GPU that loads the library holds the array until the process exits.
+ * Errors: EINVAL, ECUDA.
+ */
+#define MLFMA_NOALLOC_SCRATCH_BYTES (32 * 1024 * 1024)
+mlfma_status mlfma_matvec_noalloc(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
+                                  int64_t B, int prec, void *stream);
+
 /* Wait for the plan's work on `stream` and report any pending device-side
  * error. */
 mlfma_status mlfma_sync(mlfma_plan_t plan, void *stream);

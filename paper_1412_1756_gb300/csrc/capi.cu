@@ -470,6 +470,26 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
 
 }  // namespace
 
+namespace mlfma {
+// Read-only view of a device plan's product arguments for entry points
+// defined in other translation units.
+bool plan_product_view(mlfma_plan_t p, int prec, ProductArgs<float> *a32, ProductArgs<double> *a64, int *device,
+                       int *max_batch, int64_t *n)
+{
+    if (!p || !p->on_device) return false;
+    if (prec == MLFMA_FP32 && !p->has32) return false;
+    if (prec == MLFMA_FP64 && !p->has64) return false;
+    if (prec == MLFMA_FP32 && a32) *a32 = p->a32;
+    if (prec == MLFMA_FP64 && a64) *a64 = p->a64;
+    *device = p->device;
+    *max_batch = p->opts.max_batch;
+    *n = p->host.N;
+    return true;
+}
+
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace mlfma
+
 extern "C" {
 
 mlfma_status mlfma_default_opts(mlfma_opts *o)

@@ -23,7 +23,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIM
 
 EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg_edges", "mlfma_matvec",
             "mlfma_matvec_adjoint", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
-            "mlfma_profile_stages", "mlfma_destroy", "mlfma_last_error"]
+            "mlfma_profile_stages", "mlfma_matvec_noalloc", "mlfma_destroy", "mlfma_last_error"]
 STAGE_COUNT = 71
 
 
@@ -72,7 +72,7 @@ def load(build_if_missing: bool = False):
                              ctypes.POINTER(P)]
     L.mlfma_num_unknowns.argtypes = [P, ctypes.POINTER(I64)]
     L.mlfma_rwg_edges.argtypes = [P, P, P]
-    for f in ("mlfma_matvec", "mlfma_matvec_adjoint", "mlfma_matvec_host"):
+    for f in ("mlfma_matvec", "mlfma_matvec_adjoint", "mlfma_matvec_host", "mlfma_matvec_noalloc"):
         getattr(L, f).argtypes = [P, P, I, P, I64, I, P]
     L.mlfma_sync.argtypes = [P, P]
     L.mlfma_profile_stages.argtypes = [P, P, I, P, I64, I, P, P]
