@@ -182,6 +182,19 @@ cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *ne
             if ((e = M.upload(cast(Lv.ph_up.coef), &D.phu_c)) != cudaSuccess) return e;
             if ((e = M.upload(cast(Lv.th_dn.coef), &D.thd_c)) != cudaSuccess) return e;
             if ((e = M.upload(cast(Lv.ph_dn.coef), &D.phd_c)) != cudaSuccess) return e;
+            auto pack = [](const Stencil &st) {
+                std::vector<Tap<R>> t(st.idx.size());
+                for (size_t i = 0; i < t.size(); ++i) {
+                    t[i].i = st.idx[i] | ((!st.refl.empty() && st.refl[i]) ? kTapRefl : 0);
+                    t[i].c = (R)st.coef[i];
+                }
+                return t;
+            };
+            if ((e = M.upload(pack(Lv.th_up), &D.thu)) != cudaSuccess) return e;
+            D.up_order = H.order;
+            if ((e = M.upload(pack(Lv.ph_up), &D.phu)) != cudaSuccess) return e;
+            if ((e = M.upload(pack(Lv.th_dn), &D.thd)) != cudaSuccess) return e;
+            if ((e = M.upload(pack(Lv.ph_dn), &D.phd)) != cudaSuccess) return e;
             const Level &C = H.lv[l + 1];
             scratch = std::max<int64_t>(scratch, (int64_t)C.nbox() * 2 * Lv.nth * C.nph * Bmax);
         }

@@ -31,6 +31,15 @@ struct DevNear {
     int max_rows = 0;                    // largest leaf box
 };
 
+// One stencil tap: source index (theta stencils: bit 30 set = take the
+// sample at phi + pi) and its coefficient.
+template <class R>
+struct Tap {
+    int32_t i;
+    R c;
+};
+constexpr int32_t kTapRefl = 1 << 30;
+
 // One far level's tables in arithmetic type R (complex values as R pairs).
 template <class R>
 struct DevLevel {
@@ -55,6 +64,8 @@ struct DevLevel {
     const R *thd_c = nullptr;
     const int32_t *phd_ptr = nullptr, *phd_idx = nullptr;
     const R *phd_c = nullptr;
+    const Tap<R> *thu = nullptr, *phu = nullptr, *thd = nullptr, *phd = nullptr;   // packed taps
+    int up_order = 0;           // taps per forward stencil row (the interpolation order)
     const R *wq = nullptr;               // [K] quadrature weight (leaf: times -k^2 eta / 4 pi)
     R *S = nullptr;                      // outgoing field [nbox][2][K][B]
     R *G = nullptr;                      // incoming field [nbox][2][K][B]

@@ -241,16 +241,17 @@ __global__ void __launch_bounds__(256) k_radiate(const int32_t *__restrict__ box
 // Eq. (8) sample by sample, grouped by parent: the children of one parent
 // draw on one candidate set (children of the parent's neighbours), so each
 // source field value is loaded once and applied to every child whose
-// interaction list holds it.  Each (sample q, column b) output is shared by
-// ES consecutive lanes that split the source list and meet in a shuffle
-// reduction (ES > 1 where outputs alone are too few to fill the GPU); all
-// children's accumulators live in registers.
-template <class R, int ES>
+// interaction list holds it.  A thread computes CB adjacent columns of one
+// sample (one alpha load feeds CB columns); ES consecutive lanes may split
+// the source list of one output and meet in a shuffle reduction (when a
+// level has too few outputs to fill the GPU).  All children's accumulators
+// live in registers.
+template <class R, int ES, int CB>
 __global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B)
 {
     using C = typename Cx<R>::T;
     __shared__ int s_src[216];
-    __shared__ int16_t s_ty[216 * 8];
+    __shared__ __align__(16) int16_t s_ty[216 * 8];
     const int P = blockIdx.x;
     const int e0 = lv.grp_ptr[P], ne = lv.grp_ptr[P + 1] - e0;
     const int m0 = lv.pchild_ptr[P], nc = lv.pchild_ptr[P + 1] - m0;
@@ -258,29 +259,42 @@ __global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B)
     for (int e = threadIdx.x; e < ne * 8; e += blockDim.x) s_ty[e] = lv.grp_ty[(int64_t)e0 * 8 + e];
     __syncthreads();
     const int K = lv.K;
+    const int BC = B / CB;                 // column groups (B is a multiple of CB)
     const int part = threadIdx.x % ES;
     const int t = blockIdx.y * (blockDim.x / ES) + threadIdx.x / ES;
-    const bool valid = t < K * B;
-    const int q = valid ? t / B : 0, b = valid ? t % B : 0;
+    const bool valid = t < K * BC;
+    const int q = valid ? t / BC : 0, b = valid ? (t % BC) * CB : 0;
     const C *S = reinterpret_cast<const C *>(lv.S);
     const C *alpha = reinterpret_cast<const C *>(lv.alpha) + q;
-    C acc[8][2];
+    C acc[8][2][CB];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c][0] = acc[c][1] = C{0, 0};
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int k = 0; k < CB; ++k) acc[c][0][k] = acc[c][1][k] = C{0, 0};
     const int64_t KB = (int64_t)K * B;
     const int64_t qb = (int64_t)q * B + b;
     if (valid) {
 #pragma unroll 2
         for (int e = part; e < ne; e += ES) {
             const int64_t base = (int64_t)s_src[e] * 2 * KB + qb;
-            const C s0 = S[base], s1 = S[base + KB];
+            C s0[CB], s1[CB];
+#pragma unroll
+            for (int k = 0; k < CB; ++k) {
+                s0[k] = S[base + k];
+                s1[k] = S[base + KB + k];
+            }
+            const int4 tyv = *reinterpret_cast<const int4 *>(&s_ty[e * 8]);
+            const int tw[4] = {tyv.x, tyv.y, tyv.z, tyv.w};
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const int ty = s_ty[e * 8 + c];
+                const int ty = (int)(int16_t)((tw[c >> 1] >> (16 * (c & 1))) & 0xffff);
                 if (ty >= 0) {
                     const C al = alpha[(int64_t)ty * K];
-                    cfma(acc[c][0], al, s0);
-                    cfma(acc[c][1], al, s1);
+#pragma unroll
+                    for (int k = 0; k < CB; ++k) {
+                        cfma(acc[c][0][k], al, s0[k]);
+                        cfma(acc[c][1][k], al, s1[k]);
+                    }
                 }
             }
         }
@@ -292,10 +306,12 @@ __global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B)
 #pragma unroll
             for (int off = ES / 2; off >= 1; off >>= 1)
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    acc[c][k].x += __shfl_xor_sync(0xffffffffu, acc[c][k].x, off);
-                    acc[c][k].y += __shfl_xor_sync(0xffffffffu, acc[c][k].y, off);
-                }
+                for (int m = 0; m < 2; ++m)
+#pragma unroll
+                    for (int k = 0; k < CB; ++k) {
+                        acc[c][m][k].x += __shfl_xor_sync(0xffffffffu, acc[c][m][k].x, off);
+                        acc[c][m][k].y += __shfl_xor_sync(0xffffffffu, acc[c][m][k].y, off);
+                    }
         }
     }
     if (!valid || part != 0) return;
@@ -304,124 +320,162 @@ __global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B)
     for (int c = 0; c < 8; ++c)
         if (c < nc) {
             const int64_t o = (int64_t)(m0 + c) * 2 * KB + qb;
-            G[o] = acc[c][0];
-            G[o + KB] = acc[c][1];
+#pragma unroll
+            for (int k = 0; k < CB; ++k) {
+                G[o + k] = acc[c][0][k];
+                G[o + KB + k] = acc[c][1][k];
+            }
         }
 }
 
 // ----------------------------------------------------------- upward ---
-// One CTA per (parent box, component, chunk of Bt columns): for each child,
-// its field -> shared memory, theta interpolation -> shared memory, phi
-// interpolation and phase shift accumulated in registers (MAXO outputs per
-// thread).
-template <class R, int MAXO>
-__global__ void k_up(DevLevel<R> P, DevLevel<R> Ch, int B, int Bt, int RS)
+// One CTA per (parent box, component, chunk of NB columns, band of parent
+// theta rows).  Threads are (slot, column) with the column fastest, so each
+// packed stencil tap is one broadcast load shared by the NB column lanes and
+// shared-memory accesses are conflict-free.  Forward stencils have exactly
+// PO taps per row (the interpolation order), fully unrolled.  Per child:
+// its field -> shared memory (the next child's field is prefetched into
+// registers meanwhile), theta interpolation of the band's rows -> shared
+// memory, phi interpolation and phase shift accumulated into the band's
+// outputs in shared memory; one store of the parent field at the end.
+template <class R, int NB, int PO>
+__global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B, int RS)
 {
     using C = typename Cx<R>::T;
+    constexpr int PF = 8;   // prefetch registers per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Kc = Ch.K, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph;
     const int p = blockIdx.x, comp = blockIdx.y;
-    const int nbc = (B + Bt - 1) / Bt;
-    const int bc = blockIdx.z % nbc, rs = blockIdx.z / nbc;
-    const int b0 = bc * Bt, nb = min(Bt, B - b0);
-    // this CTA's parent theta rows [t0, t1)
+    const int nbc = (B + NB - 1) / NB;
+    const int b0 = (blockIdx.z % nbc) * NB, rs = blockIdx.z / nbc;
     const int rows = (ntp + RS - 1) / RS, t0 = rs * rows, t1 = min(ntp, t0 + rows);
     if (t0 >= t1) return;
-    C *A = reinterpret_cast<C *>(smem_raw);          // [Kc][nb]
-    C *T = A + (size_t)Kc * Bt;                       // [t1-t0][nphc][nb]
+    const int bb = threadIdx.x % NB, slot = threadIdx.x / NB, nslot = blockDim.x / NB;
+    const bool bok = b0 + bb < B;
+    const int nT = (t1 - t0) * nphc, nO = (t1 - t0) * nphp;
+    C *A = reinterpret_cast<C *>(smem_raw);   // [Kc][NB]
+    C *T = A + (size_t)Kc * NB;                // [nT][NB]
+    C *O = T + (size_t)nT * NB;                // [nO][NB]
     const C *S = reinterpret_cast<const C *>(Ch.S);
     const C *shift = reinterpret_cast<const C *>(P.shift) + (int64_t)t0 * nphp;
-    C acc[MAXO];
+    const Tap<R> *thu = P.thu + (size_t)t0 * PO;
+    for (int o = slot; o < nO; o += nslot) O[o * NB + bb] = C{0, 0};
+    const int c0 = P.child_ptr[p], c1 = P.child_ptr[p + 1];
+    // rows q = slot + k * nslot of a child field; prefetch buffer for PF of them
+    C pre[PF];
+    auto fetch = [&](int c) {
+        const C *src = S + ((int64_t)c * 2 + comp) * Kc * B + b0 + bb;
 #pragma unroll
-    for (int k = 0; k < MAXO; ++k) acc[k] = C{0, 0};
-    const int Kp = (t1 - t0) * nphp;   // outputs of this CTA per column
-    const int nout = Kp * nb;
-    for (int c = P.child_ptr[p]; c < P.child_ptr[p + 1]; ++c) {
-        const C *src = S + ((int64_t)c * 2 + comp) * Kc * B + b0;
-        for (int e = threadIdx.x; e < Kc * nb; e += blockDim.x) A[e] = src[(int64_t)(e / nb) * B + e % nb];
+        for (int k = 0; k < PF; ++k) {
+            const int q = slot + k * nslot;
+            pre[k] = (bok && q < Kc) ? src[(int64_t)q * B] : C{0, 0};
+        }
+    };
+    fetch(c0);
+    for (int c = c0; c < c1; ++c) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const int q = slot + k * nslot;
+            if (q < Kc) A[q * NB + bb] = pre[k];
+        }
+        if (PF * nslot < Kc) {   // rows beyond the prefetch window
+            const C *src = S + ((int64_t)c * 2 + comp) * Kc * B + b0 + bb;
+            for (int q = slot + PF * nslot; q < Kc; q += nslot) A[q * NB + bb] = bok ? src[(int64_t)q * B] : C{0, 0};
+        }
         __syncthreads();
-        for (int e = threadIdx.x; e < (t1 - t0) * nphc * nb; e += blockDim.x) {
-            const int bb = e % nb, v = (e / nb) % nphc, tp = t0 + e / (nb * nphc);
+        if (c + 1 < c1) fetch(c + 1);
+        for (int r = slot; r < nT; r += nslot) {
+            const int tr = r / nphc, v = r - tr * nphc;
+            const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
+            const Tap<R> *tp = thu + tr * PO;
             C s{0, 0};
-            for (int f = P.thu_ptr[tp]; f < P.thu_ptr[tp + 1]; ++f) {
-                const int vv = P.thu_refl[f] ? (v + hc) % nphc : v;
-                rfma(s, P.thu_c[f], A[(P.thu_idx[f] * nphc + vv) * nb + bb]);
+#pragma unroll
+            for (int f = 0; f < PO; ++f) {
+                const Tap<R> tap = tp[f];
+                const int j = tap.i & (kTapRefl - 1);
+                rfma(s, tap.c, A[(j * nphc + ((tap.i & kTapRefl) ? vs : v)) * NB + bb]);
             }
-            T[e] = s;
+            T[r * NB + bb] = s;
         }
         __syncthreads();
         const C *sh = shift + (int64_t)Ch.octant[c] * P.K;
+        for (int o = slot; o < nO; o += nslot) {
+            const int tr = o / nphp, u = o - tr * nphp;
+            const C *trow = T + tr * nphc * NB + bb;
+            const Tap<R> *up = P.phu + u * PO;
+            C s{0, 0};
 #pragma unroll
-        for (int k = 0; k < MAXO; ++k) {
-            const int o = threadIdx.x + k * blockDim.x;
-            if (o < nout) {
-                const int q = o / nb, bb = o % nb;
-                const int tp = q / nphp, u = q % nphp;   // tp relative to t0
-                C s{0, 0};
-                for (int f = P.phu_ptr[u]; f < P.phu_ptr[u + 1]; ++f)
-                    rfma(s, P.phu_c[f], T[(tp * nphc + P.phu_idx[f]) * nb + bb]);
-                cfma(acc[k], sh[q], s);
+            for (int f = 0; f < PO; ++f) {
+                const Tap<R> tap = up[f];
+                rfma(s, tap.c, trow[tap.i * NB]);
             }
+            cfma(O[o * NB + bb], sh[o], s);
         }
         __syncthreads();
     }
-    C *dst = reinterpret_cast<C *>(P.S) + (((int64_t)p * 2 + comp) * P.K + (int64_t)t0 * nphp) * B + b0;
-#pragma unroll
-    for (int k = 0; k < MAXO; ++k) {
-        const int o = threadIdx.x + k * blockDim.x;
-        if (o < nout) dst[(int64_t)(o / nb) * B + o % nb] = acc[k];
-    }
+    if (!bok) return;
+    C *dst = reinterpret_cast<C *>(P.S) + (((int64_t)p * 2 + comp) * P.K + (int64_t)t0 * nphp) * B + b0 + bb;
+    for (int o = slot; o < nO; o += nslot) dst[(int64_t)o * B] = O[o * NB + bb];
 }
 
 // --------------------------------------------------------- downward ---
-// One CTA per (child box, component, chunk of Bt columns): parent field
+// One CTA per (child box, component, chunk of NB columns): parent field
 // times the conjugate shift -> shared memory, phi anterpolation -> shared
 // memory, theta anterpolation added into the child's incoming field.
-template <class R>
-__global__ void k_down(DevLevel<R> P, DevLevel<R> Ch, int B, int Bt)
+template <class R, int NB>
+__global__ void __launch_bounds__(256) k_down(DevLevel<R> P, DevLevel<R> Ch, int B)
 {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Kc = Ch.K, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph, Kp = P.K;
     const int c = blockIdx.x, comp = blockIdx.y;
-    const int b0 = blockIdx.z * Bt, nb = min(Bt, B - b0);
-    C *H = reinterpret_cast<C *>(smem_raw);          // [Kp][nb]
-    C *U = H + (size_t)Kp * Bt;                       // [ntp][nphc][nb]
+    const int b0 = blockIdx.z * NB;
+    const int bb = threadIdx.x % NB, slot = threadIdx.x / NB, nslot = blockDim.x / NB;
+    const bool bok = b0 + bb < B;
+    C *H = reinterpret_cast<C *>(smem_raw);   // [Kp][NB]
+    C *U = H + (size_t)Kp * NB;                // [ntp * nphc][NB]
     const int par = Ch.parent[c];
-    const C *g = reinterpret_cast<const C *>(P.G) + ((int64_t)par * 2 + comp) * Kp * B + b0;
+    const C *g = reinterpret_cast<const C *>(P.G) + ((int64_t)par * 2 + comp) * Kp * B + b0 + bb;
     const C *sh = reinterpret_cast<const C *>(P.shift) + (int64_t)Ch.octant[c] * Kp;
-    for (int e = threadIdx.x; e < Kp * nb; e += blockDim.x) {
-        const int q = e / nb;
+    for (int q = slot; q < Kp; q += nslot) {
         C h{0, 0};
-        cfmac(h, sh[q], g[(int64_t)q * B + e % nb]);
-        H[e] = h;
+        if (bok) cfmac(h, sh[q], g[(int64_t)q * B]);
+        H[q * NB + bb] = h;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < ntp * nphc * nb; e += blockDim.x) {
-        const int bb = e % nb, v = (e / nb) % nphc, tp = e / (nb * nphc);
+    for (int r = slot; r < ntp * nphc; r += nslot) {
+        const int tp = r / nphc, v = r - tp * nphc;
+        const C *hrow = H + tp * nphp * NB + bb;
         C s{0, 0};
-        for (int f = P.phd_ptr[v]; f < P.phd_ptr[v + 1]; ++f) rfma(s, P.phd_c[f], H[(tp * nphp + P.phd_idx[f]) * nb + bb]);
-        U[e] = s;
+#pragma unroll 4
+        for (int f = P.phd_ptr[v]; f < P.phd_ptr[v + 1]; ++f) {
+            const Tap<R> tap = P.phd[f];
+            rfma(s, tap.c, hrow[tap.i * NB]);
+        }
+        U[r * NB + bb] = s;
     }
     __syncthreads();
-    C *dst = reinterpret_cast<C *>(Ch.G) + ((int64_t)c * 2 + comp) * Kc * B + b0;
-    for (int e = threadIdx.x; e < Kc * nb; e += blockDim.x) {
-        const int bb = e % nb, q = e / nb;
-        const int j = q / nphc, v = q % nphc;
-        C s = dst[(int64_t)q * B + bb];
+    if (!bok) return;
+    C *dst = reinterpret_cast<C *>(Ch.G) + ((int64_t)c * 2 + comp) * Kc * B + b0 + bb;
+    for (int q = slot; q < Kc; q += nslot) {
+        const int j = q / nphc, v = q - j * nphc;
+        const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
+        C s = dst[(int64_t)q * B];
+#pragma unroll 4
         for (int f = P.thd_ptr[j]; f < P.thd_ptr[j + 1]; ++f) {
-            const int vv = P.thd_refl[f] ? (v + hc) % nphc : v;
-            rfma(s, P.thd_c[f], U[(P.thd_idx[f] * nphc + vv) * nb + bb]);
+            const Tap<R> tap = P.thd[f];
+            const int t = tap.i & (kTapRefl - 1);
+            rfma(s, tap.c, U[(t * nphc + ((tap.i & kTapRefl) ? vs : v)) * NB + bb]);
         }
-        dst[(int64_t)q * B + bb] = s;
+        dst[(int64_t)q * B] = s;
     }
 }
 
 // ------------------------------------------------------------ receive ---
-// y_i += sum_q wq_q conj(V_s,mi(q)) . G_m(q).  One CTA per (leaf box, chunk
-// of LB columns) with the box's G block in shared memory; one warp per
-// unknown at a time, lanes split into LB column lanes x 32/LB sample lanes,
-// reduced with shuffles.
+// y_i += sum_q wq_q conj(V_s,mi(q)) . G_m(q).
+// Few columns: one CTA per (leaf box, chunk of LB columns) with the box's G
+// block in shared memory; one warp per unknown at a time, lanes split into
+// LB column lanes x 32/LB sample lanes, reduced with shuffles.
 template <class R, int LB>
 __global__ void __launch_bounds__(256) k_receive(const int32_t *__restrict__ box_ptr,
                                                  const typename Cx<R>::T4 *__restrict__ V4, DevLevel<R> lf,
@@ -448,6 +502,7 @@ __global__ void __launch_bounds__(256) k_receive(const int32_t *__restrict__ box
     for (int i = i0 + warp; i < i1; i += nwarp) {
         const C4 *v = V4 + (int64_t)i * K;
         C acc{0, 0};
+#pragma unroll 4
         for (int q = lq; q < K; q += LQ) {
             const C4 vq = v[q];
             C t{0, 0};
@@ -465,6 +520,133 @@ __global__ void __launch_bounds__(256) k_receive(const int32_t *__restrict__ box
             y.x += acc.x;
             y.y += acc.y;
             yp[(int64_t)i * B + b0 + lb] = y;
+        }
+    }
+}
+
+// Many columns: one CTA per (leaf box, chunk of NB columns), samples in
+// tiles of QT: the tile of G and of every unknown's patterns go to shared
+// memory; thread (row group, column) accumulates the rows i = group + k *
+// groups of its column in registers.
+template <class R, int NB, int MAXR>
+__global__ void __launch_bounds__(256) k_receive_tiled(const int32_t *__restrict__ box_ptr,
+                                                       const typename Cx<R>::T4 *__restrict__ V4, DevLevel<R> lf,
+                                                       typename Cx<R>::T *__restrict__ yp, int B)
+{
+    using C = typename Cx<R>::T;
+    using C4 = typename Cx<R>::T4;
+    constexpr int QT = 16;
+    constexpr int NG = 256 / NB;          // row groups
+    constexpr int VP = QT + 1;            // padded row pitch of the pattern tile
+    __shared__ C Gs[2 * QT * NB];
+    __shared__ R Ws[QT];
+    __shared__ C4 Vs[NG * MAXR * VP];
+    const int K = lf.K;
+    const int box = blockIdx.x;
+    const int b0 = blockIdx.y * NB;
+    const int bb = threadIdx.x % NB, grp = threadIdx.x / NB;
+    const bool bok = b0 + bb < B;
+    const int i0 = box_ptr[box], nrows = box_ptr[box + 1] - i0;
+    const C *G = reinterpret_cast<const C *>(lf.G) + (int64_t)box * 2 * K * B + b0;
+    for (int r0 = 0; r0 < nrows; r0 += NG * MAXR) {
+        const int nr = min(NG * MAXR, nrows - r0);
+        C acc[MAXR];
+#pragma unroll
+        for (int k = 0; k < MAXR; ++k) acc[k] = C{0, 0};
+        for (int q0 = 0; q0 < K; q0 += QT) {
+            const int nq = min(QT, K - q0);
+            for (int e = threadIdx.x; e < 2 * QT * NB; e += blockDim.x) {
+                const int b = e % NB, q = (e / NB) % QT, cmp = e / (NB * QT);
+                Gs[e] = (q < nq && b0 + b < B) ? G[((int64_t)cmp * K + q0 + q) * B + b] : C{0, 0};
+            }
+            for (int e = threadIdx.x; e < nr * QT; e += blockDim.x) {
+                const int r = e / QT, q = e % QT;
+                Vs[r * VP + q] = q < nq ? V4[(int64_t)(i0 + r0 + r) * K + q0 + q] : C4{0, 0, 0, 0};
+            }
+            if (threadIdx.x < QT) Ws[threadIdx.x] = threadIdx.x < nq ? lf.wq[q0 + threadIdx.x] : R(0);
+            __syncthreads();
+#pragma unroll 4
+            for (int q = 0; q < QT; ++q) {
+                const C g0 = Gs[q * NB + bb], g1 = Gs[(QT + q) * NB + bb];
+                const R w = Ws[q];
+#pragma unroll
+                for (int k = 0; k < MAXR; ++k) {
+                    const int r = grp + k * NG;
+                    if (r < nr) {
+                        const C4 v = Vs[r * VP + q];
+                        C t{0, 0};
+                        cfmac(t, C{v.x, v.y}, g0);
+                        cfmac(t, C{v.z, v.w}, g1);
+                        rfma(acc[k], w, t);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (bok) {
+#pragma unroll
+            for (int k = 0; k < MAXR; ++k) {
+                const int r = grp + k * NG;
+                if (r < nr) {
+                    C *yv = yp + (int64_t)(i0 + r0 + r) * B + b0 + bb;
+                    C y = *yv;
+                    y.x += acc[k].x;
+                    y.y += acc[k].y;
+                    *yv = y;
+                }
+            }
+        }
+    }
+}
+
+// Radiation, many columns: thread (sample group, column) with QB samples in
+// registers; x block of the box in shared memory.
+template <class R, int NB, int QB>
+__global__ void __launch_bounds__(256) k_radiate_tiled(const int32_t *__restrict__ box_ptr,
+                                                       const typename Cx<R>::T4 *__restrict__ V4,
+                                                       const R *__restrict__ xp, typename Cx<R>::T *__restrict__ S,
+                                                       int K, int B)
+{
+    using C = typename Cx<R>::T;
+    using C4 = typename Cx<R>::T4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *xs = reinterpret_cast<R *>(smem_raw);   // [nj][NB]
+    constexpr int NS = 256 / NB;
+    const int box = blockIdx.x;
+    const int b0 = blockIdx.y * NB;
+    const int bb = threadIdx.x % NB, slot = threadIdx.x / NB;
+    const int j0 = box_ptr[box], nj = box_ptr[box + 1] - j0;
+    for (int e = threadIdx.x; e < nj * NB; e += blockDim.x) {
+        const int b = e % NB;
+        xs[e] = b0 + b < B ? xp[(int64_t)(j0 + e / NB) * B + b0 + b] : R(0);
+    }
+    __syncthreads();
+    const bool bok = b0 + bb < B;
+    for (int qs = slot * QB; qs < K; qs += NS * QB) {
+        C a0[QB], a1[QB];
+#pragma unroll
+        for (int k = 0; k < QB; ++k) a0[k] = a1[k] = C{0, 0};
+        const C4 *vj = V4 + (int64_t)j0 * K + qs;
+        for (int j = 0; j < nj; ++j) {
+            const R xv = xs[j * NB + bb];
+#pragma unroll
+            for (int k = 0; k < QB; ++k) {
+                if (qs + k < K) {
+                    const C4 v = vj[(int64_t)j * K + k];
+                    a0[k].x = fma(v.x, xv, a0[k].x);
+                    a0[k].y = fma(v.y, xv, a0[k].y);
+                    a1[k].x = fma(v.z, xv, a1[k].x);
+                    a1[k].y = fma(v.w, xv, a1[k].y);
+                }
+            }
+        }
+        if (bok) {
+#pragma unroll
+            for (int k = 0; k < QB; ++k)
+                if (qs + k < K) {
+                    S[((int64_t)(box * 2 + 0) * K + qs + k) * B + b0 + bb] = a0[k];
+                    S[((int64_t)(box * 2 + 1) * K + qs + k) * B + b0 + bb] = a1[k];
+                }
         }
     }
 }
@@ -496,12 +678,29 @@ cudaError_t launch_near(const ProductArgs<R> &a, cudaStream_t s)
     return launch_near_bt<R, 16>(a, s);
 }
 
+template <class R, int NB, int QB>
+cudaError_t launch_radiate_tiled(const ProductArgs<R> &a, cudaStream_t s)
+{
+    using C = typename Cx<R>::T;
+    using C4 = typename Cx<R>::T4;
+    const DevLevel<R> &Lf = a.lv[a.leaf];
+    const size_t smem = (size_t)a.nr.max_rows * NB * sizeof(R);
+    if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
+    dim3 grid(Lf.nbox, (a.B + NB - 1) / NB);
+    k_radiate_tiled<R, NB, QB><<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), a.xp,
+                                                       reinterpret_cast<C *>(Lf.S), Lf.K, a.B);
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t launch_radiate(const ProductArgs<R> &a, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
     const DevLevel<R> &Lf = a.lv[a.leaf];
+    if (a.B >= 32 && (size_t)a.nr.max_rows * 32 * sizeof(R) <= (size_t)kSmemCap) return launch_radiate_tiled<R, 32, 4>(a, s);
+    if (a.B >= 16 && (size_t)a.nr.max_rows * 16 * sizeof(R) <= (size_t)kSmemCap) return launch_radiate_tiled<R, 16, 4>(a, s);
+    if (a.B >= 8 && (size_t)a.nr.max_rows * 8 * sizeof(R) <= (size_t)kSmemCap) return launch_radiate_tiled<R, 8, 4>(a, s);
     int Bt = std::min(a.B, 32);
     while (Bt > 1 && (size_t)a.nr.max_rows * Bt * sizeof(R) > (size_t)kSmemCap) Bt /= 2;
     const size_t smem = (size_t)a.nr.max_rows * Bt * sizeof(R);
@@ -524,81 +723,126 @@ cudaError_t launch_receive_lb(const ProductArgs<R> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <class R, int NB>
+cudaError_t launch_receive_tiled(const ProductArgs<R> &a, cudaStream_t s)
+{
+    using C = typename Cx<R>::T;
+    using C4 = typename Cx<R>::T4;
+    const DevLevel<R> &Lf = a.lv[a.leaf];
+    dim3 grid(Lf.nbox, (a.B + NB - 1) / NB);
+    k_receive_tiled<R, NB, NB / 4><<<grid, 256, 0, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), Lf,
+                                                        reinterpret_cast<C *>(a.yp), a.B);
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t launch_receive(const ProductArgs<R> &a, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
+    if (a.B >= 32 && sizeof(R) == 4) return launch_receive_tiled<R, 32>(a, s);
+    if (a.B >= 16) return launch_receive_tiled<R, 16>(a, s);
+    if (a.B >= 8) return launch_receive_tiled<R, 8>(a, s);
     const int K = a.lv[a.leaf].K;
     int lb = 1;
-    while (lb < a.B && lb < 32) lb *= 2;
+    while (lb < a.B) lb *= 2;
     while (lb > 1 && (size_t)2 * K * lb * sizeof(C) > (size_t)kSmemCap) lb /= 2;
     switch (lb) {
     case 1: return launch_receive_lb<R, 1>(a, s);
     case 2: return launch_receive_lb<R, 2>(a, s);
-    case 4: return launch_receive_lb<R, 4>(a, s);
-    case 8: return launch_receive_lb<R, 8>(a, s);
-    case 16: return launch_receive_lb<R, 16>(a, s);
-    default: return launch_receive_lb<R, 32>(a, s);
+    default: return launch_receive_lb<R, 4>(a, s);
     }
 }
 
-template <class R, int MAXO>
-cudaError_t launch_up_t(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bt, int RS, int nt, size_t smem,
-                        cudaStream_t s)
+// ---- upward: columns per CTA NB, parent theta rows split RS ways
+template <class R, int NB, int PO>
+cudaError_t launch_up_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, cudaStream_t s)
 {
-    dim3 grid(P.nbox, 2, ((B + Bt - 1) / Bt) * RS);
-    k_up<R, MAXO><<<grid, nt, smem, s>>>(P, Ch, B, Bt, RS);
+    using C = typename Cx<R>::T;
+    auto smem_of = [&](int rs) {
+        const int rows = (P.nth + rs - 1) / rs;
+        return ((size_t)Ch.K + (size_t)rows * (Ch.nph + P.nph)) * NB * sizeof(C);
+    };
+    int RS = 1;
+    while (RS < P.nth && smem_of(RS) > (size_t)(64 * 1024)) ++RS;
+    if (smem_of(RS) > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
+    const int64_t ctas = (int64_t)P.nbox * 2 * ((B + NB - 1) / NB);
+    while (ctas * RS < 8 * 152 && 2 * RS <= P.nth / 2) RS *= 2;
+    dim3 grid(P.nbox, 2, ((B + NB - 1) / NB) * RS);
+    k_up<R, NB, PO><<<grid, 256, smem_of(RS), s>>>(P, Ch, B, RS);
     return cudaGetLastError();
 }
 
-// Column chunk Bt bounded by shared memory and by 16 register outputs per
-// thread; the parent's theta rows split RS ways until there are enough CTAs.
+template <class R, int NB>
+cudaError_t launch_up_po(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int order, cudaStream_t s)
+{
+    switch (order) {
+    case 4: return launch_up_nb<R, NB, 4>(P, Ch, B, s);
+    case 6: return launch_up_nb<R, NB, 6>(P, Ch, B, s);
+    case 8: return launch_up_nb<R, NB, 8>(P, Ch, B, s);
+    case 10: return launch_up_nb<R, NB, 10>(P, Ch, B, s);
+    case 12: return launch_up_nb<R, NB, 12>(P, Ch, B, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class R>
+int column_chunk(int B, size_t per_col_bytes)
+{
+    int nb = 1;
+    while (nb * 2 <= std::min(B, 16)) nb *= 2;
+    while (nb > 1 && per_col_bytes * nb > (size_t)(64 * 1024)) nb /= 2;
+    return nb;
+}
+
 template <class R>
 cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
-    const int nt = P.K > 4096 ? 512 : 256;
-    int Bt = std::min(B, 16), RS = 1;
-    auto fits = [&](int bt, int rs) {
-        const int rows = (P.nth + rs - 1) / rs;
-        const size_t smem = ((size_t)Ch.K + (size_t)rows * Ch.nph) * bt * sizeof(C);
-        return smem <= (size_t)kSmemCap && (rows * P.nph * bt + nt - 1) / nt <= 16;
-    };
-    while (Bt > 1 && !fits(Bt, RS)) --Bt;
-    while (!fits(Bt, RS) && RS < P.nth) ++RS;
-    if (!fits(Bt, RS)) return cudaErrorInvalidConfiguration;
-    const int64_t ctas = (int64_t)P.nbox * 2 * ((B + Bt - 1) / Bt);
-    while (ctas * RS < 4 * 152 && RS * 2 <= P.nth / 2) RS *= 2;
-    const int rows = (P.nth + RS - 1) / RS;
-    const size_t smem = ((size_t)Ch.K + (size_t)rows * Ch.nph) * Bt * sizeof(C);
-    const int no = (rows * P.nph * Bt + nt - 1) / nt;
-    if (no <= 4) return launch_up_t<R, 4>(P, Ch, B, Bt, RS, nt, smem, s);
-    if (no <= 8) return launch_up_t<R, 8>(P, Ch, B, Bt, RS, nt, smem, s);
-    return launch_up_t<R, 16>(P, Ch, B, Bt, RS, nt, smem, s);
+    const int order = P.up_order;
+    switch (column_chunk<R>(B, ((size_t)Ch.K + (size_t)P.nth * (Ch.nph + P.nph)) * sizeof(C))) {
+    case 1: return launch_up_po<R, 1>(P, Ch, B, order, s);
+    case 2: return launch_up_po<R, 2>(P, Ch, B, order, s);
+    case 4: return launch_up_po<R, 4>(P, Ch, B, order, s);
+    case 8: return launch_up_po<R, 8>(P, Ch, B, order, s);
+    default: return launch_up_po<R, 16>(P, Ch, B, order, s);
+    }
 }
 
-template <class R, int ES>
+template <class R, int ES, int CB>
 cudaError_t launch_translate_es(const DevLevel<R> &Lv, int B, cudaStream_t s)
 {
-    dim3 grid(Lv.nparent, (Lv.K * B + 128 / ES - 1) / (128 / ES));
-    k_translate<R, ES><<<grid, 128, 0, s>>>(Lv, B);
+    const int outs = Lv.K * (B / CB);
+    dim3 grid(Lv.nparent, (outs + 128 / ES - 1) / (128 / ES));
+    k_translate<R, ES, CB><<<grid, 128, 0, s>>>(Lv, B);
     return cudaGetLastError();
 }
 
-// Lanes per output grow until the level offers ~16 warps per SM.
+// Two columns per thread when B is even and there is enough parallelism;
+// lanes per output grow until the level offers ~16 warps per SM.
 template <class R>
 cudaError_t launch_translate(const DevLevel<R> &Lv, int B, cudaStream_t s)
 {
+    const bool pair = (B % 2 == 0) && (int64_t)Lv.nparent * ((Lv.K * (B / 2) + 31) / 32) >= 16 * 152;
+    if (pair) return launch_translate_es<R, 1, 2>(Lv, B, s);
     const int64_t warps1 = (int64_t)Lv.nparent * ((Lv.K * B + 31) / 32);
     int es = 1;
     while (es < 16 && warps1 * es < 16 * 152 && es * 2 <= std::max(1, Lv.max_grp / 4)) es *= 2;
     switch (es) {
-    case 1: return launch_translate_es<R, 1>(Lv, B, s);
-    case 2: return launch_translate_es<R, 2>(Lv, B, s);
-    case 4: return launch_translate_es<R, 4>(Lv, B, s);
-    case 8: return launch_translate_es<R, 8>(Lv, B, s);
-    default: return launch_translate_es<R, 16>(Lv, B, s);
+    case 1: return launch_translate_es<R, 1, 1>(Lv, B, s);
+    case 2: return launch_translate_es<R, 2, 1>(Lv, B, s);
+    case 4: return launch_translate_es<R, 4, 1>(Lv, B, s);
+    case 8: return launch_translate_es<R, 8, 1>(Lv, B, s);
+    default: return launch_translate_es<R, 16, 1>(Lv, B, s);
     }
+}
+
+// ---- downward: columns per CTA NB
+template <class R, int NB>
+cudaError_t launch_down_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, size_t smem, cudaStream_t s)
+{
+    dim3 grid(Ch.nbox, 2, (B + NB - 1) / NB);
+    k_down<R, NB><<<grid, 256, smem, s>>>(P, Ch, B);
+    return cudaGetLastError();
 }
 
 template <class R>
@@ -606,24 +850,18 @@ cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, cuda
 {
     using C = typename Cx<R>::T;
     const size_t per_col = ((size_t)P.K + (size_t)P.nth * Ch.nph) * sizeof(C);
-    int Bt = std::min(B, 16);
-    while (Bt > 1 && per_col * Bt > (size_t)kSmemCap) --Bt;
-    if (per_col * Bt > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
-    dim3 grid(Ch.nbox, 2, (B + Bt - 1) / Bt);
-    k_down<R><<<grid, 256, per_col * Bt, s>>>(P, Ch, B, Bt);
-    return cudaGetLastError();
+    const int nb = column_chunk<R>(B, per_col);
+    const size_t smem = per_col * nb;
+    if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
+    switch (nb) {
+    case 1: return launch_down_nb<R, 1>(P, Ch, B, smem, s);
+    case 2: return launch_down_nb<R, 2>(P, Ch, B, smem, s);
+    case 4: return launch_down_nb<R, 4>(P, Ch, B, smem, s);
+    case 8: return launch_down_nb<R, 8>(P, Ch, B, smem, s);
+    default: return launch_down_nb<R, 16>(P, Ch, B, smem, s);
+    }
 }
 
-}  // namespace
-
-namespace {
-inline cudaError_t tick(StageClock *clk, int stage, cudaStream_t s)
-{
-    if (!clk) return cudaSuccess;
-    if (clk->n >= 96) return cudaErrorInvalidValue;
-    clk->stage[clk->n] = stage;
-    return cudaEventRecord(clk->ev[clk->n++], s);
-}
 }  // namespace
 
 // Raise the dynamic shared-memory limit of every kernel that stages data,
@@ -633,13 +871,15 @@ cudaError_t prime_kernels()
 {
     cudaError_t e;
 #define ALLOW(k) do { if ((e = allow_smem(k)) != cudaSuccess) return e; } while (0)
+#define ALLOW_UP(NB) ALLOW((k_up<R, NB, 4>)); ALLOW((k_up<R, NB, 6>)); ALLOW((k_up<R, NB, 8>)); \
+    ALLOW((k_up<R, NB, 10>)); ALLOW((k_up<R, NB, 12>)); ALLOW((k_down<R, NB>))
     ALLOW((k_near<R, 1, true>)); ALLOW((k_near<R, 2, true>)); ALLOW((k_near<R, 4, true>));
     ALLOW((k_near<R, 8, true>)); ALLOW((k_near<R, 16, true>));
     ALLOW(k_radiate<R>);
+    ALLOW((k_radiate_tiled<R, 8, 4>)); ALLOW((k_radiate_tiled<R, 16, 4>)); ALLOW((k_radiate_tiled<R, 32, 4>));
     ALLOW((k_receive<R, 1>)); ALLOW((k_receive<R, 2>)); ALLOW((k_receive<R, 4>));
-    ALLOW((k_receive<R, 8>)); ALLOW((k_receive<R, 16>)); ALLOW((k_receive<R, 32>));
-    ALLOW((k_up<R, 4>)); ALLOW((k_up<R, 8>)); ALLOW((k_up<R, 16>));
-    ALLOW(k_down<R>);
+    ALLOW_UP(1); ALLOW_UP(2); ALLOW_UP(4); ALLOW_UP(8); ALLOW_UP(16);
+#undef ALLOW_UP
 #undef ALLOW
     return cudaSuccess;
 }
@@ -662,6 +902,16 @@ cudaError_t launch_finalize(const ProductArgs<R> &a, void *y_user, int x_complex
                                                             a.perm, a.n, adjoint, static_cast<C *>(y_user));
     return cudaGetLastError();
 }
+
+namespace {
+inline cudaError_t tick(StageClock *clk, int stage, cudaStream_t s)
+{
+    if (!clk) return cudaSuccess;
+    if (clk->n >= 96) return cudaErrorInvalidValue;
+    clk->stage[clk->n] = stage;
+    return cudaEventRecord(clk->ev[clk->n++], s);
+}
+}  // namespace
 
 template <class R>
 cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClock *clk)
