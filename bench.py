@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stages-only", action="store_true",
+                    help="build the plan and run one serial per-stage pass (for profilers), print stage times")
     return ap.parse_args()
 
 
@@ -115,6 +117,45 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+def reduce_max(x, dist, device):
+    """Max over ranks of a per-rank scalar (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(columns, steps, seconds_max, world):
+    """Whole-job rate of N independent replicas: every rank processes the same
+    number of columns; the job takes the slowest rank's time."""
+    return world * columns * steps / seconds_max
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def kernel_digest():
+    """Digest of the product kernels' source: a DRAM-traffic figure taken by
+    ncu is reported only while the kernels are the ones it was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("product_kernels.cu", "device.h"):
+        with open(os.path.join(ROOT, "paper_1412_1756_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes (read + write) per launch measured by ncu at this workload and
+# B = 64: {(stage, kernel source digest): bytes}.  Summaries in profiles/.
+NCU_TRAFFIC = {
+    ("translate4", "d0bad89bd907ec1b"): 193_311_488 + 155_109_120,
+}
 
 
 def algorithmic(info, B, stage, rsz=4):
@@ -228,6 +269,10 @@ def main():
     v, t = wl.mesh()
     B = a.batch
     plan = MlfmaPlan(v, t, wl.k, wl.levels, wl.digits, max_batch=max(B, 1), device=local)
+    if a.stages_only:
+        xs = torch.from_numpy(workloads.rhs(plan.n, B, wl.seed)).to("cuda", torch.float32)
+        print(json.dumps({"stage_ms": plan.profile_stages(xs)}))
+        return
     info = plan.info()
     n = plan.n
     x_np = workloads.rhs(n, B, wl.seed)
@@ -253,22 +298,17 @@ def main():
             ev[s][1].record(stream)
         torch.cuda.synchronize()
         ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-        if dist:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
-        return ms
+        return reduce_max(ms, dist, "cuda")
 
     # --- mixed precision, batched (the headline)
     with ClockSampler(local) as clk:
         ms = timed(lambda: plan.matvec(x32, y32), a.steps, a.warmup)
     clocks = clk.summary()
-    value_rank = B * a.steps / (ms / 1e3)
-    value = value_rank * world
+    value = replica_rate(B, a.steps, ms / 1e3, world)
     # --- plain FP64 single vector on the same GPU and input column
     steps64 = max(3, a.steps)
     ms64 = timed(lambda: plan.matvec(x64_1, y64), steps64, a.warmup)
-    fp64_rate = steps64 / (ms64 / 1e3)
+    fp64_rate = replica_rate(1, steps64, ms64 / 1e3, 1)
 
     # --- error against the FP64 oracle on the timed inputs (sampled rows)
     y32_np = y32.cpu().numpy()
@@ -288,15 +328,29 @@ def main():
     hbm_peak, peak_src = peaks()
     abytes, aflops = algorithmic(info, B, dom)
     dom_ms = stages[dom]
-    roof = {"kernel": dom, "bound": "hbm", "achieved": abytes / (dom_ms / 1e3) / 1e9, "peak": hbm_peak,
-            "unit": "GB/s", "frac": abytes / (dom_ms / 1e3) / 1e9 / hbm_peak, "traffic": None,
-            "algorithmic_bytes": abytes, "ms": dom_ms, "peak_source": peak_src,
-            "timing": "CUDA events around the kernel in a serial pass on the launching stream"}
-    hbm_stages = {}
+    traffic = NCU_TRAFFIC.get((dom, kernel_digest()))
+    if dom.startswith("translate"):
+        # diagonal complex products over the interaction lists: FP32 ALU-bound
+        clk = clocks.get("sm_mhz") or 2070.0
+        peak = fp32_peak_tflops(clk)
+        ach = aflops / (dom_ms / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": traffic, "algorithmic_flops": aflops, "algorithmic_bytes": abytes,
+                "ms": dom_ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (median "
+                                          "SM clock under load)" % clk}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": abytes / (dom_ms / 1e3) / 1e9, "peak": hbm_peak,
+                "unit": "GB/s", "frac": abytes / (dom_ms / 1e3) / 1e9 / hbm_peak, "traffic": traffic,
+                "algorithmic_bytes": abytes, "ms": dom_ms, "peak_source": peak_src}
+    roof["timing"] = "CUDA events around the kernel in a serial pass on the launching stream"
+    roof["kernel_digest"] = kernel_digest()
+    hbm_stages, alu_stages = {}, {}
     for k, msk in stages.items():
-        b_, _ = algorithmic(info, B, k)
+        b_, f_ = algorithmic(info, B, k)
         if b_ and msk > 0:
             hbm_stages[k] = round(b_ / (msk / 1e3) / 1e9 / hbm_peak, 3)
+        if f_ and msk > 0:
+            alu_stages[k] = round(f_ / (msk / 1e3) / 1e12 / fp32_peak_tflops(clocks.get("sm_mhz") or 2070.0), 3)
 
     # --- end to end through the public host-buffer entry point (pinned memory)
     xh = torch.from_numpy(x_np.astype(np.float32)).pin_memory().numpy()
@@ -308,12 +362,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(a.steps):
         plan.matvec_host(xh, FP32, yh)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": B * a.steps / e2e_s * world, "unit": UNIT, "h2d_bytes_per_step": int(xh.nbytes),
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": replica_rate(B, a.steps, e2e_s, world), "unit": UNIT, "h2d_bytes_per_step": int(xh.nbytes),
            "d2h_bytes_per_step": int(yh.nbytes),
            "how": "mlfma_matvec_host: pinned host x -> device, product, device -> pinned host y, stream sync"}
 
@@ -340,6 +390,7 @@ def main():
                               "rows": 16, "bound": 1e-3},
             "roofline": roof,
             "hbm_frac_by_stage": hbm_stages,
+            "fp32_alu_frac_by_stage": alu_stages,
             "stage_ms": {k: round(vv, 4) for k, vv in stages.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
