@@ -196,6 +196,57 @@ mlfma_status mlfma_matvec_noalloc(mlfma_plan_t plan, const void *x, int x_is_com
  * error. */
 mlfma_status mlfma_sync(mlfma_plan_t plan, void *stream);
 
+/*
+ * Characteristic modes (Section IV): the nev characteristic values nearest
+ * zero of X J = lambda R J (Eq. (GEP)) with R = -Re Z, X = Im Z, by the
+ * implicitly restarted Arnoldi method (exact shifts) on
+ *   MLFMA_CM_ZINV_R: Z_H^-1 R, Z_H = R + iX, eigenvalues 1/(1 + i lambda)
+ *                    (Eq. (SEP1), the paper's preferred form), or
+ *   MLFMA_CM_XINV_R: X^-1 R, eigenvalues 1/lambda (Eq. (SEP)),
+ * selecting the largest magnitudes.  Every operator application is one
+ * product with R and one inner solve (with Z or X) by restarted GMRES,
+ * right-preconditioned with a sparse approximate inverse P of the stored
+ * near-field matrix (minimising ||I - A_near P||_F, Section IV) on the
+ * near-field pattern (column j lives on the unknowns of j's leaf box and its
+ * neighbours; the thresholds of the paper's cited SAI variant are not given,
+ * so the whole near pattern is kept); all products run
+ * through the GPU MLFMA in `prec`, an inner solve done with FP32 products is
+ * checked with an FP64 product when the plan has FP64 and refined if needed.
+ * Arnoldi vectors, Hessenberg matrices and Ritz pairs are FP64 on the host.
+ *  lambda  host [nev], sorted by |lambda|
+ *  J       host [N][nev] real characteristic currents (unit 2-norm), canonical
+ *          RWG order; may be NULL
+ *  stats   may be NULL
+ * Synchronous.  Errors: EINVAL, ENOTCONV (Arnoldi did not converge within
+ * max_restarts, or a near-field block of the preconditioner is singular;
+ * lambda then holds the current Ritz values), ECUDA.
+ */
+typedef enum { MLFMA_CM_ZINV_R = 0, MLFMA_CM_XINV_R = 1 } mlfma_cm_op;
+typedef struct {
+    int nev;            /* characteristic values wanted (default 10) */
+    int ncv;            /* Arnoldi basis size, nev + 2 <= ncv <= N (default 30) */
+    int op;             /* mlfma_cm_op (default MLFMA_CM_ZINV_R) */
+    int prec;           /* mlfma_prec of the products (default MLFMA_FP32) */
+    double tol;         /* Ritz residual tolerance, relative (default 1e-8) */
+    double gmres_tol;   /* inner relative residual (default 1e-6) */
+    int gmres_restart;  /* GMRES restart length (default 50) */
+    int max_inner;      /* GMRES iterations per solve (default 2000) */
+    int max_restarts;   /* implicit restarts (default 200) */
+    int use_sai;        /* 1: sparse-approximate-inverse preconditioner (default 1) */
+    uint64_t seed;      /* start vector: N(0,1) from a 64-bit Mersenne twister */
+} mlfma_cm_opts;
+typedef struct {
+    int restarts;
+    int64_t inner_iterations;
+    int64_t products;   /* MLFMA products issued */
+    int converged;
+    int inner_converged;
+    double seconds;
+} mlfma_cm_stats;
+mlfma_status mlfma_cm_default_opts(mlfma_cm_opts *opts);
+mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opts, double *lambda, double *J,
+                          mlfma_cm_stats *stats);
+
 /* Summary of a plan (host copy; all fields filled). */
 #define MLFMA_MAX_LEVELS 22
 typedef struct {

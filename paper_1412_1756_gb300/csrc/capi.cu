@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <complex>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -501,6 +502,26 @@ bool plan_product_view(mlfma_plan_t p, int prec, ProductArgs<float> *a32, Produc
 }
 
 void set_last_error(const std::string &msg) { g_err = msg; }
+
+// Host copy of the near-field strips (leaf order, FP64 when the plan has
+// FP64 values, else widened from FP32) and the plan's host tables.
+bool plan_near_host(mlfma_plan_t p, std::vector<std::complex<double>> &vals, const PlanHost **host)
+{
+    if (!p || !p->on_device) return false;
+    DeviceGuard g(p->device);
+    vals.resize((size_t)p->host.nnz);
+    if (p->has64) {
+        if (cudaMemcpy(vals.data(), p->a64.near_val, vals.size() * 16, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return false;
+    } else {
+        std::vector<float> tmp(2 * vals.size());
+        if (cudaMemcpy(tmp.data(), p->a32.near_val, tmp.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return false;
+        for (size_t i = 0; i < vals.size(); ++i) vals[i] = std::complex<double>(tmp[2 * i], tmp[2 * i + 1]);
+    }
+    *host = &p->host;
+    return true;
+}
 }  // namespace mlfma
 
 extern "C" {

@@ -1,0 +1,669 @@
+// Characteristic modes by implicitly restarted Arnoldi (Section IV).
+//
+// Eq. (SEP1): Z^-1 R J = J / (1 + i lambda), values nearest zero = largest
+// |mu|; or Eq. (SEP): X^-1 R J = J / lambda.  Each Arnoldi step applies the
+// operator once: a product with R through the GPU MLFMA, then an inner
+// solve (Z or X) by restarted GMRES, right-preconditioned by a sparse
+// approximate inverse P of the stored near-field matrix (minimising
+// ||I - Z_near P||_F over a prescribed pattern, Section IV), its products
+// through the GPU MLFMA as well.  The Krylov bases, Hessenberg matrices and
+// Ritz pairs are FP64 on the host; an inner solve that used FP32 products is
+// checked with an FP64 product and refined when needed.
+//
+// Sign reading (the paper's Z = R + iX taken with exp(ikR)/R and +ik eta
+// gives characteristic values of the wrong sign): with Zp the literal
+// product, R := -Re Zp and X := +Im Zp, so Z_H := R + iX = -conj(Zp) and
+// Z_H^-1 b = conj(Zp^-1 (-conj b)).
+#include "../../include/mlfma.h"
+#include "plan_host.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <random>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace mlfma {
+bool plan_near_host(mlfma_plan_t p, std::vector<std::complex<double>> &vals, const PlanHost **host);
+void set_last_error(const std::string &msg);
+}  // namespace mlfma
+
+using namespace mlfma;
+using cd = std::complex<double>;
+
+namespace {
+
+mlfma_status fail(mlfma_status st, const std::string &msg)
+{
+    set_last_error(msg);
+    return st;
+}
+
+double nrm2(const std::vector<cd> &v)
+{
+    double s = 0;
+    for (const cd &z : v) s += std::norm(z);
+    return std::sqrt(s);
+}
+
+cd dotc(const cd *a, const cd *b, int64_t n)   // a^H b
+{
+    cd s = 0;
+    for (int64_t i = 0; i < n; ++i) s += std::conj(a[i]) * b[i];
+    return s;
+}
+
+// ------------------------------------------------- dense complex eigen ---
+// Givens rotation G = [c s; -conj(s) c] (c real) with G [x; y] = [r; 0].
+void givens(cd x, cd y, double &c, cd &s)
+{
+    const double ax = std::abs(x), ay = std::abs(y);
+    if (ay == 0) { c = 1; s = 0; return; }
+    if (ax == 0) { c = 0; s = std::conj(y) / ay; return; }
+    const double nr = std::hypot(ax, ay);
+    c = ax / nr;
+    s = (x / ax) * std::conj(y) / nr;
+}
+
+// One implicitly shifted QR sweep with shift mu on rows/columns [lo, hi] of
+// the m x m upper Hessenberg H (row-major); the similarity is applied to the
+// whole matrix and accumulated into the columns of Q (m x m, row-major).
+void qr_sweep(int m, std::vector<cd> &H, std::vector<cd> &Q, int lo, int hi, cd mu)
+{
+    auto h = [&](int i, int j) -> cd & { return H[(size_t)i * m + j]; };
+    cd x = h(lo, lo) - mu, y = h(lo + 1, lo);
+    for (int k = lo; k < hi; ++k) {
+        double c;
+        cd s;
+        givens(x, y, c, s);
+        for (int j = std::max(lo, k - 1); j < m; ++j) {   // rows k, k+1
+            const cd a = h(k, j), b = h(k + 1, j);
+            h(k, j) = c * a + s * b;
+            h(k + 1, j) = -std::conj(s) * a + c * b;
+        }
+        const int rmax = std::min(k + 2, hi);
+        for (int i = 0; i <= rmax; ++i) {                  // columns k, k+1
+            const cd a = h(i, k), b = h(i, k + 1);
+            h(i, k) = c * a + std::conj(s) * b;
+            h(i, k + 1) = -s * a + c * b;
+        }
+        for (int i = 0; i < m; ++i) {
+            cd &a = Q[(size_t)i * m + k], &b = Q[(size_t)i * m + k + 1];
+            const cd qa = a, qb = b;
+            a = c * qa + std::conj(s) * qb;
+            b = -s * qa + c * qb;
+        }
+        if (k < hi - 1) {
+            x = h(k + 1, k);
+            y = h(k + 2, k);
+        }
+    }
+}
+
+// Eigenvalues w and unit eigenvectors (columns of X) of an m x m upper
+// Hessenberg matrix by shifted QR (Wilkinson shifts, deflation) to Schur
+// form and back-substitution.
+bool hessenberg_eig(int m, std::vector<cd> H, std::vector<cd> &w, std::vector<cd> &X)
+{
+    std::vector<cd> Q((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
+    auto h = [&](int i, int j) -> cd & { return H[(size_t)i * m + j]; };
+    const double eps = 1e-15;
+    int hi = m - 1, iter = 0, total = 0;
+    while (hi > 0) {
+        int l = hi;
+        while (l > 0 && std::abs(h(l, l - 1)) > eps * (std::abs(h(l - 1, l - 1)) + std::abs(h(l, l)))) --l;
+        if (l > 0) h(l, l - 1) = 0.0;
+        if (l == hi) {
+            --hi;
+            iter = 0;
+            continue;
+        }
+        const cd a = h(hi - 1, hi - 1), b = h(hi - 1, hi), c = h(hi, hi - 1), d = h(hi, hi);
+        const cd tr = a + d, disc = std::sqrt(0.25 * tr * tr - (a * d - b * c));
+        cd mu1 = 0.5 * tr + disc, mu2 = 0.5 * tr - disc;
+        cd mu = std::abs(mu1 - d) < std::abs(mu2 - d) ? mu1 : mu2;
+        if (iter > 0 && iter % 10 == 0) mu = d + cd(std::abs(c), 0.0);   // exceptional shift
+        qr_sweep(m, H, Q, l, hi, mu);
+        if (++iter > 60 || ++total > 100 * m) return false;
+    }
+    w.resize(m);
+    for (int i = 0; i < m; ++i) w[i] = h(i, i);
+    X.assign((size_t)m * m, 0.0);
+    std::vector<cd> y(m);
+    double tnorm = 0;
+    for (int i = 0; i < m; ++i)
+        for (int j = i; j < m; ++j) tnorm = std::max(tnorm, std::abs(h(i, j)));
+    for (int j = 0; j < m; ++j) {
+        std::fill(y.begin(), y.end(), 0.0);
+        y[j] = 1.0;
+        for (int i = j - 1; i >= 0; --i) {
+            cd s = 0;
+            for (int k = i + 1; k <= j; ++k) s += h(i, k) * y[k];
+            cd den = h(i, i) - h(j, j);
+            if (std::abs(den) < 1e-14 * tnorm) den = 1e-14 * tnorm;
+            y[i] = -s / den;
+        }
+        double nn = 0;
+        for (int i = 0; i < m; ++i) {
+            cd s = 0;
+            for (int k = 0; k <= j; ++k) s += Q[(size_t)i * m + k] * y[k];
+            X[(size_t)i * m + j] = s;
+            nn += std::norm(s);
+        }
+        nn = std::sqrt(nn);
+        for (int i = 0; i < m; ++i) X[(size_t)i * m + j] /= nn;
+    }
+    return true;
+}
+
+// ------------------------------------------------------- products ---
+enum Which { PROD_Z, PROD_X, PROD_R };
+
+struct Products {
+    mlfma_plan_t plan;
+    int64_t n;
+    int prec;
+    std::vector<float> xf, yf;
+    std::vector<double> xd, yd;
+    int64_t count = 0;
+
+    // y = M x for complex x (host, canonical order); M = Zp, X = Im Zp or
+    // R = -Re Zp (the last two through two real columns).
+    mlfma_status apply(Which w, const cd *x, cd *y, int p)
+    {
+        const bool real_cols = w != PROD_Z;
+        mlfma_status st;
+        if (p == MLFMA_FP32) {
+            xf.resize(2 * n);
+            yf.resize(4 * n);
+            for (int64_t i = 0; i < n; ++i) {
+                xf[2 * i] = (float)x[i].real();
+                xf[2 * i + 1] = (float)x[i].imag();
+            }
+            st = mlfma_matvec_host(plan, xf.data(), real_cols ? 0 : 1, yf.data(), real_cols ? 2 : 1, MLFMA_FP32, nullptr);
+            if (st) return st;
+            for (int64_t i = 0; i < n; ++i) {
+                if (!real_cols) y[i] = cd(yf[2 * i], yf[2 * i + 1]);
+                else if (w == PROD_X) y[i] = cd(yf[4 * i + 1], yf[4 * i + 3]);
+                else y[i] = cd(-yf[4 * i], -yf[4 * i + 2]);
+            }
+        } else {
+            xd.resize(2 * n);
+            yd.resize(4 * n);
+            for (int64_t i = 0; i < n; ++i) {
+                xd[2 * i] = x[i].real();
+                xd[2 * i + 1] = x[i].imag();
+            }
+            st = mlfma_matvec_host(plan, xd.data(), real_cols ? 0 : 1, yd.data(), real_cols ? 2 : 1, MLFMA_FP64, nullptr);
+            if (st) return st;
+            for (int64_t i = 0; i < n; ++i) {
+                if (!real_cols) y[i] = cd(yd[2 * i], yd[2 * i + 1]);
+                else if (w == PROD_X) y[i] = cd(yd[4 * i + 1], yd[4 * i + 3]);
+                else y[i] = cd(-yd[4 * i], -yd[4 * i + 2]);
+            }
+        }
+        ++count;
+        return MLFMA_OK;
+    }
+};
+
+// ------------------------------------------------------------ SAI ---
+// P = argmin ||I - A_near P||_F over the prescribed pattern "column j of P
+// lives on the unknowns of j's leaf box and its neighbours" (the near-field
+// pattern; the thresholds of the paper's cited SAI variant are not given, so
+// the whole near pattern is kept).  For leaf box b with unknowns J, the
+// columns j in J share the support S = near unknowns of b; the rows that can
+// be non-zero are those of the boxes near any box of S (the two-ring of b).
+// With A = A_near[rows, S], P[S, J] solves the normal equations
+// (A^H A) P = A^H E_J.  A_near is symmetric, so column s of A is row s of
+// the stored strip of box(s).  P is stored in the near-strip layout (rows of
+// a box x its neighbours' unknowns), so applying it is a near-field product.
+struct Sai {
+    const PlanHost *H = nullptr;
+    std::vector<cd> vals;                 // strip layout, like the near field
+    std::vector<int32_t> box_of;          // leaf-order unknown -> leaf box
+
+    int col_offset(int a, int b) const    // first strip column of box b in box a's strip
+    {
+        int off = 0;
+        for (int e = H->nb_ptr[a]; e < H->nb_ptr[a + 1]; ++e) {
+            const int c = H->nb_box[e];
+            if (c == b) return off;
+            off += H->box_ptr[c + 1] - H->box_ptr[c];
+        }
+        return -1;
+    }
+
+    bool build(const PlanHost *host, const std::vector<cd> &near, bool imag_only)
+    {
+        H = host;
+        const int nbox = (int)host->box_ptr.size() - 1;
+        box_of.resize(host->N);
+        for (int b = 0; b < nbox; ++b)
+            for (int u = host->box_ptr[b]; u < host->box_ptr[b + 1]; ++u) box_of[u] = b;
+        vals.assign((size_t)host->nnz, 0.0);
+        const int nthreads = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        std::vector<char> bad(nthreads, 0);
+        for (int t = 0; t < nthreads; ++t)
+            pool.emplace_back([&, t]() {
+                std::vector<int> rowpos(host->N, -1);
+                for (int b = t; b < nbox; b += nthreads)
+                    if (!build_box(b, near, imag_only, rowpos)) bad[t] = 1;
+            });
+        for (auto &th : pool) th.join();
+        for (char c : bad)
+            if (c) return false;
+        return true;
+    }
+
+    cd z(const std::vector<cd> &near, bool imag_only, int a, int row, int col) const   // strip of a at (row, col)
+    {
+        const int na = H->box_ptr[a + 1] - H->box_ptr[a];
+        const cd v = near[(size_t)H->strip_off[a] + (size_t)col * na + row];
+        return imag_only ? cd(v.imag(), 0.0) : v;
+    }
+
+    bool build_box(int b, const std::vector<cd> &near, bool imag_only, std::vector<int> &rowpos)
+    {
+        const int r0 = H->box_ptr[b], nJ = H->box_ptr[b + 1] - r0;
+        // support S: the strip columns of b (unknowns of b's neighbours)
+        const int c0 = H->col_ptr[b], nS = H->col_ptr[b + 1] - c0;
+        const int32_t *S = H->strip_col.data() + c0;
+        // rows: the two-ring of b, grouped by box
+        std::vector<int> ring;
+        for (int e = H->nb_ptr[b]; e < H->nb_ptr[b + 1]; ++e) {
+            const int a = H->nb_box[e];
+            for (int f = H->nb_ptr[a]; f < H->nb_ptr[a + 1]; ++f) ring.push_back(H->nb_box[f]);
+        }
+        std::sort(ring.begin(), ring.end());
+        ring.erase(std::unique(ring.begin(), ring.end()), ring.end());
+        int nR = 0;
+        std::vector<int> ring_off(ring.size() + 1);
+        for (size_t i = 0; i < ring.size(); ++i) {
+            ring_off[i] = nR;
+            for (int u = H->box_ptr[ring[i]]; u < H->box_ptr[ring[i] + 1]; ++u) rowpos[u] = nR++;
+        }
+        ring_off[ring.size()] = nR;
+        // A [nR x nS], column-major: column s = row s of box(s)'s strip
+        std::vector<cd> A((size_t)nR * nS, 0.0);
+        for (int k = 0; k < nS; ++k) {
+            const int s = S[k], a = box_of[s];
+            const int na = H->box_ptr[a + 1] - H->box_ptr[a];
+            const int ac0 = H->col_ptr[a], anc = H->col_ptr[a + 1] - ac0;
+            (void)na;
+            for (int c = 0; c < anc; ++c) {
+                const int r = rowpos[H->strip_col[ac0 + c]];
+                A[(size_t)k * nR + r] = z(near, imag_only, a, s - H->box_ptr[a], c);
+            }
+        }
+        // N = A^H A (Hermitian; upper triangle then mirrored)
+        std::vector<cd> N((size_t)nS * nS, 0.0);
+        for (int i = 0; i < nS; ++i) {
+            const cd *ai = A.data() + (size_t)i * nR;
+            for (int j = i; j < nS; ++j) {
+                const cd *aj = A.data() + (size_t)j * nR;
+                cd s = 0;
+                for (int r = 0; r < nR; ++r) s += std::conj(ai[r]) * aj[r];
+                N[(size_t)i * nS + j] = s;
+                N[(size_t)j * nS + i] = std::conj(s);
+            }
+        }
+        // rhs = A^H E_J: rhs[i][jj] = conj(A[row(J_jj), i])
+        std::vector<cd> P((size_t)nS * nJ);
+        for (int i = 0; i < nS; ++i)
+            for (int jj = 0; jj < nJ; ++jj) P[(size_t)i * nJ + jj] = std::conj(A[(size_t)i * nR + rowpos[r0 + jj]]);
+        for (int u : ring)
+            for (int w = H->box_ptr[u]; w < H->box_ptr[u + 1]; ++w) rowpos[w] = -1;
+        // Cholesky N = L L^H in place (lower), then L L^H P = rhs
+        for (int j = 0; j < nS; ++j) {
+            double d = N[(size_t)j * nS + j].real();
+            for (int k = 0; k < j; ++k) d -= std::norm(N[(size_t)j * nS + k]);
+            if (!(d > 0)) return false;
+            const double ljj = std::sqrt(d);
+            N[(size_t)j * nS + j] = ljj;
+            for (int i = j + 1; i < nS; ++i) {
+                cd s = N[(size_t)i * nS + j];
+                for (int k = 0; k < j; ++k) s -= N[(size_t)i * nS + k] * std::conj(N[(size_t)j * nS + k]);
+                N[(size_t)i * nS + j] = s / ljj;
+            }
+        }
+        for (int jj = 0; jj < nJ; ++jj) {
+            for (int i = 0; i < nS; ++i) {
+                cd s = P[(size_t)i * nJ + jj];
+                for (int k = 0; k < i; ++k) s -= N[(size_t)i * nS + k] * P[(size_t)k * nJ + jj];
+                P[(size_t)i * nJ + jj] = s / N[(size_t)i * nS + i];
+            }
+            for (int i = nS - 1; i >= 0; --i) {
+                cd s = P[(size_t)i * nJ + jj];
+                for (int k = i + 1; k < nS; ++k) s -= std::conj(N[(size_t)k * nS + i]) * P[(size_t)k * nJ + jj];
+                P[(size_t)i * nJ + jj] = s / N[(size_t)i * nS + i];
+            }
+        }
+        // scatter P[S, J] into the strips of the boxes holding S
+        for (int k = 0; k < nS; ++k) {
+            const int s = S[k], a = box_of[s];
+            const int na = H->box_ptr[a + 1] - H->box_ptr[a];
+            const int off = col_offset(a, b);
+            if (off < 0) return false;
+            cd *strip = vals.data() + H->strip_off[a];
+            for (int jj = 0; jj < nJ; ++jj) strip[(size_t)(off + jj) * na + (s - H->box_ptr[a])] = P[(size_t)k * nJ + jj];
+        }
+        return true;
+    }
+
+    // y = P x, canonical order in and out (near-field-shaped product)
+    void apply(const cd *x, cd *y) const
+    {
+        const int nbox = (int)H->box_ptr.size() - 1;
+        const int nthreads = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nthreads; ++t)
+            pool.emplace_back([&, t]() {
+                for (int a = t; a < nbox; a += nthreads) {
+                    const int r0 = H->box_ptr[a], na = H->box_ptr[a + 1] - r0;
+                    const int c0 = H->col_ptr[a], nc = H->col_ptr[a + 1] - c0;
+                    const cd *strip = vals.data() + H->strip_off[a];
+                    for (int i = 0; i < na; ++i) {
+                        cd s = 0;
+                        for (int c = 0; c < nc; ++c) s += strip[(size_t)c * na + i] * x[H->perm[H->strip_col[c0 + c]]];
+                        y[H->perm[r0 + i]] = s;
+                    }
+                }
+            });
+        for (auto &th : pool) th.join();
+    }
+};
+
+// --------------------------------------------------------- GMRES ---
+// Solve M w = b (M = Zp or X) with right preconditioning by P, restarted
+// every m iterations; FP64 Krylov arithmetic, products in precision `prec`;
+// the final residual is re-checked with an FP64 product when the plan has
+// one, and the solve continues from there if it is above tol.
+struct Gmres {
+    Products *prod;
+    const Sai *sai;
+    Which which;
+    int prec, restart, maxit, check_prec;
+    double tol;
+    int64_t iterations = 0;
+
+    mlfma_status solve(const std::vector<cd> &b, std::vector<cd> &w, bool &converged)
+    {
+        const int64_t n = (int64_t)b.size();
+        w.assign(n, 0.0);
+        const double bn = nrm2(b);
+        converged = false;
+        if (bn == 0) {
+            converged = true;
+            return MLFMA_OK;
+        }
+        std::vector<cd> r = b, t(n), z(n);
+        std::vector<std::vector<cd>> V;
+        int used = 0;
+        for (int refine = 0; refine < 8 && used < maxit; ++refine) {
+            // inner restarted GMRES on M d = r (r = current residual)
+            std::vector<cd> d(n, 0.0), rr = r;
+            double rn = nrm2(rr);
+            // a pass with FP32 products can lower its own residual by ~1e-5 at
+            // most; the FP64 check and further passes do the rest
+            const double target = std::max(0.5 * tol * bn, (prec == MLFMA_FP32 ? 1e-5 : 0.0) * rn);
+            while (used < maxit && rn > target) {
+                const int m = std::min(restart, maxit - used);
+                V.assign(m + 1, std::vector<cd>(n));
+                std::vector<cd> Hm((size_t)(m + 1) * m, 0.0), g(m + 1, 0.0), cs(m), sn(m);
+                std::vector<double> cr(m);
+                for (int64_t i = 0; i < n; ++i) V[0][i] = rr[i] / rn;
+                g[0] = rn;
+                int k = 0;
+                for (; k < m; ++k) {
+                    if (sai) sai->apply(V[k].data(), z.data());
+                    else z = V[k];
+                    mlfma_status st = prod->apply(which, z.data(), V[k + 1].data(), prec);
+                    if (st) return st;
+                    ++used;
+                    ++iterations;
+                    for (int pass = 0; pass < 2; ++pass)   // classical Gram-Schmidt, twice
+                        for (int j = 0; j <= k; ++j) {
+                            const cd hj = dotc(V[j].data(), V[k + 1].data(), n);
+                            Hm[(size_t)j * m + k] += hj;
+                            for (int64_t i = 0; i < n; ++i) V[k + 1][i] -= hj * V[j][i];
+                        }
+                    const double hn = nrm2(V[k + 1]);
+                    Hm[(size_t)(k + 1) * m + k] = hn;
+                    if (hn > 0)
+                        for (int64_t i = 0; i < n; ++i) V[k + 1][i] /= hn;
+                    for (int j = 0; j < k; ++j) {   // previous rotations
+                        const cd a = Hm[(size_t)j * m + k], bb = Hm[(size_t)(j + 1) * m + k];
+                        Hm[(size_t)j * m + k] = cr[j] * a + sn[j] * bb;
+                        Hm[(size_t)(j + 1) * m + k] = -std::conj(sn[j]) * a + cr[j] * bb;
+                    }
+                    double c;
+                    cd s;
+                    givens(Hm[(size_t)k * m + k], Hm[(size_t)(k + 1) * m + k], c, s);
+                    cr[k] = c;
+                    sn[k] = s;
+                    Hm[(size_t)k * m + k] = c * Hm[(size_t)k * m + k] + s * Hm[(size_t)(k + 1) * m + k];
+                    Hm[(size_t)(k + 1) * m + k] = 0.0;
+                    g[k + 1] = -std::conj(s) * g[k];
+                    g[k] = c * g[k];
+                    if (std::abs(g[k + 1]) <= target || used >= maxit) {
+                        ++k;
+                        break;
+                    }
+                }
+                // y = H^-1 g; d += P V y
+                std::vector<cd> y(k);
+                for (int i = k - 1; i >= 0; --i) {
+                    cd s = g[i];
+                    for (int j = i + 1; j < k; ++j) s -= Hm[(size_t)i * m + j] * y[j];
+                    y[i] = s / Hm[(size_t)i * m + i];
+                }
+                std::fill(t.begin(), t.end(), 0.0);
+                for (int j = 0; j < k; ++j)
+                    for (int64_t i = 0; i < n; ++i) t[i] += y[j] * V[j][i];
+                if (sai) sai->apply(t.data(), z.data());
+                else z = t;
+                for (int64_t i = 0; i < n; ++i) d[i] += z[i];
+                // true residual of the inner system in the product precision
+                mlfma_status st = prod->apply(which, d.data(), t.data(), prec);
+                if (st) return st;
+                for (int64_t i = 0; i < n; ++i) rr[i] = r[i] - t[i];
+                rn = nrm2(rr);
+            }
+            for (int64_t i = 0; i < n; ++i) w[i] += d[i];
+            // residual check with the checking precision (FP64 when available)
+            mlfma_status st = prod->apply(which, w.data(), t.data(), check_prec);
+            if (st) return st;
+            for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+            if (nrm2(r) <= tol * bn) {
+                converged = true;
+                break;
+            }
+        }
+        return MLFMA_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" mlfma_status mlfma_cm_default_opts(mlfma_cm_opts *o)
+{
+    if (!o) return fail(MLFMA_EINVAL, "opts is NULL");
+    o->nev = 10;
+    o->ncv = 30;
+    o->op = MLFMA_CM_ZINV_R;
+    o->prec = MLFMA_FP32;
+    o->tol = 1e-8;
+    o->gmres_tol = 1e-6;
+    o->gmres_restart = 50;
+    o->max_inner = 2000;
+    o->max_restarts = 200;
+    o->use_sai = 1;
+    o->seed = 1412175602ULL;
+    return MLFMA_OK;
+}
+
+extern "C" mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opts, double *lambda, double *J,
+                                     mlfma_cm_stats *stats)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!plan || !opts || !lambda) return fail(MLFMA_EINVAL, "plan, opts and lambda are required");
+    mlfma_cm_opts o = *opts;
+    int64_t n = 0;
+    if (mlfma_num_unknowns(plan, &n)) return MLFMA_EINVAL;
+    if (o.nev < 1 || o.ncv <= o.nev + 1 || o.ncv > n) return fail(MLFMA_EINVAL, "need 1 <= nev < ncv - 1 and ncv <= N");
+    if (o.op != MLFMA_CM_ZINV_R && o.op != MLFMA_CM_XINV_R) return fail(MLFMA_EINVAL, "unknown operator");
+    if (o.prec != MLFMA_FP32 && o.prec != MLFMA_FP64) return fail(MLFMA_EINVAL, "unknown precision");
+    if (!(o.gmres_tol > 0) || o.gmres_restart < 2 || o.max_inner < 1 || o.max_restarts < 1)
+        return fail(MLFMA_EINVAL, "bad GMRES settings");
+    std::vector<cd> near;
+    const PlanHost *H = nullptr;
+    if (!plan_near_host(plan, near, &H)) return fail(MLFMA_EINVAL, "plan is host-only or its near field is unreadable");
+    const bool has64 = [&]() {   // can the residual be checked in FP64?
+        std::vector<double> x(2 * n, 0.0), y(4 * n);
+        return mlfma_matvec_host(plan, x.data(), 1, y.data(), 1, MLFMA_FP64, nullptr) == MLFMA_OK;
+    }();
+    Products prod{plan, n, o.prec};
+    Sai sai;
+    if (o.use_sai && !sai.build(H, near, o.op == MLFMA_CM_XINV_R))
+        return fail(MLFMA_ENOTCONV, "sparse approximate inverse: a near-field block is singular");
+    near.clear();
+    near.shrink_to_fit();
+    Gmres gm{&prod, o.use_sai ? &sai : nullptr, o.op == MLFMA_CM_ZINV_R ? PROD_Z : PROD_X, o.prec,
+             o.gmres_restart, o.max_inner, has64 ? MLFMA_FP64 : o.prec, o.gmres_tol};
+
+    // the operator of Eq. (SEP1) or (SEP)
+    std::vector<cd> tmp(n), rhs(n), sol(n);
+    bool inner_ok = true;
+    auto op = [&](const cd *v, cd *out) -> mlfma_status {
+        mlfma_status st;
+        bool conv = false;
+        if (o.op == MLFMA_CM_ZINV_R) {
+            // Z_H^-1 R v = conj(Zp^-1 (-R conj v))
+            for (int64_t i = 0; i < n; ++i) tmp[i] = std::conj(v[i]);
+            if ((st = prod.apply(PROD_R, tmp.data(), rhs.data(), o.prec))) return st;
+            for (int64_t i = 0; i < n; ++i) rhs[i] = -rhs[i];
+            if ((st = gm.solve(rhs, sol, conv))) return st;
+            for (int64_t i = 0; i < n; ++i) out[i] = std::conj(sol[i]);
+        } else {
+            if ((st = prod.apply(PROD_R, v, rhs.data(), o.prec))) return st;
+            if ((st = gm.solve(rhs, sol, conv))) return st;
+            for (int64_t i = 0; i < n; ++i) out[i] = sol[i];
+        }
+        inner_ok = inner_ok && conv;
+        return MLFMA_OK;
+    };
+
+    const int m = o.ncv, k = o.nev;
+    std::vector<std::vector<cd>> V(m + 1, std::vector<cd>(n));
+    std::vector<cd> Hm((size_t)(m + 1) * m, 0.0);   // (m+1) x m, row-major
+    std::mt19937_64 rng(o.seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    for (int64_t i = 0; i < n; ++i) V[0][i] = nd(rng);
+    {
+        const double v0 = nrm2(V[0]);
+        for (auto &z : V[0]) z /= v0;
+    }
+    int kstart = 0, restarts = 0;
+    bool converged = false;
+    std::vector<cd> w, X;
+    std::vector<int> order;
+    mlfma_status st;
+    for (; restarts < o.max_restarts; ++restarts) {
+        for (int j = kstart; j < m; ++j) {   // extend the Arnoldi factorisation to m steps
+            if ((st = op(V[j].data(), V[j + 1].data()))) return st;
+            for (int pass = 0; pass < 2; ++pass)
+                for (int i = 0; i <= j; ++i) {
+                    const cd h = dotc(V[i].data(), V[j + 1].data(), n);
+                    Hm[(size_t)i * m + j] += h;
+                    for (int64_t q = 0; q < n; ++q) V[j + 1][q] -= h * V[i][q];
+                }
+            const double hn = nrm2(V[j + 1]);
+            Hm[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0)
+                for (auto &z : V[j + 1]) z /= hn;
+        }
+        std::vector<cd> Hsq(Hm.begin(), Hm.begin() + (size_t)m * m);
+        if (!hessenberg_eig(m, Hsq, w, X)) return fail(MLFMA_ENOTCONV, "Hessenberg eigenvalue iteration failed");
+        order.resize(m);
+        for (int i = 0; i < m; ++i) order[i] = i;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return std::abs(w[a]) > std::abs(w[b]); });
+        const double beta = std::abs(Hm[(size_t)m * m + (m - 1)]);
+        converged = true;
+        for (int i = 0; i < k; ++i) {
+            const int e = order[i];
+            const double res = beta * std::abs(X[(size_t)(m - 1) * m + e]);
+            if (res > o.tol * std::max(std::abs(w[e]), 1e-300)) converged = false;
+        }
+        if (converged || restarts + 1 == o.max_restarts) break;
+        // implicit restart with the m - k unwanted Ritz values as shifts
+        std::vector<cd> Q((size_t)m * m, 0.0);
+        for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
+        std::vector<cd> Hw(Hm.begin(), Hm.begin() + (size_t)m * m);
+        for (int i = k; i < m; ++i) qr_sweep(m, Hw, Q, 0, m - 1, w[order[i]]);
+        // f_k = V Q e_{k} * H+(k, k-1) + f_m * Q(m-1, k-1),  f_m = H(m, m-1) v_m
+        std::vector<std::vector<cd>> Vn(k + 1, std::vector<cd>(n, 0.0));
+        for (int j = 0; j <= k; ++j)
+            for (int i = 0; i < m; ++i) {
+                const cd q = Q[(size_t)i * m + j];
+                if (q != 0.0)
+                    for (int64_t r = 0; r < n; ++r) Vn[j][r] += q * V[i][r];
+            }
+        std::vector<cd> f(n);
+        const cd hk = Hw[(size_t)k * m + (k - 1)], fm = Hm[(size_t)m * m + (m - 1)] * Q[(size_t)(m - 1) * m + (k - 1)];
+        for (int64_t r = 0; r < n; ++r) f[r] = Vn[k][r] * hk + V[m][r] * fm;
+        std::fill(Hm.begin(), Hm.end(), 0.0);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) Hm[(size_t)i * m + j] = Hw[(size_t)i * m + j];
+        const double fn = nrm2(f);
+        for (int j = 0; j < k; ++j) V[j] = Vn[j];
+        Hm[(size_t)k * m + (k - 1)] = fn;
+        for (int64_t r = 0; r < n; ++r) V[k][r] = fn > 0 ? f[r] / fn : 0.0;
+        kstart = k;
+    }
+    // Ritz pairs -> characteristic values and real currents
+    std::vector<std::pair<double, int>> lam;
+    for (int i = 0; i < k; ++i) {
+        const cd mu = w[order[i]];
+        const double l = o.op == MLFMA_CM_ZINV_R ? ((1.0 / mu - 1.0) / cd(0, 1)).real() : (1.0 / mu).real();
+        lam.push_back({l, order[i]});
+    }
+    std::sort(lam.begin(), lam.end(), [](const auto &a, const auto &b) { return std::abs(a.first) < std::abs(b.first); });
+    for (int i = 0; i < k; ++i) lambda[i] = lam[i].first;
+    if (J) {
+        std::vector<cd> v(n);
+        for (int i = 0; i < k; ++i) {
+            const int e = lam[i].second;
+            std::fill(v.begin(), v.end(), 0.0);
+            for (int j = 0; j < m; ++j) {
+                const cd s = X[(size_t)j * m + e];
+                for (int64_t r = 0; r < n; ++r) v[r] += s * V[j][r];
+            }
+            // characteristic currents are real up to a phase: rotate to the
+            // phase that maximises the real part's norm, normalise
+            cd s2 = 0;
+            for (const cd &z : v) s2 += z * z;
+            const cd ph = std::polar(1.0, -0.5 * std::arg(s2));
+            double nn = 0;
+            for (const cd &z : v) nn += std::pow((z * ph).real(), 2);
+            nn = std::sqrt(nn);
+            for (int64_t r = 0; r < n; ++r) J[r * k + i] = (v[r] * ph).real() / nn;
+        }
+    }
+    if (stats) {
+        stats->restarts = restarts;
+        stats->inner_iterations = gm.iterations;
+        stats->products = prod.count;
+        stats->converged = converged ? 1 : 0;
+        stats->inner_converged = inner_ok ? 1 : 0;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!converged) return fail(MLFMA_ENOTCONV, "Arnoldi did not converge within max_restarts");
+    return MLFMA_OK;
+}

@@ -23,7 +23,9 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIM
 
 EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg_edges", "mlfma_matvec",
             "mlfma_matvec_adjoint", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
-            "mlfma_profile_stages", "mlfma_matvec_noalloc", "mlfma_destroy", "mlfma_last_error"]
+            "mlfma_profile_stages", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
+            "mlfma_destroy", "mlfma_last_error"]
+CM_ZINV_R, CM_XINV_R = 0, 1
 STAGE_COUNT = 71
 
 
@@ -36,6 +38,18 @@ class MlfmaError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("interp_order", ctypes.c_int), ("max_batch", ctypes.c_int), ("precisions", ctypes.c_int),
                 ("host_only", ctypes.c_int), ("device", ctypes.c_int), ("eta", ctypes.c_double)]
+
+
+class CmOpts(ctypes.Structure):
+    _fields_ = [("nev", ctypes.c_int), ("ncv", ctypes.c_int), ("op", ctypes.c_int), ("prec", ctypes.c_int),
+                ("tol", ctypes.c_double), ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
+                ("max_inner", ctypes.c_int), ("max_restarts", ctypes.c_int), ("use_sai", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
+class CmStats(ctypes.Structure):
+    _fields_ = [("restarts", ctypes.c_int), ("inner_iterations", ctypes.c_int64), ("products", ctypes.c_int64),
+                ("converged", ctypes.c_int), ("inner_converged", ctypes.c_int), ("seconds", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -76,6 +90,8 @@ def load(build_if_missing: bool = False):
         getattr(L, f).argtypes = [P, P, I, P, I64, I, P]
     L.mlfma_sync.argtypes = [P, P]
     L.mlfma_profile_stages.argtypes = [P, P, I, P, I64, I, P, P]
+    L.mlfma_cm_default_opts.argtypes = [ctypes.POINTER(CmOpts)]
+    L.cm_ira_solve.argtypes = [P, ctypes.POINTER(CmOpts), P, P, ctypes.POINTER(CmStats)]
     L.mlfma_plan_info.argtypes = [P, ctypes.POINTER(Info)]
     L.mlfma_export.argtypes = [P, I, I, P, I64, ctypes.POINTER(I64)]
     L.mlfma_destroy.argtypes = [P]
@@ -242,6 +258,24 @@ class MlfmaPlan:
             if ms[47 + l]:
                 out["down%d" % l] = ms[47 + l]
         return out
+
+    def cm_solve(self, nev=10, ncv=30, op=CM_ZINV_R, prec=FP32, tol=1e-8, gmres_tol=1e-6, gmres_restart=50,
+                 max_inner=2000, max_restarts=200, use_sai=True, seed=1412175602, vectors=True):
+        """Characteristic values nearest zero (and real currents) by IRA:
+        returns (lambda [nev], J [N, nev] or None, stats dict)."""
+        o = CmOpts()
+        _check(self._lib.mlfma_cm_default_opts(ctypes.byref(o)))
+        o.nev, o.ncv, o.op, o.prec = int(nev), int(ncv), int(op), int(prec)
+        o.tol, o.gmres_tol = float(tol), float(gmres_tol)
+        o.gmres_restart, o.max_inner, o.max_restarts = int(gmres_restart), int(max_inner), int(max_restarts)
+        o.use_sai, o.seed = 1 if use_sai else 0, int(seed)
+        lam = np.zeros(nev)
+        J = np.zeros((self.n, nev)) if vectors else None
+        st = CmStats()
+        _check(self._lib.cm_ira_solve(self._h, ctypes.byref(o), _np_ptr(lam), _np_ptr(J) if vectors else None,
+                                      ctypes.byref(st)))
+        stats = {f: getattr(st, f) for f, _ in CmStats._fields_}
+        return lam, J, stats
 
     def sync(self, stream=None):
         _check(self._lib.mlfma_sync(self._h, ctypes.c_void_p(stream or 0)))

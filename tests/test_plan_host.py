@@ -24,7 +24,7 @@ def test_library_exports_every_declared_symbol():
     import re
     import os
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "mlfma.h")).read()
-    declared = set(re.findall(r"^(?:mlfma_status|void|const char \*)\s*(mlfma_\w+)\(", hdr, re.M))
+    declared = set(re.findall(r"^(?:mlfma_status|void|const char \*)\s*((?:mlfma|cm)_\w+)\(", hdr, re.M))
     assert declared == set(M.EXPORTED)
     lib = ctypes.CDLL(M.library_path())
     for name in declared:
