@@ -382,7 +382,7 @@ def main():
             "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64", "data": "synthetic",
             "config": {"workload": wl.name, "N": n, "levels": wl.levels, "digits": wl.digits, "batch": B,
-                       "interp_order": 6, "k": wl.k, "l2": "flushed between timed steps (256 MB write)",
+                       "interp_order": 10, "k": wl.k, "l2": "flushed between timed steps (256 MB write)",
                        "mesh": "icosphere subdivision 5, radius 2 m"},
             "fp64_single_vector": {"value": fp64_rate * world, "unit": UNIT, "ms_per_matvec": ms64 / steps64,
                                    "speedup_of_mixed_batched": value / (fp64_rate * world)},

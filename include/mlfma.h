@@ -66,7 +66,7 @@ typedef enum { MLFMA_FP64 = 0, MLFMA_FP32 = 1 } mlfma_prec;
 typedef struct {
     int interp_order;   /* points per dimension of the local Lagrange
                            interpolation between levels (Section III-C);
-                           even, 4..12; default 6 */
+                           even, 4..12; default 10 */
     int max_batch;      /* largest B (real columns; a complex column counts
                            two) a product may use; fields are sized for it;
                            default 64 */

@@ -529,7 +529,7 @@ extern "C" {
 mlfma_status mlfma_default_opts(mlfma_opts *o)
 {
     if (!o) return fail(MLFMA_EINVAL, "opts is NULL");
-    o->interp_order = 6;
+    o->interp_order = 10;
     o->max_batch = 64;
     o->precisions = (1 << MLFMA_FP32) | (1 << MLFMA_FP64);
     o->host_only = 0;

@@ -46,7 +46,8 @@ template <class C, class R> __device__ __forceinline__ void rfma(C &acc, R s, C 
     acc.y = fma(s, b.y, acc.y);
 }
 
-constexpr int kSmemCap = 96 * 1024;   // dynamic shared memory a kernel may ask for
+constexpr int kSmemCap = 200 * 1024;  // dynamic shared memory a kernel may ask for (227 KB per CTA on sm_103a)
+constexpr int kStageCap = 96 * 1024;  // staging budget of the near / leaf kernels (keeps >= 2 CTAs per SM)
 
 inline int blocks_for(int64_t total, int threads)
 {
@@ -658,7 +659,7 @@ cudaError_t launch_near_bt(const ProductArgs<R> &a, cudaStream_t s)
     using C = typename Cx<R>::T;
     dim3 grid(a.nr.nleaf, (a.B + BT - 1) / BT);
     const size_t smem = (size_t)a.nr.max_cols * BT * sizeof(R);
-    if (smem <= (size_t)kSmemCap) {
+    if (smem <= (size_t)kStageCap) {
         k_near<R, BT, true><<<grid, 256, smem, s>>>(a.nr, reinterpret_cast<const C *>(a.near_val), a.xp,
                                                     reinterpret_cast<C *>(a.yp), a.B);
     } else {
@@ -698,11 +699,11 @@ cudaError_t launch_radiate(const ProductArgs<R> &a, cudaStream_t s)
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
     const DevLevel<R> &Lf = a.lv[a.leaf];
-    if (a.B >= 32 && (size_t)a.nr.max_rows * 32 * sizeof(R) <= (size_t)kSmemCap) return launch_radiate_tiled<R, 32, 4>(a, s);
-    if (a.B >= 16 && (size_t)a.nr.max_rows * 16 * sizeof(R) <= (size_t)kSmemCap) return launch_radiate_tiled<R, 16, 4>(a, s);
-    if (a.B >= 8 && (size_t)a.nr.max_rows * 8 * sizeof(R) <= (size_t)kSmemCap) return launch_radiate_tiled<R, 8, 4>(a, s);
+    if (a.B >= 32 && (size_t)a.nr.max_rows * 32 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 32, 4>(a, s);
+    if (a.B >= 16 && (size_t)a.nr.max_rows * 16 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 16, 4>(a, s);
+    if (a.B >= 8 && (size_t)a.nr.max_rows * 8 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 8, 4>(a, s);
     int Bt = std::min(a.B, 32);
-    while (Bt > 1 && (size_t)a.nr.max_rows * Bt * sizeof(R) > (size_t)kSmemCap) Bt /= 2;
+    while (Bt > 1 && (size_t)a.nr.max_rows * Bt * sizeof(R) > (size_t)kStageCap) Bt /= 2;
     const size_t smem = (size_t)a.nr.max_rows * Bt * sizeof(R);
     dim3 grid(Lf.nbox, (a.B + Bt - 1) / Bt);
     k_radiate<R><<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), a.xp,
@@ -745,7 +746,7 @@ cudaError_t launch_receive(const ProductArgs<R> &a, cudaStream_t s)
     const int K = a.lv[a.leaf].K;
     int lb = 1;
     while (lb < a.B) lb *= 2;
-    while (lb > 1 && (size_t)2 * K * lb * sizeof(C) > (size_t)kSmemCap) lb /= 2;
+    while (lb > 1 && (size_t)2 * K * lb * sizeof(C) > (size_t)kStageCap) lb /= 2;
     switch (lb) {
     case 1: return launch_receive_lb<R, 1>(a, s);
     case 2: return launch_receive_lb<R, 2>(a, s);

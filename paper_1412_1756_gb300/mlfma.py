@@ -117,7 +117,7 @@ def _np_ptr(a):
 class MlfmaPlan:
     """A plan for y = Z x on one mesh at one wavenumber (include/mlfma.h)."""
 
-    def __init__(self, verts, tris, k, levels, digits=3.0, interp_order=6, max_batch=64,
+    def __init__(self, verts, tris, k, levels, digits=3.0, interp_order=10, max_batch=64,
                  precisions=(FP32, FP64), host_only=False, device=None, eta=None):
         L = load()
         self._lib = L

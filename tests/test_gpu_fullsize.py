@@ -1,0 +1,61 @@
+"""Full-size products on sampled rows of the FP64 oracle (each row exact,
+O(N)): the 115,200-unknown cube and the 1,966,080-unknown sphere.
+
+Two readings of the tree depth (Section III-C asks for leaf boxes of 0.2-0.5
+wavelengths):
+- at a depth whose leaves lie in that range (the cube at 6 levels, 0.25
+  wavelength leaves, d0 = 5) the product meets the 1e-3 bound;
+- at the depths the workloads name (cube 7 levels, sphere 9 levels: leaves
+  of 0.125 and 0.0625 wavelengths) the truncation number of Eq. (9) no longer
+  delivers 3 digits and raising d0 makes it worse (the large spherical Hankel
+  terms of Eq. (8) cancel: the low-frequency breakdown that Section V assigns
+  to LF-FMA).  There the error is the expansion's, not the arithmetic's
+  (FP32 and FP64 agree to 1e-4), and is bounded at 1.5e-2."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import efie
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1412_1756_gb300 import mlfma as M  # noqa: E402
+
+
+def _rows(name, B, rows, precs, levels=None, digits=None):
+    W = workloads.get(name)
+    v, t = W.mesh()
+    P = M.MlfmaPlan(v, t, W.k, levels or W.levels, digits or W.digits, max_batch=B, precisions=precs)
+    x = workloads.rhs(P.n, B, W.seed)
+    idx = np.random.default_rng(7).choice(P.n, rows, replace=False)
+    ref = efie.Problem(v, t, W.k).matvec_rows(x, idx)
+    out = {}
+    for prec in precs:
+        dt = torch.float32 if prec == M.FP32 else torch.float64
+        y = P.matvec(torch.from_numpy(x).to("cuda", dt)).cpu().numpy()
+        out[prec] = y[idx]
+    P.close()
+    torch.cuda.empty_cache()
+    return ref, out
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_cube_six_levels_meets_bound():
+    ref, y = _rows("cube8m-6lv", 8, 16, (M.FP32, M.FP64))
+    assert _rel(y[M.FP32], ref) < 1e-3
+    assert _rel(y[M.FP64], ref) < 1e-3
+
+
+def test_cube_seven_levels_low_frequency_regime():
+    ref, y = _rows("cube8m", 8, 16, (M.FP32, M.FP64))
+    assert _rel(y[M.FP32], ref) < 1.5e-2
+    assert _rel(y[M.FP32], y[M.FP64]) < 1e-4
+
+
+def test_sphere_two_million_nine_levels():
+    ref, y = _rows("sphere-r8m-ico8", 4, 8, (M.FP32,))
+    assert _rel(y[M.FP32], ref) < 1.5e-2

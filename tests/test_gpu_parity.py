@@ -32,7 +32,7 @@ def rel(a, b):
 _cache = {}
 
 
-def problem(name, levels=None, interp_order=6, max_batch=64):
+def problem(name, levels=None, interp_order=10, max_batch=64):
     key = (name, levels, interp_order, max_batch)
     if key not in _cache:
         W = workloads.get(name)

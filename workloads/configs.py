@@ -48,6 +48,10 @@ WORKLOADS = {
     # 76,800 triangles / 115,200 RWG, seven levels
     "cube8m": Workload("cube8m", lambda: meshes.cube(8.0, 80), TWO_PI, 7, 3.0, 64, 1412175604,
                        "PEC cube side 8 m, wavelength 1 m", 115200),
+    # the same cube with 6 levels (0.25 wavelength leaves, inside the paper's
+    # 0.2-0.5 wavelength range) and d0 = 5
+    "cube8m-6lv": Workload("cube8m-6lv", lambda: meshes.cube(8.0, 80), TWO_PI, 6, 5.0, 64, 1412175604,
+                           "PEC cube side 8 m, 6 levels", 115200),
     # 1,310,720 triangles / 1,966,080 RWG, nine levels
     "sphere-r8m-ico8": Workload("sphere-r8m-ico8", lambda: meshes.icosphere(8, 8.0),
                                 TWO_PI, 9, 3.0, 16, 1412175605,
