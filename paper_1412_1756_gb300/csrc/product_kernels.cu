@@ -330,19 +330,65 @@ __global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B)
 }
 
 // ----------------------------------------------------------- upward ---
+// CP adjacent columns per thread (2 for FP32: one 16-byte shared-memory
+// access moves both).
+template <class R, int NB> struct ColPair { static constexpr int CP = (sizeof(R) == 4 && NB >= 2) ? 2 : 1; };
+
+template <class C, int CP>
+__device__ __forceinline__ void lds_cols(const C *p, C (&v)[CP])
+{
+    if constexpr (CP == 2) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = C{q.x, q.y};
+        v[1] = C{q.z, q.w};
+    } else {
+        v[0] = p[0];
+    }
+}
+template <class C, int CP>
+__device__ __forceinline__ void sts_cols(C *p, const C (&v)[CP])
+{
+    if constexpr (CP == 2) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    } else {
+        p[0] = v[0];
+    }
+}
+
+// Work split of a stencil step: items are (stencil row `key`, column group)
+// x chunks of the `span` rows the stencil row applies to; a thread loads an
+// item's taps into registers once and sweeps the chunk.  Threads loop over
+// items when there are more than the CTA has threads.
+struct Split {
+    int per, chunks, len, items;
+    __device__ Split(int keys, int span, int NL)
+    {
+        per = keys * NL;
+        chunks = max(1, (int)blockDim.x / per);
+        len = (span + chunks - 1) / chunks;
+        items = per * chunks;
+    }
+    __device__ void item(int it, int NL, int CP, int span, int &key, int &cg, int &lo, int &hi) const
+    {
+        key = (it % per) / NL;
+        cg = (it % NL) * CP;
+        lo = (it / per) * len;
+        hi = min(span, lo + len);
+    }
+};
+
 // One CTA per (parent box, component, chunk of NB columns, band of parent
-// theta rows).  Threads are (slot, column) with the column fastest, so each
-// packed stencil tap is one broadcast load shared by the NB column lanes and
-// shared-memory accesses are conflict-free.  Forward stencils have exactly
-// PO taps per row (the interpolation order), fully unrolled.  Per child:
-// its field -> shared memory (the next child's field is prefetched into
-// registers meanwhile), theta interpolation of the band's rows -> shared
-// memory, phi interpolation and phase shift accumulated into the band's
-// outputs in shared memory; one store of the parent field at the end.
+// theta rows).  Per child: its field -> shared memory (the next child's
+// field is prefetched into registers meanwhile), theta interpolation of the
+// band's rows -> shared memory, phi interpolation and phase shift
+// accumulated into the band's outputs in shared memory; one store of the
+// parent field at the end.  In each stencil step a thread holds the PO taps
+// of one stencil row in registers and applies them to a chunk of rows.
 template <class R, int NB, int PO>
 __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B, int RS)
 {
     using C = typename Cx<R>::T;
+    constexpr int CP = ColPair<R, NB>::CP, NL = NB / CP, PW = NB;
     constexpr int PF = 8;   // prefetch registers per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Kc = Ch.K, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph;
@@ -351,18 +397,20 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
     const int b0 = (blockIdx.z % nbc) * NB, rs = blockIdx.z / nbc;
     const int rows = (ntp + RS - 1) / RS, t0 = rs * rows, t1 = min(ntp, t0 + rows);
     if (t0 >= t1) return;
+    const int nr = t1 - t0;
+    const int nb = min(NB, B - b0);
     const int bb = threadIdx.x % NB, slot = threadIdx.x / NB, nslot = blockDim.x / NB;
-    const bool bok = b0 + bb < B;
-    const int nT = (t1 - t0) * nphc, nO = (t1 - t0) * nphp;
+    const bool bok = bb < nb;
+    const int nT = nr * nphc, nO = nr * nphp;
     C *A = reinterpret_cast<C *>(smem_raw);   // [Kc][NB]
-    C *T = A + (size_t)Kc * NB;                // [nT][NB]
-    C *O = T + (size_t)nT * NB;                // [nO][NB]
+    C *T = A + (size_t)Kc * PW;                // [nT][NB]
+    C *O = T + (size_t)nT * PW;                // [nO][NB]
     const C *S = reinterpret_cast<const C *>(Ch.S);
     const C *shift = reinterpret_cast<const C *>(P.shift) + (int64_t)t0 * nphp;
-    const Tap<R> *thu = P.thu + (size_t)t0 * PO;
-    for (int o = slot; o < nO; o += nslot) O[o * NB + bb] = C{0, 0};
+    for (int e = threadIdx.x; e < nO * PW; e += blockDim.x) O[e] = C{0, 0};
+    const Split st(nr, nphc, NL);      // theta step: key = band theta row, span = child phi index
+    const Split sp(nphp, nr, NL);      // phi step: key = parent phi index, span = band theta rows
     const int c0 = P.child_ptr[p], c1 = P.child_ptr[p + 1];
-    // rows q = slot + k * nslot of a child field; prefetch buffer for PF of them
     C pre[PF];
     auto fetch = [&](int c) {
         const C *src = S + ((int64_t)c * 2 + comp) * Kc * B + b0 + bb;
@@ -377,46 +425,82 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
 #pragma unroll
         for (int k = 0; k < PF; ++k) {
             const int q = slot + k * nslot;
-            if (q < Kc) A[q * NB + bb] = pre[k];
+            if (q < Kc) A[q * PW + bb] = pre[k];
         }
-        if (PF * nslot < Kc) {   // rows beyond the prefetch window
+        if (PF * nslot < Kc) {
             const C *src = S + ((int64_t)c * 2 + comp) * Kc * B + b0 + bb;
-            for (int q = slot + PF * nslot; q < Kc; q += nslot) A[q * NB + bb] = bok ? src[(int64_t)q * B] : C{0, 0};
+#pragma unroll 4
+            for (int q = slot + PF * nslot; q < Kc; q += nslot) A[q * PW + bb] = bok ? src[(int64_t)q * B] : C{0, 0};
         }
         __syncthreads();
         if (c + 1 < c1) fetch(c + 1);
-        for (int r = slot; r < nT; r += nslot) {
-            const int tr = r / nphc, v = r - tr * nphc;
-            const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
-            const Tap<R> *tp = thu + tr * PO;
-            C s{0, 0};
+        for (int it = threadIdx.x; it < st.items; it += blockDim.x) {
+            int key, cg, lo, hi;
+            st.item(it, NL, CP, nphc, key, cg, lo, hi);
+            int tb[PO];
+            bool rf[PO];
+            R tc[PO];
 #pragma unroll
             for (int f = 0; f < PO; ++f) {
-                const Tap<R> tap = tp[f];
-                const int j = tap.i & (kTapRefl - 1);
-                rfma(s, tap.c, A[(j * nphc + ((tap.i & kTapRefl) ? vs : v)) * NB + bb]);
+                const Tap<R> tap = P.thu[(size_t)(t0 + key) * PO + f];
+                tb[f] = (tap.i & (kTapRefl - 1)) * nphc;
+                rf[f] = (tap.i & kTapRefl) != 0;
+                tc[f] = tap.c;
             }
-            T[r * NB + bb] = s;
+            for (int v = lo; v < hi; ++v) {
+                const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
+                C s[CP];
+#pragma unroll
+                for (int k = 0; k < CP; ++k) s[k] = C{0, 0};
+#pragma unroll
+                for (int f = 0; f < PO; ++f) {
+                    C a[CP];
+                    lds_cols<C, CP>(A + (tb[f] + (rf[f] ? vs : v)) * PW + cg, a);
+#pragma unroll
+                    for (int k = 0; k < CP; ++k) rfma(s[k], tc[f], a[k]);
+                }
+                sts_cols<C, CP>(T + (key * nphc + v) * PW + cg, s);
+            }
         }
         __syncthreads();
         const C *sh = shift + (int64_t)Ch.octant[c] * P.K;
-        for (int o = slot; o < nO; o += nslot) {
-            const int tr = o / nphp, u = o - tr * nphp;
-            const C *trow = T + tr * nphc * NB + bb;
-            const Tap<R> *up = P.phu + u * PO;
-            C s{0, 0};
+        for (int it = threadIdx.x; it < sp.items; it += blockDim.x) {
+            int key, cg, lo, hi;
+            sp.item(it, NL, CP, nr, key, cg, lo, hi);
+            int pb[PO];
+            R pc[PO];
 #pragma unroll
             for (int f = 0; f < PO; ++f) {
-                const Tap<R> tap = up[f];
-                rfma(s, tap.c, trow[tap.i * NB]);
+                const Tap<R> tap = P.phu[(size_t)key * PO + f];
+                pb[f] = tap.i;
+                pc[f] = tap.c;
             }
-            cfma(O[o * NB + bb], sh[o], s);
+            for (int tr = lo; tr < hi; ++tr) {
+                const C *trow = T + tr * nphc * PW + cg;
+                C s[CP];
+#pragma unroll
+                for (int k = 0; k < CP; ++k) s[k] = C{0, 0};
+#pragma unroll
+                for (int f = 0; f < PO; ++f) {
+                    C a[CP];
+                    lds_cols<C, CP>(trow + pb[f] * PW, a);
+#pragma unroll
+                    for (int k = 0; k < CP; ++k) rfma(s[k], pc[f], a[k]);
+                }
+                const int o = tr * nphp + key;
+                const C z = sh[o];
+                C acc[CP];
+                lds_cols<C, CP>(O + o * PW + cg, acc);
+#pragma unroll
+                for (int k = 0; k < CP; ++k) cfma(acc[k], z, s[k]);
+                sts_cols<C, CP>(O + o * PW + cg, acc);
+            }
         }
         __syncthreads();
     }
     if (!bok) return;
     C *dst = reinterpret_cast<C *>(P.S) + (((int64_t)p * 2 + comp) * P.K + (int64_t)t0 * nphp) * B + b0 + bb;
-    for (int o = slot; o < nO; o += nslot) dst[(int64_t)o * B] = O[o * NB + bb];
+    for (int o = slot; o < nO; o += nslot) dst[(int64_t)o * B] = O[o * PW + bb];
 }
 
 // --------------------------------------------------------- downward ---
