@@ -29,12 +29,13 @@ def lib():
         i = ctypes.c_int
         d = ctypes.c_double
         L.oracle_zfill.argtypes = [i, P, i, P, i, P, P, P, d, d, P, i]
+        L.oracle_dzfill.argtypes = [i, P, i, P, i, P, P, P, d, d, P, i]
         L.oracle_zrows.argtypes = [i, P, i, P, i, P, P, P, d, d, i, P, P, i]
         L.oracle_tri_potential.argtypes = [i, P, i, P, P, i, d, i, P]
         L.oracle_static_potential.argtypes = [P, P, P, P, P]
         L.oracle_pair_is_singular.argtypes = [i, P, i, P, i, i]
         L.oracle_rule7.argtypes = [P]
-        for f in ("oracle_zfill", "oracle_zrows", "oracle_tri_potential",
+        for f in ("oracle_zfill", "oracle_dzfill", "oracle_zrows", "oracle_tri_potential",
                   "oracle_static_potential", "oracle_pair_is_singular", "oracle_rule7",
                   "oracle_num_threads"):
             getattr(L, f).restype = ctypes.c_int
@@ -71,6 +72,15 @@ class Problem:
         rc = lib().oracle_zfill(*self._mesh_args(), self.k, self.eta, _p(Z), int(nthreads))
         if rc != 0:
             raise MemoryError("oracle_zfill failed")
+        return Z
+
+    def dense_dk(self, nthreads: int = 0) -> np.ndarray:
+        """Dense symmetric dZ/dk [N, N] complex128 (Section II, Eq. (5)
+        differentiated in k with the quadrature fixed)."""
+        Z = np.zeros((self.n, self.n), dtype=np.complex128)
+        rc = lib().oracle_dzfill(*self._mesh_args(), self.k, self.eta, _p(Z), int(nthreads))
+        if rc != 0:
+            raise MemoryError("oracle_dzfill failed")
         return Z
 
     def rows(self, rows, nthreads: int = 0) -> np.ndarray:

@@ -321,6 +321,89 @@ static void rwg_from_args(rwg_t *B, int n, const int32_t *tri, const int32_t *vf
 }
 
 /*
+ * Ordered entry of dZ/dk.  With A = <f_i, g, f_j>, Phi = <div f_i, g, div f_j>
+ * (both as in Z, with the same singularity extraction) and the k-derivatives
+ * of the kernel, dg/dk = i exp(ikR) (bounded, plain seven-point rule):
+ *   Z = i k eta A - (i eta / k) Phi
+ *   dZ/dk = i eta A + i k eta A' + (i eta / k^2) Phi - (i eta / k) Phi'.
+ */
+static cplx dz_raw(const mesh_t *M, const rwg_t *B, int i, int j, double k, double eta)
+{
+    cplx A = 0.0, Phi = 0.0, Ad = 0.0, Phid = 0.0;
+    const double li = B->len[i], lj = B->len[j];
+    for (int a = 0; a < 2; ++a) {
+        const int t = B->tri[2 * i + a];
+        const double si = a == 0 ? 1.0 : -1.0;
+        const double *vi = M->V + 3 * B->vfree[2 * i + a];
+        const double At = M->area[t];
+        const double Di = si * li / At;
+        for (int b = 0; b < 2; ++b) {
+            const int s = B->tri[2 * j + b];
+            const double sj = b == 0 ? 1.0 : -1.0;
+            const double *vj = M->V + 3 * B->vfree[2 * j + b];
+            const double As = M->area[s];
+            const double Dj = sj * lj / As;
+            const int sing = pair_is_singular(M, t, s);
+            for (int q = 0; q < 7; ++q) {
+                const double *r = M->qp + 21 * t + 3 * q;
+                const double wo = At * Q7[q][3];
+                cplx P0, P1[3];
+                tri_potential(M, r, s, k, sing, &P0, P1);
+                cplx vec = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    const double fi = si * li / (2.0 * At) * (r[c] - vi[c]);
+                    vec += fi * (sj * lj / (2.0 * As) * (P1[c] - vj[c] * P0));
+                }
+                A += wo * vec;
+                Phi += wo * Di * Dj * P0;
+                /* derivative kernel i exp(ikR): smooth, plain rule */
+                for (int p = 0; p < 7; ++p) {
+                    const double *rp = M->qp + 21 * s + 3 * p;
+                    double d[3];
+                    sub3(r, rp, d);
+                    const cplx gd = I * cexp(I * k * norm3(d));
+                    const double wi = As * Q7[p][3];
+                    double ff = 0.0;
+                    for (int c = 0; c < 3; ++c)
+                        ff += (si * li / (2.0 * At) * (r[c] - vi[c])) * (sj * lj / (2.0 * As) * (rp[c] - vj[c]));
+                    Ad += wo * wi * ff * gd;
+                    Phid += wo * wi * Di * Dj * gd;
+                }
+            }
+        }
+    }
+    return I * eta * A + I * k * eta * Ad + I * eta / (k * k) * Phi - I * eta / k * Phid;
+}
+
+/* Dense symmetric dZ/dk [n][n] complex (interleaved), row-major. */
+int oracle_dzfill(int nv, const double *V, int nt, const int32_t *T,
+                  int n, const int32_t *tri, const int32_t *vfree, const double *len,
+                  double k, double eta, double *Z, int nthreads)
+{
+    (void)nv;
+    mesh_t M;
+    if (mesh_init(&M, nt, V, T)) return -1;
+    rwg_t B;
+    rwg_from_args(&B, n, tri, vfree, len);
+    cplx *Zc = (cplx *)Z;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            Zc[(size_t)i * n + j] = dz_raw(&M, &B, i, j, k, eta);
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            const cplx s = 0.5 * (Zc[(size_t)i * n + j] + Zc[(size_t)j * n + i]);
+            Zc[(size_t)i * n + j] = s;
+            Zc[(size_t)j * n + i] = s;
+        }
+    mesh_free(&M);
+    return 0;
+}
+
+/*
  * Dense symmetric Z [n][n] complex (interleaved re, im), row-major.
  */
 int oracle_zfill(int nv, const double *V, int nt, const int32_t *T,
