@@ -44,3 +44,28 @@ def cm_values_arnoldi(Z: np.ndarray, nev: int = 10, seed: int = 0) -> np.ndarray
                   return_eigenvectors=False)
     lam = (1.0 / mu).real
     return lam[np.argsort(np.abs(lam))]
+
+
+def cm_derivatives(Z: np.ndarray, dZ: np.ndarray, nev: int = 10):
+    """Characteristic values nearest zero and their wavenumber derivatives.
+
+    First-order perturbation of the pencil of Eq. (GEP), X J = lambda R J,
+    with R = -Re Z and X = Im Z: for an eigenpair (lambda, J),
+    d lambda / dk = J^T (X' - lambda R') J / (J^T R J), where R' = -Re dZ/dk
+    and X' = Im dZ/dk.  Returns (lambda, dlambda) sorted by |lambda|."""
+    R = -Z.real
+    X = Z.imag
+    Rd = -dZ.real
+    Xd = dZ.imag
+    mu, J = scipy.linalg.eig(R, X)
+    ok = np.isfinite(mu)
+    mu, J = mu[ok], J[:, ok]
+    idx = np.argsort(-np.abs(mu))[:nev]
+    lam = (1.0 / mu[idx]).real
+    J = J[:, idx].real
+    dl = np.empty(len(idx))
+    for m in range(len(idx)):
+        v = J[:, m]
+        dl[m] = (v @ (Xd @ v) - lam[m] * (v @ (Rd @ v))) / (v @ (R @ v))
+    order = np.argsort(np.abs(lam))
+    return lam[order], dl[order]
