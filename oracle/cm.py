@@ -46,25 +46,39 @@ def cm_values_arnoldi(Z: np.ndarray, nev: int = 10, seed: int = 0) -> np.ndarray
     return lam[np.argsort(np.abs(lam))]
 
 
-def cm_derivatives(Z: np.ndarray, dZ: np.ndarray, nev: int = 10):
+def cm_derivatives(Z: np.ndarray, dZ: np.ndarray, nev: int = 10, method: str = "dense", seed: int = 0):
     """Characteristic values nearest zero and their wavenumber derivatives.
 
     First-order perturbation of the pencil of Eq. (GEP), X J = lambda R J,
     with R = -Re Z and X = Im Z: for an eigenpair (lambda, J),
     d lambda / dk = J^T (X' - lambda R') J / (J^T R J), where R' = -Re dZ/dk
-    and X' = Im dZ/dk.  Returns (lambda, dlambda) sorted by |lambda|."""
+    and X' = Im dZ/dk.  The eigenpairs come from the dense pencil (method
+    "dense") or, with the same selection, from Arnoldi iteration on X^-1 R
+    as in ``cm_values_arnoldi`` ("arnoldi"; eigenvectors rotated to real).
+    Returns (lambda, dlambda) sorted by |lambda|."""
     R = -Z.real
     X = Z.imag
     Rd = -dZ.real
     Xd = dZ.imag
-    mu, J = scipy.linalg.eig(R, X)
-    ok = np.isfinite(mu)
-    mu, J = mu[ok], J[:, ok]
-    idx = np.argsort(-np.abs(mu))[:nev]
-    lam = (1.0 / mu[idx]).real
-    J = J[:, idx].real
-    dl = np.empty(len(idx))
-    for m in range(len(idx)):
+    if method == "dense":
+        mu, J = scipy.linalg.eig(R, X)
+        ok = np.isfinite(mu)
+        mu, J = mu[ok], J[:, ok]
+        idx = np.argsort(-np.abs(mu))[:nev]
+        mu, J = mu[idx], J[:, idx]
+    else:
+        import scipy.sparse.linalg as sla
+        lu = scipy.linalg.lu_factor(X)
+        n = Z.shape[0]
+        op = sla.LinearOperator((n, n), matvec=lambda v: scipy.linalg.lu_solve(lu, R @ v), dtype=np.float64)
+        v0 = np.random.Generator(np.random.PCG64(seed)).standard_normal(n)
+        mu, J = sla.eigs(op, k=nev, which="LM", v0=v0, ncv=max(2 * nev + 1, 40), tol=1e-12)
+        piv = np.argmax(np.abs(J), axis=0)
+        J = J * np.exp(-1j * np.angle(J[piv, np.arange(J.shape[1])]))
+    lam = (1.0 / mu).real
+    J = J.real
+    dl = np.empty(len(lam))
+    for m in range(len(lam)):
         v = J[:, m]
         dl[m] = (v @ (Xd @ v) - lam[m] * (v @ (Rd @ v))) / (v @ (R @ v))
     order = np.argsort(np.abs(lam))

@@ -31,11 +31,12 @@ def lib():
         L.oracle_zfill.argtypes = [i, P, i, P, i, P, P, P, d, d, P, i]
         L.oracle_dzfill.argtypes = [i, P, i, P, i, P, P, P, d, d, P, i]
         L.oracle_zrows.argtypes = [i, P, i, P, i, P, P, P, d, d, i, P, P, i]
+        L.oracle_dzrows.argtypes = [i, P, i, P, i, P, P, P, d, d, i, P, P, i]
         L.oracle_tri_potential.argtypes = [i, P, i, P, P, i, d, i, P]
         L.oracle_static_potential.argtypes = [P, P, P, P, P]
         L.oracle_pair_is_singular.argtypes = [i, P, i, P, i, i]
         L.oracle_rule7.argtypes = [P]
-        for f in ("oracle_zfill", "oracle_dzfill", "oracle_zrows", "oracle_tri_potential",
+        for f in ("oracle_zfill", "oracle_dzfill", "oracle_zrows", "oracle_dzrows", "oracle_tri_potential",
                   "oracle_static_potential", "oracle_pair_is_singular", "oracle_rule7",
                   "oracle_num_threads"):
             getattr(L, f).restype = ctypes.c_int
@@ -91,6 +92,16 @@ class Problem:
                                 _p(out), int(nthreads))
         if rc != 0:
             raise MemoryError("oracle_zrows failed")
+        return out
+
+    def rows_dk(self, rows, nthreads: int = 0) -> np.ndarray:
+        """Rows of the symmetric dZ/dk, complex128 [len(rows), N]."""
+        rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64).reshape(-1))
+        out = np.zeros((rows.shape[0], self.n), dtype=np.complex128)
+        rc = lib().oracle_dzrows(*self._mesh_args(), self.k, self.eta, rows.shape[0], _p(rows),
+                                 _p(out), int(nthreads))
+        if rc != 0:
+            raise MemoryError("oracle_dzrows failed")
         return out
 
     def matvec_rows(self, x: np.ndarray, rows, nthreads: int = 0) -> np.ndarray:

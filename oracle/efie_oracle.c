@@ -462,6 +462,31 @@ int oracle_zrows(int nv, const double *V, int nt, const int32_t *T,
     return 0;
 }
 
+/* Rows of the symmetric dZ/dk (each entry the mean of both orders, as in
+ * oracle_dzfill): out [nrows][n] complex. */
+int oracle_dzrows(int nv, const double *V, int nt, const int32_t *T,
+                  int n, const int32_t *tri, const int32_t *vfree, const double *len,
+                  double k, double eta, int nrows, const int64_t *rows, double *out, int nthreads)
+{
+    (void)nv;
+    mesh_t M;
+    if (mesh_init(&M, nt, V, T)) return -1;
+    rwg_t B;
+    rwg_from_args(&B, n, tri, vfree, len);
+    cplx *O = (cplx *)out;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16) collapse(2)
+#endif
+    for (int r = 0; r < nrows; ++r)
+        for (int j = 0; j < n; ++j) {
+            const int i = (int)rows[r];
+            O[(size_t)r * n + j] = 0.5 * (dz_raw(&M, &B, i, j, k, eta) + dz_raw(&M, &B, j, i, k, eta));
+        }
+    mesh_free(&M);
+    return 0;
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

@@ -96,20 +96,40 @@ def test_closed_form_derivative_against_central_differences():
             assert abs((lp - lm) / (2 * h) - d0) < 1e-6 * max(1.0, abs(d0))
 
 
-@pytest.mark.parametrize("level,tol", [(2, (0.05, 0.03, 0.16)), (3, (0.015, 0.01, 0.05))])
-def test_sphere_dlambda_dk_against_closed_form(level, tol):
+@pytest.mark.parametrize("level,tol,method", [(2, (0.05, 0.03, 0.16), "dense"),
+                                              (3, (0.015, 0.01, 0.05), "arnoldi")])
+def test_sphere_dlambda_dk_against_closed_form(level, tol, method):
     """Characteristic values of the sphere r = 0.5 m at ka = pi and their
     k-derivatives by first-order perturbation of Eq. (GEP) with the oracle's
     Z and dZ/dk; cluster means of TE1 (x3), TE2 (x5), TM3 (x7) against the
     closed form, within the mesh's discretisation error (which shrinks from
-    480 to 1,920 unknowns)."""
+    480 to 1,920 unknowns).  The two eigensolver routes must agree."""
     from oracle import cm
     a, k = 0.5, 2 * np.pi
     v, t = workloads.icosphere(level, a)
     P = efie.Problem(v, t, k)
-    lam, dl = cm.cm_derivatives(P.dense(), P.dense_dk(), 15)
+    lam, dl = cm.cm_derivatives(P.dense(), P.dense_dk(), 15, method=method)
     ref = _sphere_closed_form_dk(k * a, a)[:3]
     got = _cluster_means(lam, dl, [m for _, _, m in ref])
     for (l_ref, d_ref, _), (l_got, d_got), tl in zip(ref, got, tol):
         assert abs(d_got - d_ref) < tl * abs(d_ref), (d_got, d_ref)
         assert np.sign(l_got) == np.sign(l_ref)
+
+
+def test_dk_rows_equal_dense_rows():
+    v, t = workloads.icosphere(2, 0.5)
+    P = efie.Problem(v, t, 2 * np.pi)
+    D = P.dense_dk()
+    rows = [0, 7, 311, P.n - 1]
+    assert np.array_equal(P.rows_dk(rows), D[rows])
+
+
+def test_dlambda_dk_dense_and_arnoldi_agree():
+    from oracle import cm
+    v, t = workloads.icosphere(2, 0.5)
+    P = efie.Problem(v, t, 2 * np.pi)
+    Z, D = P.dense(), P.dense_dk()
+    l1, d1 = cm.cm_derivatives(Z, D, 8, method="dense")
+    l2, d2 = cm.cm_derivatives(Z, D, 8, method="arnoldi")
+    assert np.allclose(l1, l2, rtol=1e-8)
+    assert np.allclose(d1, d2, rtol=1e-6)
