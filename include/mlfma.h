@@ -140,6 +140,35 @@ mlfma_status mlfma_matvec_adjoint(mlfma_plan_t plan, const void *x, int x_is_com
                                   int64_t B, int prec, void *stream);
 
 /*
+ * y = (dZ/dk) x: the wavenumber derivative of the EFIE matrix of Section II,
+ * Eq. (5), applied through the multilevel product of Eq. (ZI), with the
+ * plan's quadrature, tree, sample grids, stencils and truncation numbers
+ * held fixed.  Near blocks: i eta (A + Phi/k^2) + i k eta (A' - Phi'/k^2),
+ * A and Phi the vector- and scalar-potential integrals of Z and A', Phi'
+ * those of dg/dk = i exp(ikR).  Far part: every stage of Eq. (ZI) carried as
+ * value and k-tangent (dual numbers): derivative patterns, shifts
+ * (i khat.d exp(i k khat.d)), translations (Eq. (8) with r h_l'(kr)) and
+ * the far constant (-2 k eta / 4 pi).
+ * Arguments, layouts and stream behaviour as mlfma_matvec, except that the
+ * fields carry 2 x the internal columns: B must satisfy 2 B <= max_batch
+ * (complex x: 4 B <= max_batch).  The first call in a precision builds the
+ * derivative tables (one FP64 near-field fill and two pattern tables; it
+ * allocates device memory and synchronises the device), so make it outside
+ * any stream capture; later calls replay a captured graph per column count.
+ * Errors: EINVAL (sizes, precision not set up, host-only plan), ENOMEM,
+ * ECUDA.
+ */
+mlfma_status mlfma_matvec_dk(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
+                             int64_t B, int prec, void *stream);
+
+/*
+ * y = (dZ/dk)^H x = conj((dZ/dk) conj(x)) (dZ/dk is symmetric like Z).
+ * Arguments as mlfma_matvec_dk.
+ */
+mlfma_status mlfma_matvec_dk_adjoint(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
+                                     int64_t B, int prec, void *stream);
+
+/*
  * y = Z x with HOST x and y (same layouts and types as mlfma_matvec): copies
  * x to the device, runs the product on `stream`, copies y back and waits for
  * the stream.  Uses the plan's own device staging buffers.

@@ -111,6 +111,11 @@ struct mlfma_plan_s {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (precision, columns) -> captured core
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;   // caller stream <-> plan streams
     StageClock clock;
+    // FP64 setup inputs kept for the derivative tables, built on first use
+    DevMesh dm;
+    const int32_t *d_ubox = nullptr;
+    const double *d_grid = nullptr, *d_bc = nullptr;
+    bool dk_ready[2] = {false, false};   // per precision
 };
 
 namespace {
@@ -283,6 +288,8 @@ mlfma_status setup_device(mlfma_plan_t p)
         const double *d_grid, *d_bc;
         CK(M.upload(grid, &d_grid), "upload grid");
         CK(M.upload(Lf.center, &d_bc), "upload centers");
+        p->d_grid = d_grid;
+        p->d_bc = d_bc;
         CK(M.alloc(&V64, (size_t)H.N * Lf.K * 2 * 16), "alloc patterns");
         CK(launch_leaf_patterns(dm, d_ubox, d_bc, Lf.K, d_grid, H.k, (double2 *)V64, 0), "leaf patterns");
     }
@@ -315,6 +322,8 @@ mlfma_status setup_device(mlfma_plan_t p)
             CK(M.upload(Lv.ph_dn.idx, &ip[15]), "upload stencils");
         }
     }
+    p->dm = dm;
+    p->d_ubox = d_ubox;
     const int prec = p->opts.precisions;
     if (prec & (1 << MLFMA_FP32)) {
         p->a32.nr = nr; p->a32.ubox = d_ubox; p->a32.perm = d_perm;
@@ -348,6 +357,71 @@ mlfma_status setup_device(mlfma_plan_t p)
     return MLFMA_OK;
 }
 
+// Tables of dZ/dk for one precision: near blocks (FP64 fill), derivative
+// patterns dV/dk and dV/dk + (2/k) V, and the derivatives of the translation
+// and shift tables.  Allocates; runs once per precision, outside any capture.
+template <class R>
+cudaError_t setup_dk(mlfma_plan_t p, ProductArgs<R> &a)
+{
+    PlanHost &H = p->host;
+    DevMem &M = p->mem;
+    cudaError_t e;
+    void *near64 = nullptr, *Vd64 = nullptr, *Wd64 = nullptr;
+    if ((e = M.alloc(&near64, (size_t)H.nnz * 16)) != cudaSuccess) return e;
+    if ((e = launch_near_fill_dk(p->dm, a.nr, H.k, H.eta, (double2 *)near64, 0)) != cudaSuccess) return e;
+    int64_t nv = 0;
+    if (H.leaf >= 2) {
+        const Level &Lf = H.lv[H.leaf];
+        nv = H.N * (int64_t)Lf.K * 2;
+        if ((e = M.alloc(&Vd64, (size_t)nv * 16)) != cudaSuccess) return e;
+        if ((e = M.alloc(&Wd64, (size_t)nv * 16)) != cudaSuccess) return e;
+        if ((e = launch_leaf_patterns(p->dm, p->d_ubox, p->d_bc, Lf.K, p->d_grid, H.k, (double2 *)Vd64, 0, 1)) !=
+            cudaSuccess)
+            return e;
+        if ((e = launch_leaf_patterns(p->dm, p->d_ubox, p->d_bc, Lf.K, p->d_grid, H.k, (double2 *)Wd64, 0, 2)) !=
+            cudaSuccess)
+            return e;
+    }
+    if (sizeof(R) == 8) {
+        a.near_dk = static_cast<const R *>(near64);
+        a.Vd = static_cast<const R *>(Vd64);
+        a.Wd = static_cast<const R *>(Wd64);
+    } else {
+        auto narrow = [&](void *src, int64_t n, const R **out) -> cudaError_t {
+            void *d;
+            cudaError_t e2 = M.alloc(&d, (size_t)n * 8);
+            if (e2 != cudaSuccess) return e2;
+            if ((e2 = launch_cast_c64_to_c32(static_cast<const double2 *>(src), static_cast<float2 *>(d), n, 0)) !=
+                cudaSuccess)
+                return e2;
+            *out = static_cast<const R *>(d);
+            return cudaSuccess;
+        };
+        if ((e = narrow(near64, H.nnz, &a.near_dk)) != cudaSuccess) return e;
+        if (H.leaf >= 2) {
+            if ((e = narrow(Vd64, nv, &a.Vd)) != cudaSuccess) return e;
+            if ((e = narrow(Wd64, nv, &a.Wd)) != cudaSuccess) return e;
+        }
+    }
+    for (int l = 2; l <= H.leaf; ++l) {
+        const Level &Lv = H.lv[l];
+        auto pairs = [](const std::vector<cd> &v) {
+            std::vector<R> t(2 * v.size());
+            for (size_t i = 0; i < v.size(); ++i) { t[2 * i] = (R)v[i].real(); t[2 * i + 1] = (R)v[i].imag(); }
+            return t;
+        };
+        if ((e = M.upload(pairs(Lv.alpha_dk), &a.lv[l].alpha_dk)) != cudaSuccess) return e;
+        if (l < H.leaf && (e = M.upload(pairs(Lv.shift_dk), &a.lv[l].shift_dk)) != cudaSuccess) return e;
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    if (sizeof(R) == 4) {
+        M.release(near64);
+        if (Vd64) M.release(Vd64);
+        if (Wd64) M.release(Wd64);
+    }
+    return cudaSuccess;
+}
+
 mlfma_status check_plan(mlfma_plan_t p)
 {
     if (!p) return fail(MLFMA_EINVAL, "plan is NULL");
@@ -371,9 +445,9 @@ void release_streams(mlfma_plan_t p)
 // The core pass (near field and far pass) for (precision, columns), captured
 // once into a CUDA graph on the plan's streams and replayed afterwards.
 template <class R>
-mlfma_status core_graph(mlfma_plan_t p, const ProductArgs<R> &a, int prec, cudaGraphExec_t *out)
+mlfma_status core_graph(mlfma_plan_t p, const ProductArgs<R> &a, int prec, int dk, cudaGraphExec_t *out)
 {
-    auto key = std::make_pair(prec, a.B);
+    auto key = std::make_pair(prec + 2 * dk, a.B);
     auto it = p->graphs.find(key);
     if (it != p->graphs.end()) {
         *out = it->second;
@@ -381,7 +455,7 @@ mlfma_status core_graph(mlfma_plan_t p, const ProductArgs<R> &a, int prec, cudaG
     }
     cudaError_t e = cudaStreamBeginCapture(p->cs.main, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
-    cudaError_t el = launch_core<R>(a, p->cs, nullptr);
+    cudaError_t el = dk ? launch_core_dk<R>(a, p->cs.main, nullptr) : launch_core<R>(a, p->cs, nullptr);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(p->cs.main, &g);
     if (el != cudaSuccess) {
@@ -400,7 +474,7 @@ mlfma_status core_graph(mlfma_plan_t p, const ProductArgs<R> &a, int prec, cudaG
 
 template <class R>
 mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int xc, void *yd, int Bu, int adjoint,
-                 cudaStream_t s, double *stage_ms)
+                 int dk, cudaStream_t s, double *stage_ms)
 {
     cudaError_t e;
     if (stage_ms) {
@@ -412,7 +486,8 @@ mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int
         if ((e = launch_prepare<R>(a, xd, xc, Bu, adjoint, s)) != cudaSuccess) return cuda_fail(e, "prepare");
         clk.stage[clk.n] = STAGE_PREPARE;
         if ((e = cudaEventRecord(clk.ev[clk.n++], s)) != cudaSuccess) return cuda_fail(e, "stage timer");
-        if ((e = launch_core<R>(a, serial, &clk)) != cudaSuccess) return cuda_fail(e, "core pass");
+        if ((e = dk ? launch_core_dk<R>(a, s, &clk) : launch_core<R>(a, serial, &clk)) != cudaSuccess)
+            return cuda_fail(e, "core pass");
         if ((e = launch_finalize<R>(a, yd, xc, Bu, adjoint, s)) != cudaSuccess) return cuda_fail(e, "finalize");
         clk.stage[clk.n] = STAGE_FINALIZE;
         if ((e = cudaEventRecord(clk.ev[clk.n++], s)) != cudaSuccess) return cuda_fail(e, "stage timer");
@@ -429,7 +504,7 @@ mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int
     }
     if ((e = launch_prepare<R>(a, xd, xc, Bu, adjoint, s)) != cudaSuccess) return cuda_fail(e, "prepare");
     cudaGraphExec_t ex;
-    mlfma_status st = core_graph<R>(p, a, prec, &ex);
+    mlfma_status st = core_graph<R>(p, a, prec, dk, &ex);
     if (st != MLFMA_OK) return st;
     if ((e = cudaGraphLaunch(ex, s)) != cudaSuccess) return cuda_fail(e, "graph launch");
     if ((e = launch_finalize<R>(a, yd, xc, Bu, adjoint, s)) != cudaSuccess) return cuda_fail(e, "finalize");
@@ -437,7 +512,7 @@ mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int
 }
 
 mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream, int adjoint,
-                     bool host, double *stage_ms = nullptr)
+                     bool host, double *stage_ms = nullptr, int dk = 0)
 {
     if (check_plan(p)) return MLFMA_EINVAL;
     if (!p->on_device) return fail(MLFMA_EINVAL, "plan was built host-only; products need a device plan");
@@ -446,10 +521,18 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
     if (B < 1) return fail(MLFMA_EINVAL, "B must be >= 1");
     const int64_t Bi = B * (xc ? 2 : 1);
     if (Bi > p->opts.max_batch) return fail(MLFMA_EINVAL, "B exceeds the plan's max_batch");
+    if (dk && 2 * Bi > p->opts.max_batch)
+        return fail(MLFMA_EINVAL, "dZ/dk products carry value and tangent fields: 2 x B (x2 for complex x) must not "
+                                  "exceed the plan's max_batch");
     if (prec != MLFMA_FP32 && prec != MLFMA_FP64) return fail(MLFMA_EINVAL, "unknown precision");
     if (prec == MLFMA_FP32 && !p->has32) return fail(MLFMA_EINVAL, "FP32 was not set up in this plan");
     if (prec == MLFMA_FP64 && !p->has64) return fail(MLFMA_EINVAL, "FP64 was not set up in this plan");
     DeviceGuard g(p->device);
+    if (dk && !p->dk_ready[prec]) {
+        cudaError_t e0 = prec == MLFMA_FP64 ? setup_dk<double>(p, p->a64) : setup_dk<float>(p, p->a32);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "dZ/dk tables");
+        p->dk_ready[prec] = true;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t rsz = prec == MLFMA_FP64 ? 8 : 4;
     const size_t xbytes = (size_t)p->host.N * B * (xc ? 2 : 1) * rsz;
@@ -467,11 +550,11 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
     if (prec == MLFMA_FP64) {
         ProductArgs<double> a = p->a64;
         a.B = (int)Bi;
-        st = run<double>(p, a, prec, xd, xc, yd, (int)B, adjoint, s, stage_ms);
+        st = run<double>(p, a, prec, xd, xc, yd, (int)B, adjoint, dk, s, stage_ms);
     } else {
         ProductArgs<float> a = p->a32;
         a.B = (int)Bi;
-        st = run<float>(p, a, prec, xd, xc, yd, (int)B, adjoint, s, stage_ms);
+        st = run<float>(p, a, prec, xd, xc, yd, (int)B, adjoint, dk, s, stage_ms);
     }
     if (st != MLFMA_OK) return st;
     if (host) {
@@ -613,6 +696,17 @@ mlfma_status mlfma_matvec_adjoint(mlfma_plan_t p, const void *x, int xc, void *y
 mlfma_status mlfma_matvec_host(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)
 {
     return product(p, x, xc, y, B, prec, stream, 0, true);
+}
+
+mlfma_status mlfma_matvec_dk(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)
+{
+    return product(p, x, xc, y, B, prec, stream, 0, false, nullptr, 1);
+}
+
+mlfma_status mlfma_matvec_dk_adjoint(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec,
+                                     void *stream)
+{
+    return product(p, x, xc, y, B, prec, stream, 1, false, nullptr, 1);
 }
 
 mlfma_status mlfma_profile_stages(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream,

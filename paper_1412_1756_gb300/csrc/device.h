@@ -50,10 +50,12 @@ struct DevLevel {
     const int16_t *grp_ty = nullptr;     // [entries][8]
     const int32_t *pchild_ptr = nullptr; // parent level's child ranges into this level
     const R *alpha = nullptr;            // [ntype][K][2]
+    const R *alpha_dk = nullptr;         // [ntype][K][2] d alpha / dk (derivative tables, when set up)
     const int32_t *parent = nullptr;     // [nbox] into level l-1
     const int32_t *octant = nullptr;     // [nbox]
     const int32_t *child_ptr = nullptr;  // [nbox+1] into level l+1
     const R *shift = nullptr;            // [8][K][2] (parents only)
+    const R *shift_dk = nullptr;         // [8][K][2] d shift / dk (parents only, when set up)
     // to children (parents only): up stencils rows = this level's nth / nph;
     // down stencils rows = child nth / nph
     const int32_t *thu_ptr = nullptr, *thu_idx = nullptr, *thu_refl = nullptr;
@@ -76,8 +78,13 @@ cudaError_t launch_mesh_geometry(const double *V, const int32_t *T, int nt, doub
                                  double *cen, double *hmax, cudaStream_t s);
 cudaError_t launch_near_fill(const DevMesh &m, const DevNear &nr, double k, double eta, double2 *val,
                              cudaStream_t s);
+// near blocks of dZ/dk in the strip layout of launch_near_fill
+cudaError_t launch_near_fill_dk(const DevMesh &m, const DevNear &nr, double k, double eta, double2 *val,
+                                cudaStream_t s);
+// mode 0: patterns V; 1: dV/dk; 2: dV/dk + (2/k) V
 cudaError_t launch_leaf_patterns(const DevMesh &m, const int32_t *ubox, const double *box_center, int K,
-                                 const double *grid /* [K][9]: khat, theta-hat, phi-hat */, double k, double2 *V, cudaStream_t s);
+                                 const double *grid /* [K][9]: khat, theta-hat, phi-hat */, double k, double2 *V, cudaStream_t s,
+                                 int mode = 0);
 cudaError_t launch_cast_c64_to_c32(const double2 *src, float2 *dst, int64_t n, cudaStream_t s);
 
 // ------------------------------------------------------------ product ---
@@ -89,6 +96,10 @@ struct ProductArgs {
     DevNear nr;
     const R *near_val = nullptr;    // complex, strip layout
     const R *V = nullptr;           // leaf patterns [N][K][2] complex
+    // derivative tables (set up on the first dZ/dk product in this precision)
+    const R *near_dk = nullptr;     // near blocks of dZ/dk, strip layout
+    const R *Vd = nullptr;          // dV/dk [N][K][2]
+    const R *Wd = nullptr;          // dV/dk + (2/k) V [N][K][2]
     const int32_t *ubox = nullptr;  // [N] leaf box of each leaf-order unknown
     const int64_t *perm = nullptr;  // [N]
     R *xp = nullptr;                // [N][B] real
@@ -135,5 +146,11 @@ cudaError_t launch_finalize(const ProductArgs<R> &a, void *y_user, int x_complex
 // branches on the three streams, joined back into cs.main.
 template <class R>
 cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClock *clk);
+// (dZ/dk) x into a.yp: the near blocks of dZ/dk, and the far pass carried as
+// value and k-tangent side by side (fields hold 2 a.B columns: value in
+// [0, a.B), tangent in [a.B, 2 a.B)); on one stream, an event per stage
+// with clk.
+template <class R>
+cudaError_t launch_core_dk(const ProductArgs<R> &a, cudaStream_t s, StageClock *clk);
 
 }  // namespace mlfma

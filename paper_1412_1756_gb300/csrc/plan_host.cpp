@@ -229,28 +229,36 @@ static void khat(const Level &Lv, int q, double *kh)
     kh[2] = Lv.ct[it];
 }
 
-// Eq. (8): alpha(khat, r) = sum_{l=0}^{L} i^l (2l+1) h_l^(1)(k r) P_l(khat . rhat)
+// Eq. (8): alpha(khat, r) = sum_{l=0}^{L} i^l (2l+1) h_l^(1)(k r) P_l(khat . rhat),
+// and its k-derivative with the samples and L fixed: r h_l^(1)'(k r) in place
+// of h_l^(1)(k r), where h_0' = -h_1 and h_l' = h_{l-1} - (l+1)/x h_l.
 static void translation_table(Level &Lv, double k)
 {
     Lv.alpha.assign((size_t)Lv.ntype * Lv.K, cd(0, 0));
-    std::vector<double> jn, yn, P(Lv.L + 1);
+    Lv.alpha_dk.assign((size_t)Lv.ntype * Lv.K, cd(0, 0));
+    std::vector<double> jn, yn, jd, yd, P(Lv.L + 1);
     for (int t = 0; t < Lv.ntype; ++t) {
         double r[3] = {Lv.a * Lv.type_off[3 * t], Lv.a * Lv.type_off[3 * t + 1], Lv.a * Lv.type_off[3 * t + 2]};
         double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
         double x = k * rn;
         sph_bessel_j(Lv.L, x, jn);
         sph_bessel_y(Lv.L, x, yn);
-        std::vector<cd> coef(Lv.L + 1);
+        sph_bessel_j(Lv.L + 1, x, jd);
+        sph_bessel_y(Lv.L + 1, x, yd);
+        std::vector<cd> coef(Lv.L + 1), coefd(Lv.L + 1);
         cd il(1, 0);
         for (int n = 0; n <= Lv.L; ++n) {
             coef[n] = il * (2.0 * n + 1.0) * cd(jn[n], yn[n]);
+            const cd hd = n == 0 ? -cd(jd[1], yd[1])
+                                 : cd(jd[n - 1], yd[n - 1]) - (n + 1.0) / x * cd(jd[n], yd[n]);
+            coefd[n] = il * (2.0 * n + 1.0) * rn * hd;
             il *= cd(0, 1);
         }
         for (int q = 0; q < Lv.K; ++q) {
             double kh[3];
             khat(Lv, q, kh);
             double c = (kh[0] * r[0] + kh[1] * r[1] + kh[2] * r[2]) / rn;
-            cd s(0, 0);
+            cd s(0, 0), sd(0, 0);
             double p0 = 1.0, p1 = c;
             for (int n = 0; n <= Lv.L; ++n) {
                 double pn;
@@ -262,8 +270,10 @@ static void translation_table(Level &Lv, double k)
                     p1 = pn;
                 }
                 s += coef[n] * pn;
+                sd += coefd[n] * pn;
             }
             Lv.alpha[(size_t)t * Lv.K + q] = s;
+            Lv.alpha_dk[(size_t)t * Lv.K + q] = sd;
         }
     }
 }
@@ -546,14 +556,17 @@ std::string build_plan_host(PlanHost &P, const double *verts, int64_t nv, const 
         transpose_stencil(Pa.ph_up, C.nph, [&](int, int) { return phr; }, Pa.ph_dn);
         transpose_stencil(Pa.th_up, C.nth, [&](int t, int j) { return Pa.wt[t] / C.wt[j]; }, Pa.th_dn);
         Pa.shift.resize((size_t)8 * Pa.K);
+        Pa.shift_dk.resize((size_t)8 * Pa.K);
         for (int o = 0; o < 8; ++o) {
             const double h = 0.5 * C.a;
             double d[3] = {-h * (((o >> 2) & 1) ? 1 : -1), -h * (((o >> 1) & 1) ? 1 : -1), -h * ((o & 1) ? 1 : -1)};
             for (int q = 0; q < Pa.K; ++q) {
                 double kh[3];
                 khat(Pa, q, kh);
-                double ph = k * (kh[0] * d[0] + kh[1] * d[1] + kh[2] * d[2]);
+                const double kd = kh[0] * d[0] + kh[1] * d[1] + kh[2] * d[2];
+                double ph = k * kd;
                 Pa.shift[(size_t)o * Pa.K + q] = cd(std::cos(ph), std::sin(ph));
+                Pa.shift_dk[(size_t)o * Pa.K + q] = cd(0.0, kd) * cd(std::cos(ph), std::sin(ph));
             }
         }
     }

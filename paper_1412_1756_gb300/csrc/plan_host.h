@@ -51,8 +51,10 @@ struct Level {
     std::vector<int32_t> type_off;  // [ntype][3]
     int ntype = 0;
     std::vector<cd> alpha;          // [ntype][K]
+    std::vector<cd> alpha_dk;       // [ntype][K]: d alpha / dk
     // to/from children (2 <= l < leaf)
     std::vector<cd> shift;          // [8][K]: exp(i k khat.(r_parent - r_child))
+    std::vector<cd> shift_dk;       // [8][K]: d shift / dk = i khat.(r_parent - r_child) shift
     Stencil th_up, ph_up;           // child grid -> this grid (rows: nth / nph of this level)
     Stencil ph_dn, th_dn;           // weighted transposes (rows: child nph / child nth)
     int nbox() const { return (int)code.size(); }

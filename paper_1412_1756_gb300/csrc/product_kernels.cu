@@ -197,7 +197,7 @@ template <class R>
 __global__ void __launch_bounds__(256) k_radiate(const int32_t *__restrict__ box_ptr,
                                                  const typename Cx<R>::T4 *__restrict__ V4,
                                                  const R *__restrict__ xp, typename Cx<R>::T *__restrict__ S,
-                                                 int K, int B, int Bt)
+                                                 int K, int B, int Bt, int Bs)
 {
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(256) k_radiate(const int32_t *__restrict__ box
             a1.x = fma(v.z, xv, a1.x);
             a1.y = fma(v.w, xv, a1.y);
         }
-        S[((int64_t)(box * 2 + 0) * K + q) * B + b0 + bb] = a0;
-        S[((int64_t)(box * 2 + 1) * K + q) * B + b0 + bb] = a1;
+        S[((int64_t)(box * 2 + 0) * K + q) * Bs + b0 + bb] = a0;
+        S[((int64_t)(box * 2 + 1) * K + q) * Bs + b0 + bb] = a1;
     }
 }
 
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256) k_radiate(const int32_t *__restrict__ box
 // level has too few outputs to fill the GPU).  All children's accumulators
 // live in registers.
 template <class R, int ES, int CB>
-__global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B)
+__global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B, int Bs, int accumulate)
 {
     using C = typename Cx<R>::T;
     __shared__ int s_src[216];
@@ -272,8 +272,8 @@ __global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B)
     for (int c = 0; c < 8; ++c)
 #pragma unroll
         for (int k = 0; k < CB; ++k) acc[c][0][k] = acc[c][1][k] = C{0, 0};
-    const int64_t KB = (int64_t)K * B;
-    const int64_t qb = (int64_t)q * B + b;
+    const int64_t KB = (int64_t)K * Bs;
+    const int64_t qb = (int64_t)q * Bs + b;
     if (valid) {
 #pragma unroll 2
         for (int e = part; e < ne; e += ES) {
@@ -323,8 +323,16 @@ __global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B)
             const int64_t o = (int64_t)(m0 + c) * 2 * KB + qb;
 #pragma unroll
             for (int k = 0; k < CB; ++k) {
-                G[o + k] = acc[c][0][k];
-                G[o + KB + k] = acc[c][1][k];
+                if (accumulate) {
+                    C g0 = G[o + k], g1 = G[o + KB + k];
+                    g0.x += acc[c][0][k].x; g0.y += acc[c][0][k].y;
+                    g1.x += acc[c][1][k].x; g1.y += acc[c][1][k].y;
+                    G[o + k] = g0;
+                    G[o + KB + k] = g1;
+                } else {
+                    G[o + k] = acc[c][0][k];
+                    G[o + KB + k] = acc[c][1][k];
+                }
             }
         }
 }
@@ -385,7 +393,7 @@ struct Split {
 // parent field at the end.  In each stencil step a thread holds the PO taps
 // of one stencil row in registers and applies them to a chunk of rows.
 template <class R, int NB, int PO>
-__global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B, int RS)
+__global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B, int RS, int Bs, int accumulate)
 {
     using C = typename Cx<R>::T;
     constexpr int CP = ColPair<R, NB>::CP, NL = NB / CP, PW = NB;
@@ -413,11 +421,11 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
     const int c0 = P.child_ptr[p], c1 = P.child_ptr[p + 1];
     C pre[PF];
     auto fetch = [&](int c) {
-        const C *src = S + ((int64_t)c * 2 + comp) * Kc * B + b0 + bb;
+        const C *src = S + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + bb;
 #pragma unroll
         for (int k = 0; k < PF; ++k) {
             const int q = slot + k * nslot;
-            pre[k] = (bok && q < Kc) ? src[(int64_t)q * B] : C{0, 0};
+            pre[k] = (bok && q < Kc) ? src[(int64_t)q * Bs] : C{0, 0};
         }
     };
     fetch(c0);
@@ -428,9 +436,9 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
             if (q < Kc) A[q * PW + bb] = pre[k];
         }
         if (PF * nslot < Kc) {
-            const C *src = S + ((int64_t)c * 2 + comp) * Kc * B + b0 + bb;
+            const C *src = S + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + bb;
 #pragma unroll 4
-            for (int q = slot + PF * nslot; q < Kc; q += nslot) A[q * PW + bb] = bok ? src[(int64_t)q * B] : C{0, 0};
+            for (int q = slot + PF * nslot; q < Kc; q += nslot) A[q * PW + bb] = bok ? src[(int64_t)q * Bs] : C{0, 0};
         }
         __syncthreads();
         if (c + 1 < c1) fetch(c + 1);
@@ -499,8 +507,18 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
         __syncthreads();
     }
     if (!bok) return;
-    C *dst = reinterpret_cast<C *>(P.S) + (((int64_t)p * 2 + comp) * P.K + (int64_t)t0 * nphp) * B + b0 + bb;
-    for (int o = slot; o < nO; o += nslot) dst[(int64_t)o * B] = O[o * PW + bb];
+    C *dst = reinterpret_cast<C *>(P.S) + (((int64_t)p * 2 + comp) * P.K + (int64_t)t0 * nphp) * Bs + b0 + bb;
+    if (accumulate) {
+        for (int o = slot; o < nO; o += nslot) {
+            C y = dst[(int64_t)o * Bs];
+            const C d = O[o * PW + bb];
+            y.x += d.x;
+            y.y += d.y;
+            dst[(int64_t)o * Bs] = y;
+        }
+    } else {
+        for (int o = slot; o < nO; o += nslot) dst[(int64_t)o * Bs] = O[o * PW + bb];
+    }
 }
 
 // --------------------------------------------------------- downward ---
@@ -508,7 +526,7 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
 // times the conjugate shift -> shared memory, phi anterpolation -> shared
 // memory, theta anterpolation added into the child's incoming field.
 template <class R, int NB>
-__global__ void __launch_bounds__(256) k_down(DevLevel<R> P, DevLevel<R> Ch, int B)
+__global__ void __launch_bounds__(256) k_down(DevLevel<R> P, DevLevel<R> Ch, int B, int Bs)
 {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -520,11 +538,11 @@ __global__ void __launch_bounds__(256) k_down(DevLevel<R> P, DevLevel<R> Ch, int
     C *H = reinterpret_cast<C *>(smem_raw);   // [Kp][NB]
     C *U = H + (size_t)Kp * NB;                // [ntp * nphc][NB]
     const int par = Ch.parent[c];
-    const C *g = reinterpret_cast<const C *>(P.G) + ((int64_t)par * 2 + comp) * Kp * B + b0 + bb;
+    const C *g = reinterpret_cast<const C *>(P.G) + ((int64_t)par * 2 + comp) * Kp * Bs + b0 + bb;
     const C *sh = reinterpret_cast<const C *>(P.shift) + (int64_t)Ch.octant[c] * Kp;
     for (int q = slot; q < Kp; q += nslot) {
         C h{0, 0};
-        if (bok) cfmac(h, sh[q], g[(int64_t)q * B]);
+        if (bok) cfmac(h, sh[q], g[(int64_t)q * Bs]);
         H[q * NB + bb] = h;
     }
     __syncthreads();
@@ -541,18 +559,18 @@ __global__ void __launch_bounds__(256) k_down(DevLevel<R> P, DevLevel<R> Ch, int
     }
     __syncthreads();
     if (!bok) return;
-    C *dst = reinterpret_cast<C *>(Ch.G) + ((int64_t)c * 2 + comp) * Kc * B + b0 + bb;
+    C *dst = reinterpret_cast<C *>(Ch.G) + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + bb;
     for (int q = slot; q < Kc; q += nslot) {
         const int j = q / nphc, v = q - j * nphc;
         const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
-        C s = dst[(int64_t)q * B];
+        C s = dst[(int64_t)q * Bs];
 #pragma unroll 4
         for (int f = P.thd_ptr[j]; f < P.thd_ptr[j + 1]; ++f) {
             const Tap<R> tap = P.thd[f];
             const int t = tap.i & (kTapRefl - 1);
             rfma(s, tap.c, U[(t * nphc + ((tap.i & kTapRefl) ? vs : v)) * NB + bb]);
         }
-        dst[(int64_t)q * B] = s;
+        dst[(int64_t)q * Bs] = s;
     }
 }
 
@@ -564,7 +582,7 @@ __global__ void __launch_bounds__(256) k_down(DevLevel<R> P, DevLevel<R> Ch, int
 template <class R, int LB>
 __global__ void __launch_bounds__(256) k_receive(const int32_t *__restrict__ box_ptr,
                                                  const typename Cx<R>::T4 *__restrict__ V4, DevLevel<R> lf,
-                                                 typename Cx<R>::T *__restrict__ yp, int B)
+                                                 typename Cx<R>::T *__restrict__ yp, int B, int Bs)
 {
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
@@ -575,10 +593,10 @@ __global__ void __launch_bounds__(256) k_receive(const int32_t *__restrict__ box
     const int box = blockIdx.x;
     const int b0 = blockIdx.y * LB;
     const int nb = min(LB, B - b0);
-    const C *G = reinterpret_cast<const C *>(lf.G) + (int64_t)box * 2 * K * B + b0;
+    const C *G = reinterpret_cast<const C *>(lf.G) + (int64_t)box * 2 * K * Bs + b0;
     for (int e = threadIdx.x; e < 2 * K * LB; e += blockDim.x) {
         const int bb = e % LB;
-        Gs[e] = bb < nb ? G[(int64_t)(e / LB) * B + bb] : C{0, 0};
+        Gs[e] = bb < nb ? G[(int64_t)(e / LB) * Bs + bb] : C{0, 0};
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -614,9 +632,9 @@ __global__ void __launch_bounds__(256) k_receive(const int32_t *__restrict__ box
 // memory; thread (row group, column) accumulates the rows i = group + k *
 // groups of its column in registers.
 template <class R, int NB, int MAXR>
-__global__ void __launch_bounds__(256) k_receive_tiled(const int32_t *__restrict__ box_ptr,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) k_receive_tiled(const int32_t *__restrict__ box_ptr,
                                                        const typename Cx<R>::T4 *__restrict__ V4, DevLevel<R> lf,
-                                                       typename Cx<R>::T *__restrict__ yp, int B)
+                                                       typename Cx<R>::T *__restrict__ yp, int B, int Bs)
 {
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
@@ -632,7 +650,7 @@ __global__ void __launch_bounds__(256) k_receive_tiled(const int32_t *__restrict
     const int bb = threadIdx.x % NB, grp = threadIdx.x / NB;
     const bool bok = b0 + bb < B;
     const int i0 = box_ptr[box], nrows = box_ptr[box + 1] - i0;
-    const C *G = reinterpret_cast<const C *>(lf.G) + (int64_t)box * 2 * K * B + b0;
+    const C *G = reinterpret_cast<const C *>(lf.G) + (int64_t)box * 2 * K * Bs + b0;
     for (int r0 = 0; r0 < nrows; r0 += NG * MAXR) {
         const int nr = min(NG * MAXR, nrows - r0);
         C acc[MAXR];
@@ -642,7 +660,7 @@ __global__ void __launch_bounds__(256) k_receive_tiled(const int32_t *__restrict
             const int nq = min(QT, K - q0);
             for (int e = threadIdx.x; e < 2 * QT * NB; e += blockDim.x) {
                 const int b = e % NB, q = (e / NB) % QT, cmp = e / (NB * QT);
-                Gs[e] = (q < nq && b0 + b < B) ? G[((int64_t)cmp * K + q0 + q) * B + b] : C{0, 0};
+                Gs[e] = (q < nq && b0 + b < B) ? G[((int64_t)cmp * K + q0 + q) * Bs + b] : C{0, 0};
             }
             for (int e = threadIdx.x; e < nr * QT; e += blockDim.x) {
                 const int r = e / QT, q = e % QT;
@@ -690,7 +708,7 @@ template <class R, int NB, int QB>
 __global__ void __launch_bounds__(256) k_radiate_tiled(const int32_t *__restrict__ box_ptr,
                                                        const typename Cx<R>::T4 *__restrict__ V4,
                                                        const R *__restrict__ xp, typename Cx<R>::T *__restrict__ S,
-                                                       int K, int B)
+                                                       int K, int B, int Bs)
 {
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
@@ -729,8 +747,8 @@ __global__ void __launch_bounds__(256) k_radiate_tiled(const int32_t *__restrict
 #pragma unroll
             for (int k = 0; k < QB; ++k)
                 if (qs + k < K) {
-                    S[((int64_t)(box * 2 + 0) * K + qs + k) * B + b0 + bb] = a0[k];
-                    S[((int64_t)(box * 2 + 1) * K + qs + k) * B + b0 + bb] = a1[k];
+                    S[((int64_t)(box * 2 + 0) * K + qs + k) * Bs + b0 + bb] = a0[k];
+                    S[((int64_t)(box * 2 + 1) * K + qs + k) * Bs + b0 + bb] = a1[k];
                 }
         }
     }
@@ -764,7 +782,7 @@ cudaError_t launch_near(const ProductArgs<R> &a, cudaStream_t s)
 }
 
 template <class R, int NB, int QB>
-cudaError_t launch_radiate_tiled(const ProductArgs<R> &a, cudaStream_t s)
+cudaError_t launch_radiate_tiled(const ProductArgs<R> &a, int Bs, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
@@ -773,30 +791,31 @@ cudaError_t launch_radiate_tiled(const ProductArgs<R> &a, cudaStream_t s)
     if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
     dim3 grid(Lf.nbox, (a.B + NB - 1) / NB);
     k_radiate_tiled<R, NB, QB><<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), a.xp,
-                                                       reinterpret_cast<C *>(Lf.S), Lf.K, a.B);
+                                                       reinterpret_cast<C *>(Lf.S), Lf.K, a.B, Bs);
     return cudaGetLastError();
 }
 
+// Bs: row stride of the outgoing field in columns (>= a.B)
 template <class R>
-cudaError_t launch_radiate(const ProductArgs<R> &a, cudaStream_t s)
+cudaError_t launch_radiate(const ProductArgs<R> &a, int Bs, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
     const DevLevel<R> &Lf = a.lv[a.leaf];
-    if (a.B >= 32 && (size_t)a.nr.max_rows * 32 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 32, 4>(a, s);
-    if (a.B >= 16 && (size_t)a.nr.max_rows * 16 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 16, 4>(a, s);
-    if (a.B >= 8 && (size_t)a.nr.max_rows * 8 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 8, 4>(a, s);
+    if (a.B >= 32 && (size_t)a.nr.max_rows * 32 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 32, 4>(a, Bs, s);
+    if (a.B >= 16 && (size_t)a.nr.max_rows * 16 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 16, 4>(a, Bs, s);
+    if (a.B >= 8 && (size_t)a.nr.max_rows * 8 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 8, 4>(a, Bs, s);
     int Bt = std::min(a.B, 32);
     while (Bt > 1 && (size_t)a.nr.max_rows * Bt * sizeof(R) > (size_t)kStageCap) Bt /= 2;
     const size_t smem = (size_t)a.nr.max_rows * Bt * sizeof(R);
     dim3 grid(Lf.nbox, (a.B + Bt - 1) / Bt);
     k_radiate<R><<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), a.xp,
-                                         reinterpret_cast<C *>(Lf.S), Lf.K, a.B, Bt);
+                                         reinterpret_cast<C *>(Lf.S), Lf.K, a.B, Bt, Bs);
     return cudaGetLastError();
 }
 
 template <class R, int LB>
-cudaError_t launch_receive_lb(const ProductArgs<R> &a, cudaStream_t s)
+cudaError_t launch_receive_lb(const ProductArgs<R> &a, int Bs, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
@@ -804,43 +823,44 @@ cudaError_t launch_receive_lb(const ProductArgs<R> &a, cudaStream_t s)
     dim3 grid(Lf.nbox, (a.B + LB - 1) / LB);
     const size_t smem = (size_t)2 * Lf.K * LB * sizeof(C);
     k_receive<R, LB><<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), Lf,
-                                             reinterpret_cast<C *>(a.yp), a.B);
+                                             reinterpret_cast<C *>(a.yp), a.B, Bs);
     return cudaGetLastError();
 }
 
 template <class R, int NB>
-cudaError_t launch_receive_tiled(const ProductArgs<R> &a, cudaStream_t s)
+cudaError_t launch_receive_tiled(const ProductArgs<R> &a, int Bs, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
     const DevLevel<R> &Lf = a.lv[a.leaf];
     dim3 grid(Lf.nbox, (a.B + NB - 1) / NB);
     k_receive_tiled<R, NB, NB / 4><<<grid, 256, 0, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), Lf,
-                                                        reinterpret_cast<C *>(a.yp), a.B);
+                                                        reinterpret_cast<C *>(a.yp), a.B, Bs);
     return cudaGetLastError();
 }
 
+// Bs: row stride of the incoming field in columns (>= a.B)
 template <class R>
-cudaError_t launch_receive(const ProductArgs<R> &a, cudaStream_t s)
+cudaError_t launch_receive(const ProductArgs<R> &a, int Bs, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
-    if (a.B >= 32 && sizeof(R) == 4) return launch_receive_tiled<R, 32>(a, s);
-    if (a.B >= 16) return launch_receive_tiled<R, 16>(a, s);
-    if (a.B >= 8) return launch_receive_tiled<R, 8>(a, s);
+    if (a.B >= 32 && sizeof(R) == 4) return launch_receive_tiled<R, 32>(a, Bs, s);
+    if (a.B >= 16) return launch_receive_tiled<R, 16>(a, Bs, s);
+    if (a.B >= 8) return launch_receive_tiled<R, 8>(a, Bs, s);
     const int K = a.lv[a.leaf].K;
     int lb = 1;
     while (lb < a.B) lb *= 2;
     while (lb > 1 && (size_t)2 * K * lb * sizeof(C) > (size_t)kStageCap) lb /= 2;
     switch (lb) {
-    case 1: return launch_receive_lb<R, 1>(a, s);
-    case 2: return launch_receive_lb<R, 2>(a, s);
-    default: return launch_receive_lb<R, 4>(a, s);
+    case 1: return launch_receive_lb<R, 1>(a, Bs, s);
+    case 2: return launch_receive_lb<R, 2>(a, Bs, s);
+    default: return launch_receive_lb<R, 4>(a, Bs, s);
     }
 }
 
 // ---- upward: columns per CTA NB, parent theta rows split RS ways
 template <class R, int NB, int PO>
-cudaError_t launch_up_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, cudaStream_t s)
+cudaError_t launch_up_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, int acc, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     auto smem_of = [&](int rs) {
@@ -853,19 +873,19 @@ cudaError_t launch_up_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, cud
     const int64_t ctas = (int64_t)P.nbox * 2 * ((B + NB - 1) / NB);
     while (ctas * RS < 8 * 152 && 2 * RS <= P.nth / 2) RS *= 2;
     dim3 grid(P.nbox, 2, ((B + NB - 1) / NB) * RS);
-    k_up<R, NB, PO><<<grid, 256, smem_of(RS), s>>>(P, Ch, B, RS);
+    k_up<R, NB, PO><<<grid, 256, smem_of(RS), s>>>(P, Ch, B, RS, Bs, acc);
     return cudaGetLastError();
 }
 
 template <class R, int NB>
-cudaError_t launch_up_po(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int order, cudaStream_t s)
+cudaError_t launch_up_po(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, int acc, int order, cudaStream_t s)
 {
     switch (order) {
-    case 4: return launch_up_nb<R, NB, 4>(P, Ch, B, s);
-    case 6: return launch_up_nb<R, NB, 6>(P, Ch, B, s);
-    case 8: return launch_up_nb<R, NB, 8>(P, Ch, B, s);
-    case 10: return launch_up_nb<R, NB, 10>(P, Ch, B, s);
-    case 12: return launch_up_nb<R, NB, 12>(P, Ch, B, s);
+    case 4: return launch_up_nb<R, NB, 4>(P, Ch, B, Bs, acc, s);
+    case 6: return launch_up_nb<R, NB, 6>(P, Ch, B, Bs, acc, s);
+    case 8: return launch_up_nb<R, NB, 8>(P, Ch, B, Bs, acc, s);
+    case 10: return launch_up_nb<R, NB, 10>(P, Ch, B, Bs, acc, s);
+    case 12: return launch_up_nb<R, NB, 12>(P, Ch, B, Bs, acc, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -879,59 +899,61 @@ int column_chunk(int B, size_t per_col_bytes)
     return nb;
 }
 
+// B columns of fields with row stride Bs; acc: add into the parent field
 template <class R>
-cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, cudaStream_t s)
+cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, int acc, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     const int order = P.up_order;
     switch (column_chunk<R>(B, ((size_t)Ch.K + (size_t)P.nth * (Ch.nph + P.nph)) * sizeof(C))) {
-    case 1: return launch_up_po<R, 1>(P, Ch, B, order, s);
-    case 2: return launch_up_po<R, 2>(P, Ch, B, order, s);
-    case 4: return launch_up_po<R, 4>(P, Ch, B, order, s);
-    case 8: return launch_up_po<R, 8>(P, Ch, B, order, s);
-    default: return launch_up_po<R, 16>(P, Ch, B, order, s);
+    case 1: return launch_up_po<R, 1>(P, Ch, B, Bs, acc, order, s);
+    case 2: return launch_up_po<R, 2>(P, Ch, B, Bs, acc, order, s);
+    case 4: return launch_up_po<R, 4>(P, Ch, B, Bs, acc, order, s);
+    case 8: return launch_up_po<R, 8>(P, Ch, B, Bs, acc, order, s);
+    default: return launch_up_po<R, 16>(P, Ch, B, Bs, acc, order, s);
     }
 }
 
 template <class R, int ES, int CB>
-cudaError_t launch_translate_es(const DevLevel<R> &Lv, int B, cudaStream_t s)
+cudaError_t launch_translate_es(const DevLevel<R> &Lv, int B, int Bs, int acc, cudaStream_t s)
 {
     const int outs = Lv.K * (B / CB);
     dim3 grid(Lv.nparent, (outs + 128 / ES - 1) / (128 / ES));
-    k_translate<R, ES, CB><<<grid, 128, 0, s>>>(Lv, B);
+    k_translate<R, ES, CB><<<grid, 128, 0, s>>>(Lv, B, Bs, acc);
     return cudaGetLastError();
 }
 
 // Two columns per thread when B is even and there is enough parallelism;
 // lanes per output grow until the level offers ~16 warps per SM.
 template <class R>
-cudaError_t launch_translate(const DevLevel<R> &Lv, int B, cudaStream_t s)
+cudaError_t launch_translate(const DevLevel<R> &Lv, int B, int Bs, int acc, cudaStream_t s)
 {
     const bool pair = (B % 2 == 0) && (int64_t)Lv.nparent * ((Lv.K * (B / 2) + 31) / 32) >= 16 * 152;
-    if (pair) return launch_translate_es<R, 1, 2>(Lv, B, s);
+    if (pair) return launch_translate_es<R, 1, 2>(Lv, B, Bs, acc, s);
     const int64_t warps1 = (int64_t)Lv.nparent * ((Lv.K * B + 31) / 32);
     int es = 1;
     while (es < 16 && warps1 * es < 16 * 152 && es * 2 <= std::max(1, Lv.max_grp / 4)) es *= 2;
     switch (es) {
-    case 1: return launch_translate_es<R, 1, 1>(Lv, B, s);
-    case 2: return launch_translate_es<R, 2, 1>(Lv, B, s);
-    case 4: return launch_translate_es<R, 4, 1>(Lv, B, s);
-    case 8: return launch_translate_es<R, 8, 1>(Lv, B, s);
-    default: return launch_translate_es<R, 16, 1>(Lv, B, s);
+    case 1: return launch_translate_es<R, 1, 1>(Lv, B, Bs, acc, s);
+    case 2: return launch_translate_es<R, 2, 1>(Lv, B, Bs, acc, s);
+    case 4: return launch_translate_es<R, 4, 1>(Lv, B, Bs, acc, s);
+    case 8: return launch_translate_es<R, 8, 1>(Lv, B, Bs, acc, s);
+    default: return launch_translate_es<R, 16, 1>(Lv, B, Bs, acc, s);
     }
 }
 
 // ---- downward: columns per CTA NB
 template <class R, int NB>
-cudaError_t launch_down_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, size_t smem, cudaStream_t s)
+cudaError_t launch_down_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, size_t smem, cudaStream_t s)
 {
     dim3 grid(Ch.nbox, 2, (B + NB - 1) / NB);
-    k_down<R, NB><<<grid, 256, smem, s>>>(P, Ch, B);
+    k_down<R, NB><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
     return cudaGetLastError();
 }
 
+// B columns of fields with row stride Bs, added into the child's incoming field
 template <class R>
-cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, cudaStream_t s)
+cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     const size_t per_col = ((size_t)P.K + (size_t)P.nth * Ch.nph) * sizeof(C);
@@ -939,11 +961,11 @@ cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, cuda
     const size_t smem = per_col * nb;
     if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
     switch (nb) {
-    case 1: return launch_down_nb<R, 1>(P, Ch, B, smem, s);
-    case 2: return launch_down_nb<R, 2>(P, Ch, B, smem, s);
-    case 4: return launch_down_nb<R, 4>(P, Ch, B, smem, s);
-    case 8: return launch_down_nb<R, 8>(P, Ch, B, smem, s);
-    default: return launch_down_nb<R, 16>(P, Ch, B, smem, s);
+    case 1: return launch_down_nb<R, 1>(P, Ch, B, Bs, smem, s);
+    case 2: return launch_down_nb<R, 2>(P, Ch, B, Bs, smem, s);
+    case 4: return launch_down_nb<R, 4>(P, Ch, B, Bs, smem, s);
+    case 8: return launch_down_nb<R, 8>(P, Ch, B, Bs, smem, s);
+    default: return launch_down_nb<R, 16>(P, Ch, B, Bs, smem, s);
     }
 }
 
@@ -1016,26 +1038,26 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
     TRY(launch_near<R>(a, s0));
     TRY(tick(clk, STAGE_NEAR, s0));
     if (leaf >= 2) {
-        TRY(launch_radiate<R>(a, sf));
+        TRY(launch_radiate<R>(a, B, sf));
         TRY(tick(clk, STAGE_RADIATE, sf));
         if (!serial) {
             TRY(cudaEventRecord(cs.ev[3 + leaf], sf));
             TRY(cudaStreamWaitEvent(st, cs.ev[3 + leaf], 0));
         }
-        TRY(launch_translate<R>(a.lv[leaf], B, st));
+        TRY(launch_translate<R>(a.lv[leaf], B, B, 0, st));
         TRY(tick(clk, STAGE_TRANSLATE + leaf, st));
         for (int l = leaf - 1; l >= 2; --l) {
-            TRY(launch_up<R>(a.lv[l], a.lv[l + 1], B, sf));
+            TRY(launch_up<R>(a.lv[l], a.lv[l + 1], B, B, 0, sf));
             TRY(tick(clk, STAGE_UP + l, sf));
             if (l == 2) {
-                TRY(launch_translate<R>(a.lv[l], B, sf));
+                TRY(launch_translate<R>(a.lv[l], B, B, 0, sf));
                 TRY(tick(clk, STAGE_TRANSLATE + l, sf));
             } else {
                 if (!serial) {
                     TRY(cudaEventRecord(cs.ev[3 + l], sf));
                     TRY(cudaStreamWaitEvent(st, cs.ev[3 + l], 0));
                 }
-                TRY(launch_translate<R>(a.lv[l], B, st));
+                TRY(launch_translate<R>(a.lv[l], B, B, 0, st));
                 TRY(tick(clk, STAGE_TRANSLATE + l, st));
             }
         }
@@ -1044,15 +1066,89 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
             TRY(cudaStreamWaitEvent(sf, cs.ev[2], 0));
         }
         for (int l = 2; l < leaf; ++l) {
-            TRY(launch_down<R>(a.lv[l], a.lv[l + 1], B, sf));
+            TRY(launch_down<R>(a.lv[l], a.lv[l + 1], B, B, sf));
             TRY(tick(clk, STAGE_DOWN + l, sf));
         }
         if (!serial) {
             TRY(cudaEventRecord(cs.ev[1], sf));
             TRY(cudaStreamWaitEvent(s0, cs.ev[1], 0));
         }
-        TRY(launch_receive<R>(a, s0));
+        TRY(launch_receive<R>(a, B, s0));
         TRY(tick(clk, STAGE_RECEIVE, s0));
+    }
+#undef TRY
+    return cudaSuccess;
+}
+
+// The k-derivative of the far pass, differentiated stage by stage with the
+// samples, stencils and truncation fixed.  Each field row holds the value
+// (columns [0, T)) and its k-tangent (columns [T, 2T)); every stage runs
+// once over all 2T columns with its own table, then once more from the value
+// half into the tangent half with the derivative of that table:
+//   radiate    S = V x,                 S' = V' x
+//   up         S_p' += sum_c shift'_pc Interp(S_c)
+//   translate  G' += sum alpha' S
+//   down       G_c' += Anterp(conj(shift'_pc) G_p)
+//   receive    y += w conj(V) . G' + w conj(V' + (2/k) V) . G
+// (the 2/k is the derivative of the far constant -k^2 eta / 4 pi over itself).
+template <class R>
+cudaError_t launch_core_dk(const ProductArgs<R> &a, cudaStream_t s, StageClock *clk)
+{
+    const int T = a.B, Bs = 2 * a.B, leaf = a.leaf;
+    if (!a.near_dk || (leaf >= 2 && (!a.Vd || !a.Wd))) return cudaErrorInvalidValue;
+    auto tangent = [&](R *f) { return f + 2 * (size_t)T; };   // T complex columns
+    cudaError_t e;
+#define TRY(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
+    {
+        ProductArgs<R> an = a;
+        an.near_val = a.near_dk;
+        TRY(launch_near<R>(an, s));
+        TRY(tick(clk, STAGE_NEAR, s));
+    }
+    if (leaf < 2) return cudaSuccess;
+    {
+        TRY(launch_radiate<R>(a, Bs, s));
+        ProductArgs<R> ad = a;
+        ad.V = a.Vd;
+        ad.lv[leaf].S = tangent(a.lv[leaf].S);
+        TRY(launch_radiate<R>(ad, Bs, s));
+        TRY(tick(clk, STAGE_RADIATE, s));
+    }
+    auto translate = [&](int l) -> cudaError_t {
+        cudaError_t e2 = launch_translate<R>(a.lv[l], Bs, Bs, 0, s);
+        if (e2 != cudaSuccess) return e2;
+        DevLevel<R> x = a.lv[l];
+        x.alpha = a.lv[l].alpha_dk;
+        x.G = tangent(a.lv[l].G);
+        if ((e2 = launch_translate<R>(x, T, Bs, 1, s)) != cudaSuccess) return e2;
+        return tick(clk, STAGE_TRANSLATE + l, s);
+    };
+    TRY(translate(leaf));
+    for (int l = leaf - 1; l >= 2; --l) {
+        TRY(launch_up<R>(a.lv[l], a.lv[l + 1], Bs, Bs, 0, s));
+        DevLevel<R> px = a.lv[l];
+        px.shift = a.lv[l].shift_dk;
+        px.S = tangent(a.lv[l].S);
+        TRY(launch_up<R>(px, a.lv[l + 1], T, Bs, 1, s));
+        TRY(tick(clk, STAGE_UP + l, s));
+        TRY(translate(l));
+    }
+    for (int l = 2; l < leaf; ++l) {
+        TRY(launch_down<R>(a.lv[l], a.lv[l + 1], Bs, Bs, s));
+        DevLevel<R> px = a.lv[l], cx = a.lv[l + 1];
+        px.shift = a.lv[l].shift_dk;
+        cx.G = tangent(a.lv[l + 1].G);
+        TRY(launch_down<R>(px, cx, T, Bs, s));
+        TRY(tick(clk, STAGE_DOWN + l, s));
+    }
+    {
+        ProductArgs<R> at = a;
+        at.lv[leaf].G = tangent(a.lv[leaf].G);
+        TRY(launch_receive<R>(at, Bs, s));
+        ProductArgs<R> aw = a;
+        aw.V = a.Wd;
+        TRY(launch_receive<R>(aw, Bs, s));
+        TRY(tick(clk, STAGE_RECEIVE, s));
     }
 #undef TRY
     return cudaSuccess;
@@ -1066,5 +1162,7 @@ template cudaError_t launch_finalize<float>(const ProductArgs<float> &, void *, 
 template cudaError_t launch_finalize<double>(const ProductArgs<double> &, void *, int, int, int, cudaStream_t);
 template cudaError_t launch_core<float>(const ProductArgs<float> &, const CoreStreams &, StageClock *);
 template cudaError_t launch_core<double>(const ProductArgs<double> &, const CoreStreams &, StageClock *);
+template cudaError_t launch_core_dk<float>(const ProductArgs<float> &, cudaStream_t, StageClock *);
+template cudaError_t launch_core_dk<double>(const ProductArgs<double> &, cudaStream_t, StageClock *);
 
 }  // namespace mlfma

@@ -11,6 +11,13 @@
 //
 // Leaf radiation patterns (Eq. (11)): V_s,mj(khat) = int (I - khat khat) .
 // f_j(r) exp(i k khat.(r_m - r)) dS, its theta and phi components.
+//
+// Wavenumber derivatives (quadrature, tree and samples fixed): the near
+// blocks of dZ/dk = i eta (A + Phi / k^2) + i k eta (A' - Phi' / k^2), with A
+// and Phi the vector- and scalar-potential parts of Z (singular parts
+// extracted as above) and A', Phi' the same integrals of dg/dk = i exp(ikR)
+// (bounded: plain rule); and the derivative patterns dV/dk, whose phase
+// factor gains i khat.(r_m - r).
 #include "device.h"
 
 #include <algorithm>
@@ -144,6 +151,7 @@ __device__ bool near_singular(const DevMesh &m, int t, int s)
 // Outer triangle t of test function (sign si, length li, free vertex vi),
 // inner triangle s of source function (sj, lj, vj):
 // sum_p A_t w_p [ f_i(r_p) . int f_j g  -  div f_i div f_j int g / k^2 ]
+template <int DSIGN = -1>
 __device__ Z1 pair_integral(const DevMesh &m, int t, double si, double li, P3 vi, int s, double sj, double lj,
                             P3 vj, double k, bool singular)
 {
@@ -162,8 +170,43 @@ __device__ Z1 pair_integral(const DevMesh &m, int t, double si, double li, P3 vi
         const double vre = cj * (dotp(fi, P1.re) - P0.re * dotp(fi, vj));
         const double vim = cj * (dotp(fi, P1.im) - P0.im * dotp(fi, vj));
         const double w = At * c_rule[p][3];
-        acc.re += w * (vre - dd * P0.re);
-        acc.im += w * (vim - dd * P0.im);
+        if (DSIGN < 0) {
+            acc.re += w * (vre - dd * P0.re);
+            acc.im += w * (vim - dd * P0.im);
+        } else {
+            acc.re += w * (vre + dd * P0.re);
+            acc.im += w * (vim + dd * P0.im);
+        }
+    }
+    return acc;
+}
+
+// sum_p sum_q A_t w_p A_s w_q [f_i(r_p) . f_j(r_q) - div f_i div f_j / k^2] i exp(ik|r_p - r_q|)
+__device__ Z1 pair_integral_dk(const DevMesh &m, int t, double si, double li, P3 vi, int s, double sj, double lj,
+                               P3 vj, double k)
+{
+    const double At = m.area[t], As = m.area[s];
+    const double ci = si * li / (2.0 * At), cj = sj * lj / (2.0 * As);
+    const double dd = (si * li / At) * (sj * lj / As) / (k * k);
+    Z1 acc = {0.0, 0.0};
+#pragma unroll 1
+    for (int p = 0; p < 7; ++p) {
+        const P3 r = mk(m.tq + 21 * t + 3 * p);
+        const P3 fi = ci * (r - vi);
+        double are = 0.0, aim = 0.0;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const P3 rq = mk(m.tq + 21 * s + 3 * q);
+            const double ff = dotp(fi, cj * (rq - vj)) - dd;
+            double sx, cx;
+            sincos(k * lenp(r - rq), &sx, &cx);
+            const double w = As * c_rule[q][3] * ff;
+            are -= w * sx;   // i exp(ikR) = -sin + i cos
+            aim += w * cx;
+        }
+        const double w = At * c_rule[p][3];
+        acc.re += w * are;
+        acc.im += w * aim;
     }
     return acc;
 }
@@ -205,6 +248,49 @@ __global__ void k_near_fill(DevMesh m, DevNear nr, double k, double eta, double2
     }
 }
 
+__global__ void k_near_fill_dk(DevMesh m, DevNear nr, double k, double eta, double2 *val)
+{
+    const int b = blockIdx.x;
+    const int r0 = nr.box_ptr[b];
+    const int nrow = nr.box_ptr[b + 1] - r0;
+    const int c0 = nr.col_ptr[b];
+    const int ncol = nr.col_ptr[b + 1] - c0;
+    const int64_t off = nr.strip_off[b];
+    const int64_t count = (int64_t)nrow * ncol;
+    for (int64_t e = threadIdx.x; e < count; e += blockDim.x) {
+        const int c = (int)(e / nrow), rr = (int)(e % nrow);
+        const int i = r0 + rr, j = nr.strip_col[c0 + c];
+        Z1 tv = {0.0, 0.0}, td = {0.0, 0.0};
+        for (int a = 0; a < 2; ++a) {
+            const int t = m.rtri[2 * i + a];
+            const double si = a == 0 ? 1.0 : -1.0;
+            const P3 vi = mk(m.rvf + 6 * i + 3 * a);
+            for (int bb = 0; bb < 2; ++bb) {
+                const int s = m.rtri[2 * j + bb];
+                const double sj = bb == 0 ? 1.0 : -1.0;
+                const P3 vj = mk(m.rvf + 6 * j + 3 * bb);
+                const bool sing = near_singular(m, t, s);
+                Z1 z = pair_integral<1>(m, t, si, m.rlen[i], vi, s, sj, m.rlen[j], vj, k, sing);
+                if (sing) {
+                    Z1 zr = pair_integral<1>(m, s, sj, m.rlen[j], vj, t, si, m.rlen[i], vi, k, sing);
+                    z.re = 0.5 * (z.re + zr.re);
+                    z.im = 0.5 * (z.im + zr.im);
+                }
+                tv.re += z.re;
+                tv.im += z.im;
+                const Z1 d = pair_integral_dk(m, t, si, m.rlen[i], vi, s, sj, m.rlen[j], vj, k);
+                td.re += d.re;
+                td.im += d.im;
+            }
+        }
+        // i eta (A + Phi / k^2) + i k eta (A' - Phi' / k^2)
+        val[off + e] = make_double2(-eta * tv.im - k * eta * td.im, eta * tv.re + k * eta * td.re);
+    }
+}
+
+// MODE 0: V; 1: dV/dk; 2: dV/dk + (2/k) V (the receiving side's derivative
+// pattern, with the k^2 of the far-field constant folded in).
+template <int MODE>
 __global__ void k_leaf_patterns(DevMesh m, const int32_t *ubox, const double *bc, int K, const double *grid,
                                 double k, double2 *V)
 {
@@ -226,10 +312,18 @@ __global__ void k_leaf_patterns(DevMesh m, const int32_t *ubox, const double *bc
                 const P3 rp = mk(m.tq + 21 * t + 3 * p);
                 const P3 f = c * (rp - vf);
                 double sn, cs;
-                sincos(k * dotp(kh, rc - rp), &sn, &cs);
+                const double ph = dotp(kh, rc - rp);
+                sincos(k * ph, &sn, &cs);
                 const double w = A * c_rule[p][3];
-                acc.re = acc.re + (w * cs) * f;
-                acc.im = acc.im + (w * sn) * f;
+                if (MODE == 0) {
+                    acc.re = acc.re + (w * cs) * f;
+                    acc.im = acc.im + (w * sn) * f;
+                } else {
+                    // i ph exp(i k ph) (+ (2/k) exp(i k ph))
+                    const double g = MODE == 2 ? 2.0 / k : 0.0;
+                    acc.re = acc.re + (w * (g * cs - ph * sn)) * f;
+                    acc.im = acc.im + (w * (g * sn + ph * cs)) * f;
+                }
             }
         }
         V[2 * idx] = make_double2(dotp(th, acc.re), dotp(th, acc.im));
@@ -301,15 +395,30 @@ cudaError_t launch_near_fill(const DevMesh &m, const DevNear &nr, double k, doub
     return cudaGetLastError();
 }
 
+cudaError_t launch_near_fill_dk(const DevMesh &m, const DevNear &nr, double k, double eta, double2 *val,
+                                cudaStream_t s)
+{
+    cudaError_t e = upload_rule();
+    if (e != cudaSuccess) return e;
+    if (nr.nleaf == 0) return cudaSuccess;
+    k_near_fill_dk<<<nr.nleaf, 128, 0, s>>>(m, nr, k, eta, val);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_leaf_patterns(const DevMesh &m, const int32_t *ubox, const double *box_center, int K,
-                                 const double *grid, double k, double2 *V, cudaStream_t s)
+                                 const double *grid, double k, double2 *V, cudaStream_t s, int mode)
 {
     cudaError_t e = upload_rule();
     if (e != cudaSuccess) return e;
     const int64_t total = m.n * (int64_t)K;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     if (blocks < 1) blocks = 1;
-    k_leaf_patterns<<<blocks, 256, 0, s>>>(m, ubox, box_center, K, grid, k, V);
+    switch (mode) {
+    case 0: k_leaf_patterns<0><<<blocks, 256, 0, s>>>(m, ubox, box_center, K, grid, k, V); break;
+    case 1: k_leaf_patterns<1><<<blocks, 256, 0, s>>>(m, ubox, box_center, K, grid, k, V); break;
+    case 2: k_leaf_patterns<2><<<blocks, 256, 0, s>>>(m, ubox, box_center, K, grid, k, V); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

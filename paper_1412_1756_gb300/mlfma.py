@@ -22,7 +22,7 @@ X_PERM, X_LEAF_BOX, X_GRID, X_ALPHA, X_ALPHA_OFFS, X_INTERP, X_BOX_CENTERS, X_NE
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ENOTSUP"}
 
 EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg_edges", "mlfma_matvec",
-            "mlfma_matvec_adjoint", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
+            "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
             "mlfma_profile_stages", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
             "mlfma_destroy", "mlfma_last_error"]
 CM_ZINV_R, CM_XINV_R = 0, 1
@@ -86,7 +86,8 @@ def load(build_if_missing: bool = False):
                              ctypes.POINTER(P)]
     L.mlfma_num_unknowns.argtypes = [P, ctypes.POINTER(I64)]
     L.mlfma_rwg_edges.argtypes = [P, P, P]
-    for f in ("mlfma_matvec", "mlfma_matvec_adjoint", "mlfma_matvec_host", "mlfma_matvec_noalloc"):
+    for f in ("mlfma_matvec", "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint",
+              "mlfma_matvec_host", "mlfma_matvec_noalloc"):
         getattr(L, f).argtypes = [P, P, I, P, I64, I, P]
     L.mlfma_sync.argtypes = [P, P]
     L.mlfma_profile_stages.argtypes = [P, P, I, P, I64, I, P, P]
@@ -228,6 +229,30 @@ class MlfmaPlan:
         """y = Z^H x."""
         return self._product(self._lib.mlfma_matvec_adjoint, x, y, stream)
 
+    def _dk_product(self, fn, x, y, stream):
+        # value and tangent fields share the plan's field buffers: at most
+        # max_batch / 2 internal real columns per call, so wider x is split
+        import torch
+        squeeze = x.dim() == 1
+        x2 = x.reshape(self.n, -1) if squeeze else x
+        per = max(1, (self.max_batch // 2) // (2 if x2.is_complex() else 1))
+        if x2.dim() != 2 or x2.shape[1] <= per:
+            return self._product(fn, x, y, stream)
+        cdt = torch.complex64 if self._prec_of(x2.dtype) == FP32 else torch.complex128
+        out = torch.empty((self.n, x2.shape[1]), dtype=cdt, device=x2.device) if y is None else y.view(self.n, -1)
+        for c0 in range(0, x2.shape[1], per):
+            c1 = min(x2.shape[1], c0 + per)
+            out[:, c0:c1] = self._product(fn, x2[:, c0:c1], None, stream)
+        return out
+
+    def matvec_dk(self, x, y=None, stream=None):
+        """y = (dZ/dk) x (include/mlfma.h: mlfma_matvec_dk)."""
+        return self._dk_product(self._lib.mlfma_matvec_dk, x, y, stream)
+
+    def matvec_dk_adjoint(self, x, y=None, stream=None):
+        """y = (dZ/dk)^H x."""
+        return self._dk_product(self._lib.mlfma_matvec_dk_adjoint, x, y, stream)
+
     def matvec_host(self, x: np.ndarray, prec: int = FP32, y: np.ndarray = None, stream=None) -> np.ndarray:
         """y = Z x for HOST arrays (copies inside the call; waits for completion)."""
         rdt = np.float32 if prec == FP32 else np.float64
@@ -290,3 +315,54 @@ class MlfmaPlan:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_function():
+    import torch
+    from torch.autograd.function import once_differentiable
+
+    class MlfmaZ(torch.autograd.Function):
+        """y = Z(k) x with gradients for x (through Z^H) and for the 0-d
+        wavenumber tensor k (through dZ/dk): grad_k = Re sum conj(g) (dZ/dk x)
+        for the upstream gradient g, PyTorch's convention for a real input of
+        a complex output."""
+
+        @staticmethod
+        def forward(ctx, x, k, plan):
+            if k.dim() != 0:
+                raise ValueError("k must be a 0-d tensor")
+            kv = float(k.detach().cpu())
+            if abs(kv - plan.k) > 1e-12 * abs(plan.k):
+                raise ValueError("k = %r differs from the plan's wavenumber %r" % (kv, plan.k))
+            ctx.plan = plan
+            ctx.save_for_backward(x)
+            return plan.matvec(x)
+
+        @staticmethod
+        @once_differentiable
+        def backward(ctx, g):
+            (x,) = ctx.saved_tensors
+            plan = ctx.plan
+            gx = gk = None
+            if ctx.needs_input_grad[0]:
+                gx = plan.matvec_adjoint(g.contiguous())
+                if not x.is_complex():
+                    gx = gx.real.contiguous()
+            if ctx.needs_input_grad[1]:
+                dy = plan.matvec_dk(x)
+                gk = (g.conj() * dy).real.sum().to(torch.float64)
+            return gx, gk, None
+
+    return MlfmaZ
+
+
+_MlfmaZ = None
+
+
+def efie_product(plan: MlfmaPlan, x, k):
+    """Differentiable y = Z(k) x for a CUDA tensor x [N] or [N, B] and a 0-d
+    tensor k equal to the plan's wavenumber (gradients for x and k)."""
+    global _MlfmaZ
+    if _MlfmaZ is None:
+        _MlfmaZ = _autograd_function()
+    return _MlfmaZ.apply(x, k, plan)
