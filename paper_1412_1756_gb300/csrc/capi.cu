@@ -201,6 +201,26 @@ cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *ne
             if ((e = M.upload(pack(Lv.ph_up), &D.phu)) != cudaSuccess) return e;
             if ((e = M.upload(pack(Lv.th_dn), &D.thd)) != cudaSuccess) return e;
             if ((e = M.upload(pack(Lv.ph_dn), &D.phd)) != cudaSuccess) return e;
+            int longest = 0;
+            for (const Stencil *st : {&Lv.th_dn, &Lv.ph_dn})
+                for (size_t r = 0; r + 1 < st->ptr.size(); ++r) longest = std::max(longest, st->ptr[r + 1] - st->ptr[r]);
+            D.dn_taps = 0;
+            for (int tm : {16, 20, 24, 32})
+                if (!D.dn_taps && longest <= tm) D.dn_taps = tm;
+            if (!D.dn_taps) return cudaErrorInvalidValue;   // needs interpolation order <= 12
+            auto pad = [&](const Stencil &st) {
+                const int rows = (int)st.ptr.size() - 1;
+                std::vector<Tap<R>> t((size_t)rows * D.dn_taps, Tap<R>{0, (R)0});
+                for (int r = 0; r < rows; ++r)
+                    for (int e2 = st.ptr[r]; e2 < st.ptr[r + 1]; ++e2) {
+                        Tap<R> &tp = t[(size_t)r * D.dn_taps + (e2 - st.ptr[r])];
+                        tp.i = st.idx[e2] | ((!st.refl.empty() && st.refl[e2]) ? kTapRefl : 0);
+                        tp.c = (R)st.coef[e2];
+                    }
+                return t;
+            };
+            if ((e = M.upload(pad(Lv.th_dn), &D.thd_pad)) != cudaSuccess) return e;
+            if ((e = M.upload(pad(Lv.ph_dn), &D.phd_pad)) != cudaSuccess) return e;
             const Level &C = H.lv[l + 1];
             scratch = std::max<int64_t>(scratch, (int64_t)C.nbox() * 2 * Lv.nth * C.nph * Bmax);
         }

@@ -67,6 +67,9 @@ struct DevLevel {
     const int32_t *phd_ptr = nullptr, *phd_idx = nullptr;
     const R *phd_c = nullptr;
     const Tap<R> *thu = nullptr, *phu = nullptr, *thd = nullptr, *phd = nullptr;   // packed taps
+    // anterpolation stencils zero-padded to dn_taps taps per row (16, 20, 24 or 32)
+    const Tap<R> *thd_pad = nullptr, *phd_pad = nullptr;
+    int dn_taps = 0;
     int up_order = 0;           // taps per forward stencil row (the interpolation order)
     const R *wq = nullptr;               // [K] quadrature weight (leaf: times -k^2 eta / 4 pi)
     R *S = nullptr;                      // outgoing field [nbox][2][K][B]

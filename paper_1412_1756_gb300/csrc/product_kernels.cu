@@ -46,6 +46,21 @@ template <class C, class R> __device__ __forceinline__ void rfma(C &acc, R s, C 
     acc.y = fma(s, b.y, acc.y);
 }
 
+// Asynchronous global -> shared copies of one complex value (8 or 16 bytes),
+// completed by cp_async_wait: the copy's latency overlaps later work.
+template <class C>
+__device__ __forceinline__ void cp_async(C *smem, const C *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(C) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 constexpr int kSmemCap = 200 * 1024;  // dynamic shared memory a kernel may ask for (227 KB per CTA on sm_103a)
 constexpr int kStageCap = 96 * 1024;  // staging budget of the near / leaf kernels (keeps >= 2 CTAs per SM)
 
@@ -385,6 +400,25 @@ struct Split {
     }
 };
 
+// Interleaved variant: item (key, column group, phase ch) takes the rows
+// ch, ch + chunks, ...; the threads of a quarter warp then read adjacent
+// rows of one key (bank-conflict free when rows are PW columns wide).
+struct SplitIL {
+    int chunks, items, NLc;
+    __device__ SplitIL(int keys, int NL)
+    {
+        NLc = NL;
+        chunks = max(1, (int)blockDim.x / (keys * NL));
+        items = keys * NL * chunks;
+    }
+    __device__ void item(int it, int CP, int &key, int &cg, int &ch) const
+    {
+        cg = (it % NLc) * CP;
+        ch = (it / NLc) % chunks;
+        key = it / (NLc * chunks);
+    }
+};
+
 // One CTA per (parent box, component, chunk of NB columns, band of parent
 // theta rows).  Per child: its field -> shared memory (the next child's
 // field is prefetched into registers meanwhile), theta interpolation of the
@@ -416,7 +450,7 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
     const C *S = reinterpret_cast<const C *>(Ch.S);
     const C *shift = reinterpret_cast<const C *>(P.shift) + (int64_t)t0 * nphp;
     for (int e = threadIdx.x; e < nO * PW; e += blockDim.x) O[e] = C{0, 0};
-    const Split st(nr, nphc, NL);      // theta step: key = band theta row, span = child phi index
+    const SplitIL st(nr, NL);          // theta step: key = band theta row, rows = child phi index
     const Split sp(nphp, nr, NL);      // phi step: key = parent phi index, span = band theta rows
     const int c0 = P.child_ptr[p], c1 = P.child_ptr[p + 1];
     C pre[PF];
@@ -443,8 +477,8 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
         __syncthreads();
         if (c + 1 < c1) fetch(c + 1);
         for (int it = threadIdx.x; it < st.items; it += blockDim.x) {
-            int key, cg, lo, hi;
-            st.item(it, NL, CP, nphc, key, cg, lo, hi);
+            int key, cg, ch;
+            st.item(it, CP, key, cg, ch);
             int tb[PO];
             bool rf[PO];
             R tc[PO];
@@ -455,7 +489,7 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
                 rf[f] = (tap.i & kTapRefl) != 0;
                 tc[f] = tap.c;
             }
-            for (int v = lo; v < hi; ++v) {
+            for (int v = ch; v < nphc; v += st.chunks) {
                 const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
                 C s[CP];
 #pragma unroll
@@ -522,55 +556,126 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
 }
 
 // --------------------------------------------------------- downward ---
-// One CTA per (child box, component, chunk of NB columns): parent field
-// times the conjugate shift -> shared memory, phi anterpolation -> shared
-// memory, theta anterpolation added into the child's incoming field.
-template <class R, int NB>
-__global__ void __launch_bounds__(256) k_down(DevLevel<R> P, DevLevel<R> Ch, int B, int Bs)
+// One CTA per (child box, component, chunk of NB columns).  At entry both the
+// parent's incoming field and the child's own are requested with
+// asynchronous copies into shared memory; the parent's is multiplied by the
+// conjugate shift in place, phi anterpolation -> shared memory, theta
+// anterpolation -> shared memory (over the first buffer), and the child's
+// copy (waited for only now) plus the result is stored back.  The
+// anterpolation stencils (weighted transposes of the interpolation
+// stencils) are zero-padded to TM taps per row so that a thread holds one
+// row's taps in registers and sweeps them over a chunk of rows, CP adjacent
+// columns per 16-byte shared-memory access (the layout of the upward pass).
+template <class R, int NB, int TM>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && TM <= 20) ? 4 : 1) k_down(DevLevel<R> P, DevLevel<R> Ch, int B, int Bs)
 {
     using C = typename Cx<R>::T;
+    constexpr int CP = ColPair<R, NB>::CP, NL = NB / CP, PW = NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Kc = Ch.K, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph, Kp = P.K;
+    const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph, Kp = P.K;
     const int c = blockIdx.x, comp = blockIdx.y;
     const int b0 = blockIdx.z * NB;
+    const int nb = min(NB, B - b0);
+    const int hp = nphp + 1;                   // H row pitch per parent theta row (one pad row)
+    C *H = reinterpret_cast<C *>(smem_raw);   // [ntp][hp][PW]; later the child result [Kc][PW]
+    C *U = H + (size_t)ntp * hp * PW;          // [ntp * nphc][PW]
+    C *X = U + (size_t)ntp * nphc * PW;        // [Kc][PW] the child's incoming field
     const int bb = threadIdx.x % NB, slot = threadIdx.x / NB, nslot = blockDim.x / NB;
-    const bool bok = b0 + bb < B;
-    C *H = reinterpret_cast<C *>(smem_raw);   // [Kp][NB]
-    C *U = H + (size_t)Kp * NB;                // [ntp * nphc][NB]
-    const int par = Ch.parent[c];
-    const C *g = reinterpret_cast<const C *>(P.G) + ((int64_t)par * 2 + comp) * Kp * Bs + b0 + bb;
-    const C *sh = reinterpret_cast<const C *>(P.shift) + (int64_t)Ch.octant[c] * Kp;
-    for (int q = slot; q < Kp; q += nslot) {
-        C h{0, 0};
-        if (bok) cfmac(h, sh[q], g[(int64_t)q * Bs]);
-        H[q * NB + bb] = h;
+    const bool bok = bb < nb;
+    C *dst = reinterpret_cast<C *>(Ch.G) + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + bb;
+    {
+        const int par = Ch.parent[c];
+        const C *g = reinterpret_cast<const C *>(P.G) + ((int64_t)par * 2 + comp) * Kp * Bs + b0 + bb;
+        for (int q = slot; q < Kp; q += nslot) {
+            const int hq = q + q / nphp;   // padded row
+            if (bok) cp_async(H + hq * PW + bb, g + (int64_t)q * Bs);
+            else H[hq * PW + bb] = C{0, 0};
+        }
+        cp_async_commit();
+        if (bok)
+            for (int q = slot; q < Kc; q += nslot) cp_async(X + q * PW + bb, dst + (int64_t)q * Bs);
+        cp_async_commit();
+        const C *sh = reinterpret_cast<const C *>(P.shift) + (int64_t)Ch.octant[c] * Kp;
+        cp_async_wait<1>();
+#pragma unroll 4
+        for (int q = slot; q < Kp; q += nslot) {   // the elements this thread copied
+            const int hq = q + q / nphp;
+            C h{0, 0};
+            cfmac(h, sh[q], H[hq * PW + bb]);
+            H[hq * PW + bb] = h;
+        }
     }
     __syncthreads();
-    for (int r = slot; r < ntp * nphc; r += nslot) {
-        const int tp = r / nphc, v = r - tp * nphc;
-        const C *hrow = H + tp * nphp * NB + bb;
-        C s{0, 0};
-#pragma unroll 4
-        for (int f = P.phd_ptr[v]; f < P.phd_ptr[v + 1]; ++f) {
-            const Tap<R> tap = P.phd[f];
-            rfma(s, tap.c, hrow[tap.i * NB]);
+    // phi: U(tp, v) = sum_f c_f H(tp, u_f(v)); key = child phi index v, rows = parent theta rows
+    const SplitIL sp(nphc, NL);
+    for (int it = threadIdx.x; it < sp.items; it += blockDim.x) {
+        int key, cg, ch;
+        sp.item(it, CP, key, cg, ch);
+        int pb[TM];
+        R pc[TM];
+#pragma unroll
+        for (int f = 0; f < TM; ++f) {
+            const Tap<R> tap = P.phd_pad[(size_t)key * TM + f];
+            pb[f] = tap.i * PW;
+            pc[f] = tap.c;
         }
-        U[r * NB + bb] = s;
+        for (int tp = ch; tp < ntp; tp += sp.chunks) {
+            const C *hrow = H + tp * hp * PW + cg;
+            C s[CP];
+#pragma unroll
+            for (int k = 0; k < CP; ++k) s[k] = C{0, 0};
+#pragma unroll
+            for (int f = 0; f < TM; ++f) {
+                C a[CP];
+                lds_cols<C, CP>(hrow + pb[f], a);
+#pragma unroll
+                for (int k = 0; k < CP; ++k) rfma(s[k], pc[f], a[k]);
+            }
+            sts_cols<C, CP>(U + (tp * nphc + key) * PW + cg, s);
+        }
     }
+    __syncthreads();
+    // theta: W(j, v) = sum_f c_f U(t_f, v or v + pi); key = child theta row j, span = child phi index
+    const SplitIL st(nthc, NL);
+    C *W = H;
+    for (int it = threadIdx.x; it < st.items; it += blockDim.x) {
+        int key, cg, ch;
+        st.item(it, CP, key, cg, ch);
+        int tb[TM];
+        bool rf[TM];
+        R tc[TM];
+#pragma unroll
+        for (int f = 0; f < TM; ++f) {
+            const Tap<R> tap = P.thd_pad[(size_t)key * TM + f];
+            tb[f] = (tap.i & (kTapRefl - 1)) * nphc;
+            rf[f] = (tap.i & kTapRefl) != 0;
+            tc[f] = tap.c;
+        }
+        for (int v = ch; v < nphc; v += st.chunks) {
+            const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
+            C s[CP];
+#pragma unroll
+            for (int k = 0; k < CP; ++k) s[k] = C{0, 0};
+#pragma unroll
+            for (int f = 0; f < TM; ++f) {
+                C a[CP];
+                lds_cols<C, CP>(U + (tb[f] + (rf[f] ? vs : v)) * PW + cg, a);
+#pragma unroll
+                for (int k = 0; k < CP; ++k) rfma(s[k], tc[f], a[k]);
+            }
+            sts_cols<C, CP>(W + (key * nphc + v) * PW + cg, s);
+        }
+    }
+    cp_async_wait<0>();
     __syncthreads();
     if (!bok) return;
-    C *dst = reinterpret_cast<C *>(Ch.G) + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + bb;
-    for (int q = slot; q < Kc; q += nslot) {
-        const int j = q / nphc, v = q - j * nphc;
-        const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
-        C s = dst[(int64_t)q * Bs];
-#pragma unroll 4
-        for (int f = P.thd_ptr[j]; f < P.thd_ptr[j + 1]; ++f) {
-            const Tap<R> tap = P.thd[f];
-            const int t = tap.i & (kTapRefl - 1);
-            rfma(s, tap.c, U[(t * nphc + ((tap.i & kTapRefl) ? vs : v)) * NB + bb]);
-        }
-        dst[(int64_t)q * Bs] = s;
+#pragma unroll 8
+    for (int q = slot; q < Kc; q += nslot) {   // X elements: copied by this thread
+        C y = X[q * PW + bb];
+        const C w = W[q * PW + bb];
+        y.x += w.x;
+        y.y += w.y;
+        dst[(int64_t)q * Bs] = y;
     }
 }
 
@@ -942,13 +1047,25 @@ cudaError_t launch_translate(const DevLevel<R> &Lv, int B, int Bs, int acc, cuda
     }
 }
 
-// ---- downward: columns per CTA NB
-template <class R, int NB>
+// ---- downward: columns per CTA NB, anterpolation taps per row TM
+template <class R, int NB, int TM>
 cudaError_t launch_down_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, size_t smem, cudaStream_t s)
 {
     dim3 grid(Ch.nbox, 2, (B + NB - 1) / NB);
-    k_down<R, NB><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
+    k_down<R, NB, TM><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
     return cudaGetLastError();
+}
+
+template <class R, int NB>
+cudaError_t launch_down_tm(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, size_t smem, cudaStream_t s)
+{
+    switch (P.dn_taps) {
+    case 16: return launch_down_nb<R, NB, 16>(P, Ch, B, Bs, smem, s);
+    case 20: return launch_down_nb<R, NB, 20>(P, Ch, B, Bs, smem, s);
+    case 24: return launch_down_nb<R, NB, 24>(P, Ch, B, Bs, smem, s);
+    case 32: return launch_down_nb<R, NB, 32>(P, Ch, B, Bs, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // B columns of fields with row stride Bs, added into the child's incoming field
@@ -956,16 +1073,16 @@ template <class R>
 cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
-    const size_t per_col = ((size_t)P.K + (size_t)P.nth * Ch.nph) * sizeof(C);
+    const size_t per_col = ((size_t)P.K + (size_t)P.nth + (size_t)P.nth * Ch.nph + (size_t)Ch.K) * sizeof(C);
     const int nb = column_chunk<R>(B, per_col);
     const size_t smem = per_col * nb;
     if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
     switch (nb) {
-    case 1: return launch_down_nb<R, 1>(P, Ch, B, Bs, smem, s);
-    case 2: return launch_down_nb<R, 2>(P, Ch, B, Bs, smem, s);
-    case 4: return launch_down_nb<R, 4>(P, Ch, B, Bs, smem, s);
-    case 8: return launch_down_nb<R, 8>(P, Ch, B, Bs, smem, s);
-    default: return launch_down_nb<R, 16>(P, Ch, B, Bs, smem, s);
+    case 1: return launch_down_tm<R, 1>(P, Ch, B, Bs, smem, s);
+    case 2: return launch_down_tm<R, 2>(P, Ch, B, Bs, smem, s);
+    case 4: return launch_down_tm<R, 4>(P, Ch, B, Bs, smem, s);
+    case 8: return launch_down_tm<R, 8>(P, Ch, B, Bs, smem, s);
+    default: return launch_down_tm<R, 16>(P, Ch, B, Bs, smem, s);
     }
 }
 
@@ -979,7 +1096,8 @@ cudaError_t prime_kernels()
     cudaError_t e;
 #define ALLOW(k) do { if ((e = allow_smem(k)) != cudaSuccess) return e; } while (0)
 #define ALLOW_UP(NB) ALLOW((k_up<R, NB, 4>)); ALLOW((k_up<R, NB, 6>)); ALLOW((k_up<R, NB, 8>)); \
-    ALLOW((k_up<R, NB, 10>)); ALLOW((k_up<R, NB, 12>)); ALLOW((k_down<R, NB>))
+    ALLOW((k_up<R, NB, 10>)); ALLOW((k_up<R, NB, 12>)); ALLOW((k_down<R, NB, 16>)); ALLOW((k_down<R, NB, 20>)); \
+    ALLOW((k_down<R, NB, 24>)); ALLOW((k_down<R, NB, 32>))
     ALLOW((k_near<R, 1, true>)); ALLOW((k_near<R, 2, true>)); ALLOW((k_near<R, 4, true>));
     ALLOW((k_near<R, 8, true>)); ALLOW((k_near<R, 16, true>));
     ALLOW(k_radiate<R>);
