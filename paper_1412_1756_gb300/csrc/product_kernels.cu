@@ -48,6 +48,11 @@ template <class C, class R> __device__ __forceinline__ void rfma(C &acc, R s, C 
 
 // Asynchronous global -> shared copies of one complex value (8 or 16 bytes),
 // completed by cp_async_wait: the copy's latency overlaps later work.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 template <class C>
 __device__ __forceinline__ void cp_async(C *smem, const C *gmem)
 {
@@ -201,6 +206,101 @@ __global__ void __launch_bounds__(256) k_near(DevNear nr, const typename Cx<R>::
                 yp[(int64_t)(r0 + rt + t) * B + b0 + bb] = s;
             }
             __syncthreads();
+        }
+    }
+}
+
+// Many columns: one CTA per leaf box and all B columns, so the strip is read
+// from memory once.  Chunks of CCH strip columns - their values (contiguous
+// in the column-major strip) and the x rows they multiply - are staged in
+// shared memory by double-buffered asynchronous copies, so the next chunk's
+// loads are in flight while this one is used; thread (row r, column group
+// g) accumulates BPT columns of its row, its x values coming from one
+// broadcast 16-byte load per 4 (FP32) or 2 (FP64) columns.  Needs B a
+// multiple of 16 bytes of R; shared memory 2 CCH (B R + max_rows C).
+template <class R, int BPT>
+__global__ void __launch_bounds__(256) k_near_wide(DevNear nr, const typename Cx<R>::T *__restrict__ val,
+                                                   const R *__restrict__ xp, typename Cx<R>::T *__restrict__ yp, int B)
+{
+    using C = typename Cx<R>::T;
+    constexpr int CCH = 32;
+    constexpr int VEC = 16 / sizeof(R);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *xs = reinterpret_cast<R *>(smem_raw);                       // [2][CCH][B]
+    C *zs = reinterpret_cast<C *>(xs + (size_t)2 * CCH * B);       // [2][CCH][max_rows]
+    const int box = blockIdx.x;
+    const int r0 = nr.box_ptr[box];
+    const int nrow = nr.box_ptr[box + 1] - r0;
+    const int c0 = nr.col_ptr[box];
+    const int ncol = nr.col_ptr[box + 1] - c0;
+    const int64_t off = nr.strip_off[box];
+    const int ng = (B + BPT - 1) / BPT;
+    const int RT = max(1, min(nrow, (int)blockDim.x / ng));
+    const int t = threadIdx.x, r = t % RT, g = t / RT;
+    const bool active = g < ng;
+    const int nchunk = (ncol + CCH - 1) / CCH;
+    const int per = B / VEC;
+    const int zpitch = nr.max_rows;
+    auto stage = [&](int k) {
+        const int cb = k * CCH, cn = min(CCH, ncol - cb);
+        R *dst = xs + (size_t)(k & 1) * CCH * B;
+        for (int e = t; e < cn * per; e += blockDim.x) {
+            const int cc = e / per, p = e - cc * per;
+            cp_async16(dst + cc * B + p * VEC, xp + (int64_t)nr.strip_col[c0 + cb + cc] * B + p * VEC);
+        }
+        C *zd = zs + (size_t)(k & 1) * CCH * zpitch;
+        const C *zsrc = val + off + (int64_t)cb * nrow;
+        for (int e = t; e < cn * nrow; e += blockDim.x) {
+            const int cc = e / nrow, rr = e - cc * nrow;
+            cp_async(zd + cc * zpitch + rr, zsrc + e);
+        }
+        cp_async_commit();
+    };
+    for (int rt = 0; rt < nrow; rt += RT) {
+        C acc[BPT];
+#pragma unroll
+        for (int bb = 0; bb < BPT; ++bb) acc[bb] = C{0, 0};
+        const bool live = active && rt + r < nrow;
+        stage(0);
+        for (int k = 0; k < nchunk; ++k) {
+            if (k + 1 < nchunk) {
+                stage(k + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            if (live) {
+                const R *xb = xs + (size_t)(k & 1) * CCH * B + g * BPT;
+                const C *v = zs + (size_t)(k & 1) * CCH * zpitch + rt + r;
+                const int cn = min(CCH, ncol - k * CCH);
+#pragma unroll 4
+                for (int cc = 0; cc < cn; ++cc) {
+                    const C z = v[cc * zpitch];
+                    const R *xr = xb + cc * B;
+#pragma unroll
+                    for (int bb = 0; bb < BPT; bb += VEC) {
+                        if constexpr (VEC == 4) {
+                            const float4 x4 = *reinterpret_cast<const float4 *>(xr + bb);
+                            rfma(acc[bb], x4.x, z);
+                            rfma(acc[bb + 1], x4.y, z);
+                            rfma(acc[bb + 2], x4.z, z);
+                            rfma(acc[bb + 3], x4.w, z);
+                        } else {
+                            const double2 x2 = *reinterpret_cast<const double2 *>(xr + bb);
+                            rfma(acc[bb], x2.x, z);
+                            rfma(acc[bb + 1], x2.y, z);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (live) {
+            C *yr = yp + (int64_t)(r0 + rt + r) * B + g * BPT;
+#pragma unroll
+            for (int bb = 0; bb < BPT; ++bb)
+                if (g * BPT + bb < B) yr[bb] = acc[bb];
         }
     }
 }
@@ -876,9 +976,25 @@ cudaError_t launch_near_bt(const ProductArgs<R> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <class R, int BPT>
+cudaError_t launch_near_wide(const ProductArgs<R> &a, cudaStream_t s)
+{
+    using C = typename Cx<R>::T;
+    const size_t smem = (size_t)2 * 32 * (a.B * sizeof(R) + a.nr.max_rows * sizeof(C));
+    k_near_wide<R, BPT><<<a.nr.nleaf, 256, smem, s>>>(a.nr, reinterpret_cast<const C *>(a.near_val), a.xp,
+                                                      reinterpret_cast<C *>(a.yp), a.B);
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t launch_near(const ProductArgs<R> &a, cudaStream_t s)
 {
+    // wide path: all columns per strip pass (B a multiple of 16 bytes of R and BPT)
+    if (a.B >= 32 && a.B % 16 == 0 && a.nr.nleaf > 0 &&
+        (size_t)2 * 32 * (a.B * sizeof(R) + a.nr.max_rows * sizeof(typename Cx<R>::T)) <= (size_t)kStageCap) {
+        if (a.B <= 256) return launch_near_wide<R, 8>(a, s);   // 8 columns x rows per thread; row tiles of 256 / (B/8)
+        return launch_near_wide<R, 16>(a, s);
+    }
     if (a.B == 1) return launch_near_bt<R, 1>(a, s);
     if (a.B == 2) return launch_near_bt<R, 2>(a, s);
     if (a.B <= 4) return launch_near_bt<R, 4>(a, s);
@@ -1100,6 +1216,7 @@ cudaError_t prime_kernels()
     ALLOW((k_down<R, NB, 24>)); ALLOW((k_down<R, NB, 32>))
     ALLOW((k_near<R, 1, true>)); ALLOW((k_near<R, 2, true>)); ALLOW((k_near<R, 4, true>));
     ALLOW((k_near<R, 8, true>)); ALLOW((k_near<R, 16, true>));
+    ALLOW((k_near_wide<R, 8>)); ALLOW((k_near_wide<R, 16>));
     ALLOW(k_radiate<R>);
     ALLOW((k_radiate_tiled<R, 8, 4>)); ALLOW((k_radiate_tiled<R, 16, 4>)); ALLOW((k_radiate_tiled<R, 32, 4>));
     ALLOW((k_receive<R, 1>)); ALLOW((k_receive<R, 2>)); ALLOW((k_receive<R, 4>));
