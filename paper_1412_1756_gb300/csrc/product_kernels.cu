@@ -833,11 +833,13 @@ __global__ void __launch_bounds__(256) k_receive(const int32_t *__restrict__ box
 }
 
 // Many columns: one CTA per (leaf box, chunk of NB columns), samples in
-// tiles of QT: the tile of G and of every unknown's patterns go to shared
-// memory; thread (row group, column) accumulates the rows i = group + k *
-// groups of its column in registers.
+// tiles of QT: the tile of G, of the weights and of every unknown's patterns
+// go to shared memory by double-buffered asynchronous copies (the next
+// tile's copies are in flight while this one is used); thread (row group,
+// column) accumulates the rows i = group + k * groups of its column in
+// registers.
 template <class R, int NB, int MAXR>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) k_receive_tiled(const int32_t *__restrict__ box_ptr,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_receive_tiled(const int32_t *__restrict__ box_ptr,
                                                        const typename Cx<R>::T4 *__restrict__ V4, DevLevel<R> lf,
                                                        typename Cx<R>::T *__restrict__ yp, int B, int Bs)
 {
@@ -846,9 +848,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) k_receive_tiled(c
     constexpr int QT = 16;
     constexpr int NG = 256 / NB;          // row groups
     constexpr int VP = QT + 1;            // padded row pitch of the pattern tile
-    __shared__ C Gs[2 * QT * NB];
-    __shared__ R Ws[QT];
-    __shared__ C4 Vs[NG * MAXR * VP];
+    constexpr int GSZ = 2 * QT * NB, VSZ = NG * MAXR * VP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C4 *Vbuf = reinterpret_cast<C4 *>(smem_raw);                 // [2][VSZ]
+    C *Gbuf = reinterpret_cast<C *>(Vbuf + 2 * VSZ);             // [2][GSZ]
+    R *Wbuf = reinterpret_cast<R *>(Gbuf + 2 * GSZ);             // [2][QT]
     const int K = lf.K;
     const int box = blockIdx.x;
     const int b0 = blockIdx.y * NB;
@@ -856,23 +860,49 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) k_receive_tiled(c
     const bool bok = b0 + bb < B;
     const int i0 = box_ptr[box], nrows = box_ptr[box + 1] - i0;
     const C *G = reinterpret_cast<const C *>(lf.G) + (int64_t)box * 2 * K * Bs + b0;
+    const int ntile = (K + QT - 1) / QT;
     for (int r0 = 0; r0 < nrows; r0 += NG * MAXR) {
         const int nr = min(NG * MAXR, nrows - r0);
-        C acc[MAXR];
-#pragma unroll
-        for (int k = 0; k < MAXR; ++k) acc[k] = C{0, 0};
-        for (int q0 = 0; q0 < K; q0 += QT) {
-            const int nq = min(QT, K - q0);
-            for (int e = threadIdx.x; e < 2 * QT * NB; e += blockDim.x) {
+        auto stage = [&](int tile) {
+            const int q0 = tile * QT, nq = min(QT, K - q0);
+            C *Gs = Gbuf + (tile & 1) * GSZ;
+            C4 *Vs = Vbuf + (tile & 1) * VSZ;
+            R *Ws = Wbuf + (tile & 1) * QT;
+            for (int e = threadIdx.x; e < GSZ; e += blockDim.x) {
                 const int b = e % NB, q = (e / NB) % QT, cmp = e / (NB * QT);
-                Gs[e] = (q < nq && b0 + b < B) ? G[((int64_t)cmp * K + q0 + q) * Bs + b] : C{0, 0};
+                if (q < nq && b0 + b < B) cp_async(Gs + e, G + ((int64_t)cmp * K + q0 + q) * Bs + b);
+                else Gs[e] = C{0, 0};
             }
             for (int e = threadIdx.x; e < nr * QT; e += blockDim.x) {
                 const int r = e / QT, q = e % QT;
-                Vs[r * VP + q] = q < nq ? V4[(int64_t)(i0 + r0 + r) * K + q0 + q] : C4{0, 0, 0, 0};
+                C4 *d = Vs + r * VP + q;
+                if (q < nq) {
+                    const C4 *src = V4 + (int64_t)(i0 + r0 + r) * K + q0 + q;
+#pragma unroll
+                    for (int h = 0; h < (int)(sizeof(C4) / 16); ++h)
+                        cp_async16(reinterpret_cast<char *>(d) + 16 * h, reinterpret_cast<const char *>(src) + 16 * h);
+                } else {
+                    *d = C4{0, 0, 0, 0};
+                }
             }
             if (threadIdx.x < QT) Ws[threadIdx.x] = threadIdx.x < nq ? lf.wq[q0 + threadIdx.x] : R(0);
+            cp_async_commit();
+        };
+        C acc[MAXR];
+#pragma unroll
+        for (int k = 0; k < MAXR; ++k) acc[k] = C{0, 0};
+        stage(0);
+        for (int tile = 0; tile < ntile; ++tile) {
+            if (tile + 1 < ntile) {
+                stage(tile + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
             __syncthreads();
+            const C *Gs = Gbuf + (tile & 1) * GSZ;
+            const C4 *Vs = Vbuf + (tile & 1) * VSZ;
+            const R *Ws = Wbuf + (tile & 1) * QT;
 #pragma unroll 4
             for (int q = 0; q < QT; ++q) {
                 const C g0 = Gs[q * NB + bb], g1 = Gs[(QT + q) * NB + bb];
@@ -880,13 +910,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) k_receive_tiled(c
 #pragma unroll
                 for (int k = 0; k < MAXR; ++k) {
                     const int r = grp + k * NG;
-                    if (r < nr) {
-                        const C4 v = Vs[r * VP + q];
-                        C t{0, 0};
-                        cfmac(t, C{v.x, v.y}, g0);
-                        cfmac(t, C{v.z, v.w}, g1);
-                        rfma(acc[k], w, t);
-                    }
+                    if (r >= nr) break;   // rows grow with k
+                    const C4 v = Vs[r * VP + q];
+                    C t{0, 0};
+                    cfmac(t, C{v.x, v.y}, g0);
+                    cfmac(t, C{v.z, v.w}, g1);
+                    rfma(acc[k], w, t);
                 }
             }
             __syncthreads();
@@ -959,6 +988,95 @@ __global__ void __launch_bounds__(256) k_radiate_tiled(const int32_t *__restrict
     }
 }
 
+// Radiation, all columns of a leaf box in one CTA (B a multiple of 4): the
+// box's x block is staged once, the pattern tiles [rows x QT samples] by
+// double-buffered asynchronous copies; thread (sample of the tile, group of
+// 4 columns) accumulates both components of its 4 columns over the rows,
+// from one broadcast pattern load and one 4-column x load per row.
+template <class R>
+__global__ void __launch_bounds__(256) k_radiate_wide(const int32_t *__restrict__ box_ptr,
+                                                      const typename Cx<R>::T4 *__restrict__ V4,
+                                                      const R *__restrict__ xp, typename Cx<R>::T *__restrict__ S,
+                                                      int K, int B, int Bs, int max_rows)
+{
+    using C = typename Cx<R>::T;
+    using C4 = typename Cx<R>::T4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ncg = B / 4, QT = blockDim.x / ncg;
+    C4 *Vbuf = reinterpret_cast<C4 *>(smem_raw);                      // [2][max_rows][QT]
+    R *xs = reinterpret_cast<R *>(Vbuf + (size_t)2 * max_rows * QT);  // [nj][B]
+    const int box = blockIdx.x;
+    const int j0 = box_ptr[box], nj = box_ptr[box + 1] - j0;
+    const int t = threadIdx.x, cg = t % ncg, qi = t / ncg;
+    constexpr int VEC = 16 / sizeof(R);
+    for (int e = t; e < nj * (B / VEC); e += blockDim.x)
+        cp_async16(xs + e * VEC, xp + (int64_t)j0 * B + e * VEC);
+    const int ntile = (K + QT - 1) / QT;
+    auto stage = [&](int tile) {
+        const int q0 = tile * QT, nq = min(QT, K - q0);
+        C4 *Vs = Vbuf + (size_t)(tile & 1) * max_rows * QT;
+        for (int e = t; e < nj * QT; e += blockDim.x) {
+            const int j = e / QT, q = e - j * QT;
+            C4 *d = Vs + e;
+            if (q < nq) {
+                const C4 *src = V4 + (int64_t)(j0 + j) * K + q0 + q;
+#pragma unroll
+                for (int h = 0; h < (int)(sizeof(C4) / 16); ++h)
+                    cp_async16(reinterpret_cast<char *>(d) + 16 * h, reinterpret_cast<const char *>(src) + 16 * h);
+            } else {
+                *d = C4{0, 0, 0, 0};
+            }
+        }
+        cp_async_commit();
+    };
+    stage(0);   // the x block joins the first group
+    for (int tile = 0; tile < ntile; ++tile) {
+        if (tile + 1 < ntile) {
+            stage(tile + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int q = tile * QT + qi;
+        if (qi < QT && q < K) {
+            const C4 *Vs = Vbuf + (size_t)(tile & 1) * max_rows * QT + qi;
+            const R *xr = xs + cg * 4;
+            C a0[4], a1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a0[k] = a1[k] = C{0, 0};
+#pragma unroll 2
+            for (int j = 0; j < nj; ++j) {
+                const C4 v = Vs[j * QT];
+                R xv[4];
+                if constexpr (sizeof(R) == 4) {
+                    const float4 x4 = *reinterpret_cast<const float4 *>(xr + j * B);
+                    xv[0] = x4.x; xv[1] = x4.y; xv[2] = x4.z; xv[3] = x4.w;
+                } else {
+                    const double2 xa = *reinterpret_cast<const double2 *>(xr + j * B);
+                    const double2 xb = *reinterpret_cast<const double2 *>(xr + j * B + 2);
+                    xv[0] = xa.x; xv[1] = xa.y; xv[2] = xb.x; xv[3] = xb.y;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    a0[k].x = fma(v.x, xv[k], a0[k].x);
+                    a0[k].y = fma(v.y, xv[k], a0[k].y);
+                    a1[k].x = fma(v.z, xv[k], a1[k].x);
+                    a1[k].y = fma(v.w, xv[k], a1[k].y);
+                }
+            }
+            C *s0 = S + ((int64_t)(box * 2 + 0) * K + q) * Bs + cg * 4;
+            C *s1 = S + ((int64_t)(box * 2 + 1) * K + q) * Bs + cg * 4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                s0[k] = a0[k];
+                s1[k] = a1[k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------- launchers ---
 template <class R, int BT>
 cudaError_t launch_near_bt(const ProductArgs<R> &a, cudaStream_t s)
@@ -1023,6 +1141,15 @@ cudaError_t launch_radiate(const ProductArgs<R> &a, int Bs, cudaStream_t s)
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
     const DevLevel<R> &Lf = a.lv[a.leaf];
+    if (a.B % 4 == 0 && a.B >= 16 && a.B <= 256 && (a.B * sizeof(R)) % 16 == 0) {
+        const int QT = 256 / (a.B / 4);
+        const size_t smem = (size_t)2 * a.nr.max_rows * QT * sizeof(C4) + (size_t)a.nr.max_rows * a.B * sizeof(R);
+        if (smem <= (size_t)kStageCap) {
+            k_radiate_wide<R><<<Lf.nbox, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), a.xp,
+                                                         reinterpret_cast<C *>(Lf.S), Lf.K, a.B, Bs, a.nr.max_rows);
+            return cudaGetLastError();
+        }
+    }
     if (a.B >= 32 && (size_t)a.nr.max_rows * 32 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 32, 4>(a, Bs, s);
     if (a.B >= 16 && (size_t)a.nr.max_rows * 16 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 16, 4>(a, Bs, s);
     if (a.B >= 8 && (size_t)a.nr.max_rows * 8 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 8, 4>(a, Bs, s);
@@ -1055,8 +1182,10 @@ cudaError_t launch_receive_tiled(const ProductArgs<R> &a, int Bs, cudaStream_t s
     using C4 = typename Cx<R>::T4;
     const DevLevel<R> &Lf = a.lv[a.leaf];
     dim3 grid(Lf.nbox, (a.B + NB - 1) / NB);
-    k_receive_tiled<R, NB, NB / 4><<<grid, 256, 0, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), Lf,
-                                                        reinterpret_cast<C *>(a.yp), a.B, Bs);
+    constexpr int NG = 256 / NB, MAXR = NB / 4, QT = 16;
+    const size_t smem = 2 * ((size_t)NG * MAXR * (QT + 1) * sizeof(C4) + (size_t)2 * QT * NB * sizeof(C) + QT * sizeof(R));
+    k_receive_tiled<R, NB, MAXR><<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), Lf,
+                                                         reinterpret_cast<C *>(a.yp), a.B, Bs);
     return cudaGetLastError();
 }
 
@@ -1218,8 +1347,10 @@ cudaError_t prime_kernels()
     ALLOW((k_near<R, 8, true>)); ALLOW((k_near<R, 16, true>));
     ALLOW((k_near_wide<R, 8>)); ALLOW((k_near_wide<R, 16>));
     ALLOW(k_radiate<R>);
+    ALLOW(k_radiate_wide<R>);
     ALLOW((k_radiate_tiled<R, 8, 4>)); ALLOW((k_radiate_tiled<R, 16, 4>)); ALLOW((k_radiate_tiled<R, 32, 4>));
     ALLOW((k_receive<R, 1>)); ALLOW((k_receive<R, 2>)); ALLOW((k_receive<R, 4>));
+    ALLOW((k_receive_tiled<R, 8, 2>)); ALLOW((k_receive_tiled<R, 16, 4>)); ALLOW((k_receive_tiled<R, 32, 8>));
     ALLOW_UP(1); ALLOW_UP(2); ALLOW_UP(4); ALLOW_UP(8); ALLOW_UP(16);
 #undef ALLOW_UP
 #undef ALLOW
