@@ -120,11 +120,12 @@ struct mlfma_plan_s {
 
 namespace {
 
-constexpr int kIntSlots = 20;   // device integer tables per level
+constexpr int kIntSlots = 22;   // device integer tables per level
 
 template <class R>
 cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *near64, const double2 *V64,
-                            const std::vector<const int32_t *> &dev_ints, const std::vector<const int16_t *> &dev_ty)
+                            const std::vector<const int32_t *> &dev_ints, const std::vector<const int16_t *> &dev_ty,
+                            const std::vector<const int16_t *> &dev_lty)
 {
     PlanHost &H = p->host;
     DevMem &M = p->mem;
@@ -168,6 +169,7 @@ cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *ne
         const int32_t *const *ip = &dev_ints[(size_t)l * kIntSlots];
         D.grp_ptr = ip[16]; D.grp_src = ip[17]; D.pchild_ptr = ip[18];
         D.grp_ty = dev_ty[l];
+        D.lty_ptr = ip[19]; D.lty = ip[20]; D.grp_lty = dev_lty[l]; D.max_lty = Lv.max_lty;
         D.nparent = H.lv[l - 1].nbox();
         D.max_grp = Lv.max_grp;
         D.il_ptr = ip[0]; D.il_src = ip[1]; D.il_type = ip[2];
@@ -315,7 +317,7 @@ mlfma_status setup_device(mlfma_plan_t p)
     }
     // integer tables shared by both precisions: 16 slots per level
     std::vector<const int32_t *> ints((size_t)H.levels * kIntSlots, nullptr);
-    std::vector<const int16_t *> tys((size_t)H.levels, nullptr);
+    std::vector<const int16_t *> tys((size_t)H.levels, nullptr), ltys((size_t)H.levels, nullptr);
     for (int l = 2; l <= H.leaf; ++l) {
         const Level &Lv = H.lv[l];
         const int32_t **ip = &ints[(size_t)l * kIntSlots];
@@ -323,6 +325,9 @@ mlfma_status setup_device(mlfma_plan_t p)
         CK(M.upload(Lv.grp_src, &ip[17]), "upload lists");
         CK(M.upload(H.lv[l - 1].child_ptr, &ip[18]), "upload lists");
         CK(M.upload(Lv.grp_ty, &tys[l]), "upload lists");
+        CK(M.upload(Lv.grp_lty, &ltys[l]), "upload lists");
+        CK(M.upload(Lv.lty_ptr, &ip[19]), "upload lists");
+        CK(M.upload(Lv.lty, &ip[20]), "upload lists");
         CK(M.upload(Lv.il_ptr, &ip[0]), "upload lists");
         CK(M.upload(Lv.il_src, &ip[1]), "upload lists");
         CK(M.upload(Lv.il_type, &ip[2]), "upload lists");
@@ -347,12 +352,12 @@ mlfma_status setup_device(mlfma_plan_t p)
     const int prec = p->opts.precisions;
     if (prec & (1 << MLFMA_FP32)) {
         p->a32.nr = nr; p->a32.ubox = d_ubox; p->a32.perm = d_perm;
-        CK(setup_precision<float>(p, p->a32, (const double2 *)near64, (const double2 *)V64, ints, tys), "setup FP32");
+        CK(setup_precision<float>(p, p->a32, (const double2 *)near64, (const double2 *)V64, ints, tys, ltys), "setup FP32");
         p->has32 = true;
     }
     if (prec & (1 << MLFMA_FP64)) {
         p->a64.nr = nr; p->a64.ubox = d_ubox; p->a64.perm = d_perm;
-        CK(setup_precision<double>(p, p->a64, (const double2 *)near64, (const double2 *)V64, ints, tys), "setup FP64");
+        CK(setup_precision<double>(p, p->a64, (const double2 *)near64, (const double2 *)V64, ints, tys, ltys), "setup FP64");
         p->has64 = true;
     }
     const size_t stage = (size_t)H.N * p->opts.max_batch * 2 * sizeof(double);

@@ -48,6 +48,9 @@ struct DevLevel {
     int nparent = 0, max_grp = 0;        // translation grouped by parent (level l-1)
     const int32_t *grp_ptr = nullptr, *grp_src = nullptr;
     const int16_t *grp_ty = nullptr;     // [entries][8]
+    const int32_t *lty_ptr = nullptr, *lty = nullptr;   // per parent: distinct types used
+    const int16_t *grp_lty = nullptr;    // [entries][8] index into the parent's type list, or -1
+    int max_lty = 0;
     const int32_t *pchild_ptr = nullptr; // parent level's child ranges into this level
     const R *alpha = nullptr;            // [ntype][K][2]
     const R *alpha_dk = nullptr;         // [ntype][K][2] d alpha / dk (derivative tables, when set up)

@@ -541,6 +541,28 @@ std::string build_plan_host(PlanHost &P, const double *verts, int64_t nv, const 
                 Lv.max_grp = std::max(Lv.max_grp, Lv.grp_ptr[pb + 1] - Lv.grp_ptr[pb]);
             }
             if (Lv.max_grp > 216) return "grouped source list longer than 216 (internal error)";
+            // distinct types per parent and the entries' local type indices
+            Lv.lty_ptr.assign(1, 0);
+            Lv.lty.clear();
+            Lv.grp_lty.assign(Lv.grp_ty.size(), (int16_t)-1);
+            Lv.max_lty = 0;
+            std::vector<int> local(Lv.ntype, -1);
+            for (int pb = 0; pb + 1 < (int)Lv.grp_ptr.size(); ++pb) {
+                const int base = (int)Lv.lty.size();
+                for (int e = Lv.grp_ptr[pb]; e < Lv.grp_ptr[pb + 1]; ++e)
+                    for (int c = 0; c < 8; ++c) {
+                        const int ty = Lv.grp_ty[(size_t)e * 8 + c];
+                        if (ty < 0) continue;
+                        if (local[ty] < 0) {
+                            local[ty] = (int)Lv.lty.size() - base;
+                            Lv.lty.push_back(ty);
+                        }
+                        Lv.grp_lty[(size_t)e * 8 + c] = (int16_t)local[ty];
+                    }
+                for (size_t i = base; i < Lv.lty.size(); ++i) local[Lv.lty[i]] = -1;
+                Lv.lty_ptr.push_back((int32_t)Lv.lty.size());
+                Lv.max_lty = std::max(Lv.max_lty, (int)Lv.lty.size() - base);
+            }
         }
         translation_table(Lv, k);
     }

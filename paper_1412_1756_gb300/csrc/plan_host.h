@@ -48,6 +48,11 @@ struct Level {
     std::vector<int32_t> grp_ptr, grp_src;
     std::vector<int16_t> grp_ty;    // [entries][8]
     int max_grp = 0;
+    // per parent, the distinct translation types its entries use
+    // (lty[lty_ptr[P] ..]) and each entry slot's index into that list or -1
+    std::vector<int32_t> lty_ptr, lty;
+    std::vector<int16_t> grp_lty;   // [entries][8]
+    int max_lty = 0;
     std::vector<int32_t> type_off;  // [ntype][3]
     int ntype = 0;
     std::vector<cd> alpha;          // [ntype][K]

@@ -361,27 +361,46 @@ __global__ void __launch_bounds__(256) k_radiate(const int32_t *__restrict__ box
 // sample (one alpha load feeds CB columns); ES consecutive lanes may split
 // the source list of one output and meet in a shuffle reduction (when a
 // level has too few outputs to fill the GPU).  All children's accumulators
-// live in registers.
-template <class R, int ES, int CB>
+// live in registers.  With SA the CTA first copies the coefficients it
+// needs - the parent's distinct translation types at the CTA's few samples -
+// into shared memory, and the entries carry local type indices.
+template <class R, int ES, int CB, bool SA>
 __global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B, int Bs, int accumulate)
 {
     using C = typename Cx<R>::T;
     __shared__ int s_src[216];
     __shared__ __align__(16) int16_t s_ty[216 * 8];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s_al = reinterpret_cast<C *>(smem_raw);   // SA: [local type][NQ]
     const int P = blockIdx.x;
     const int e0 = lv.grp_ptr[P], ne = lv.grp_ptr[P + 1] - e0;
     const int m0 = lv.pchild_ptr[P], nc = lv.pchild_ptr[P + 1] - m0;
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) s_src[e] = lv.grp_src[e0 + e];
-    for (int e = threadIdx.x; e < ne * 8; e += blockDim.x) s_ty[e] = lv.grp_ty[(int64_t)e0 * 8 + e];
-    __syncthreads();
     const int K = lv.K;
     const int BC = B / CB;                 // column groups (B is a multiple of CB)
+    const int outs = blockDim.x / ES;
+    const int q_lo = (blockIdx.y * outs) / BC;
+    const int NQ = min(K - 1, (blockIdx.y * outs + outs - 1) / BC) - q_lo + 1;
+    if (SA) {
+        const int l0 = lv.lty_ptr[P], nl = lv.lty_ptr[P + 1] - l0;
+        const C *al = reinterpret_cast<const C *>(lv.alpha);
+        for (int i = threadIdx.x; i < nl * NQ; i += blockDim.x) {
+            const int lt = i / NQ, qq = i - lt * NQ;
+            cp_async(s_al + i, al + (int64_t)lv.lty[l0 + lt] * K + q_lo + qq);
+        }
+        cp_async_commit();
+    }
+    const int16_t *tysrc = SA ? lv.grp_lty : lv.grp_ty;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) s_src[e] = lv.grp_src[e0 + e];
+    for (int e = threadIdx.x; e < ne * 8; e += blockDim.x) s_ty[e] = tysrc[(int64_t)e0 * 8 + e];
+    if (SA) cp_async_wait<0>();
+    __syncthreads();
     const int part = threadIdx.x % ES;
-    const int t = blockIdx.y * (blockDim.x / ES) + threadIdx.x / ES;
+    const int t = blockIdx.y * outs + threadIdx.x / ES;
     const bool valid = t < K * BC;
     const int q = valid ? t / BC : 0, b = valid ? (t % BC) * CB : 0;
     const C *S = reinterpret_cast<const C *>(lv.S);
-    const C *alpha = reinterpret_cast<const C *>(lv.alpha) + q;
+    const C *alpha = SA ? s_al + (q - q_lo) : reinterpret_cast<const C *>(lv.alpha) + q;
+    const int astride = SA ? NQ : K;
     C acc[8][2][CB];
 #pragma unroll
     for (int c = 0; c < 8; ++c)
@@ -403,9 +422,10 @@ __global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B, int Bs
             const int tw[4] = {tyv.x, tyv.y, tyv.z, tyv.w};
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
+                if (c >= nc) break;   // the parent's children occupy slots 0 .. nc-1
                 const int ty = (int)(int16_t)((tw[c >> 1] >> (16 * (c & 1))) & 0xffff);
                 if (ty >= 0) {
-                    const C al = alpha[(int64_t)ty * K];
+                    const C al = alpha[ty * astride];
 #pragma unroll
                     for (int k = 0; k < CB; ++k) {
                         cfma(acc[c][0][k], al, s0[k]);
@@ -1267,9 +1287,16 @@ cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs
 template <class R, int ES, int CB>
 cudaError_t launch_translate_es(const DevLevel<R> &Lv, int B, int Bs, int acc, cudaStream_t s)
 {
+    using C = typename Cx<R>::T;
     const int outs = Lv.K * (B / CB);
     dim3 grid(Lv.nparent, (outs + 128 / ES - 1) / (128 / ES));
-    k_translate<R, ES, CB><<<grid, 128, 0, s>>>(Lv, B, Bs, acc);
+    // samples one CTA touches, at most (its outputs may straddle a sample)
+    const int nq = std::min(Lv.K, (128 / ES - 1) / (B / CB) + 2);
+    const size_t smem = (size_t)Lv.max_lty * nq * sizeof(C);
+    if (Lv.lty && smem <= (size_t)48 * 1024)
+        k_translate<R, ES, CB, true><<<grid, 128, smem, s>>>(Lv, B, Bs, acc);
+    else
+        k_translate<R, ES, CB, false><<<grid, 128, 0, s>>>(Lv, B, Bs, acc);
     return cudaGetLastError();
 }
 
