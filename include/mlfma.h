@@ -169,6 +169,38 @@ mlfma_status mlfma_matvec_dk_adjoint(mlfma_plan_t plan, const void *x, int x_is_
                                      int64_t B, int prec, void *stream);
 
 /*
+ * y = X x with X = Im Z (Section IV, the reactance matrix), by the
+ * cos(kR)/R kernel of Eq. (CosKer) in the multilevel product of Eq. (XI):
+ * the same tree, lists and grids as mlfma_matvec, near blocks Im Z, and the
+ * translation table of Eq. (CosKer) (spherical Neumann functions y_l).  As
+ * Section V's point test shows, the expansion is accurate only where the
+ * addition theorem holds and the leaf boxes are not small: below about half
+ * a wavelength the y_l terms grow and the product loses accuracy (the
+ * low-frequency breakdown the paper assigns to LF-FMA).  For real x the
+ * result is real up to quadrature rounding; y is returned complex.
+ * Arguments as mlfma_matvec.  The first call in a precision builds the
+ * tables (an FP64 near-field fill; allocates and synchronises the device).
+ * Errors as mlfma_matvec.
+ */
+mlfma_status mlfma_matvec_x(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
+                            int64_t B, int prec, void *stream);
+
+/*
+ * y = R x with R = Re Z (Section IV, the resistance matrix as the paper
+ * defines it; the characteristic-mode pencil uses -R, see cm_ira_solve), by
+ * the sin(kR)/R kernel of Eq. (SinKer) in the multilevel form of Eq. (RI):
+ * the near part is each leaf box with itself only; every other pair of
+ * leaf boxes is translated once, at the level where their ancestors are
+ * siblings (boxes with the same parent), level 1 being the coarsest, with
+ * the spherical-Bessel table of Eq. (SinKer).  The regular kernel has no
+ * addition-theorem restriction, so nearby boxes translate too.  Needs a plan
+ * with at least 3 levels (MLFMA_ENOTSUP otherwise).  Arguments, result type
+ * and first-call behaviour as mlfma_matvec_x.
+ */
+mlfma_status mlfma_matvec_r(mlfma_plan_t plan, const void *x, int x_is_complex, void *y,
+                            int64_t B, int prec, void *stream);
+
+/*
  * y = Z x with HOST x and y (same layouts and types as mlfma_matvec): copies
  * x to the device, runs the product on `stream`, copies y back and waits for
  * the stream.  Uses the plan's own device staging buffers.
@@ -315,11 +347,22 @@ mlfma_status mlfma_plan_info(mlfma_plan_t plan, mlfma_info *info);
  *   MLFMA_X_ANTERP     float64 [K_child][K_parent]  dense form of the level ->
  *                                      level+1 anterpolation, built from its own
  *                                      (transposed, weighted) stencils
+ *   MLFMA_X_ALPHA_J    float64 [T][K][2] the j_l half of MLFMA_X_ALPHA,
+ *                                      sum i^l (2l+1) j_l(kr) P_l (= i x Eq. (SinKer)'s
+ *                                      alpha), same types as MLFMA_X_ALPHA_OFFS
+ *   MLFMA_X_ALPHA_Y    float64 [T][K][2] the y_l half, sum i^l (2l+1) y_l(kr) P_l
+ *                                      (= -i x Eq. (CosKer)'s alpha); ALPHA = J + i Y
+ *   MLFMA_X_SIB_ALPHA  float64 [T][K][2] sin-kernel table of the sibling
+ *                                      translations of Eq. (RI) at `level` (1..leaf)
+ *   MLFMA_X_SIB_OFFS   int32 [T][3]    their offsets (in boxes)
+ * The grid of level 1 exists for plans with at least 3 levels (it serves the
+ * sibling scheme only).
  */
 enum {
     MLFMA_X_PERM = 1, MLFMA_X_LEAF_BOX = 2, MLFMA_X_GRID = 3, MLFMA_X_ALPHA = 4,
     MLFMA_X_ALPHA_OFFS = 5, MLFMA_X_INTERP = 6, MLFMA_X_BOX_CENTERS = 7, MLFMA_X_NEAR_COUNT = 8,
-    MLFMA_X_ANTERP = 9
+    MLFMA_X_ANTERP = 9, MLFMA_X_ALPHA_J = 10, MLFMA_X_ALPHA_Y = 11, MLFMA_X_SIB_ALPHA = 12,
+    MLFMA_X_SIB_OFFS = 13
 };
 mlfma_status mlfma_export(mlfma_plan_t plan, int what, int level, void *dst, int64_t cap,
                           int64_t *needed);

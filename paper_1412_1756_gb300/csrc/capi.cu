@@ -116,11 +116,68 @@ struct mlfma_plan_s {
     const int32_t *d_ubox = nullptr;
     const double *d_grid = nullptr, *d_bc = nullptr;
     bool dk_ready[2] = {false, false};   // per precision
+    // products of the paper's kernel variants (Section IV): X u by the
+    // cos(kR)/R kernel (Eq. (XI)) and R u by the sin(kR)/R kernel with
+    // sibling translations (Eq. (RI)), set up on first use per precision
+    ProductArgs<float> ax32, ar32;
+    ProductArgs<double> ax64, ar64;
+    bool x_ready[2] = {false, false}, r_ready[2] = {false, false};
 };
 
 namespace {
 
 constexpr int kIntSlots = 22;   // device integer tables per level
+
+template <class R>
+cudaError_t upload_pairs(DevMem &M, const std::vector<cd> &v, const R **out)
+{
+    std::vector<R> t(2 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) { t[2 * i] = (R)v[i].real(); t[2 * i + 1] = (R)v[i].imag(); }
+    return M.upload(t, out);
+}
+
+// Tables of a parent level l (to and from level l + 1): phase shifts, the
+// packed interpolation stencils and the anterpolation stencils zero-padded
+// to dn_taps taps per row.
+template <class R>
+cudaError_t upload_parent_tables(DevMem &M, const PlanHost &H, const Level &Lv, DevLevel<R> &D)
+{
+    cudaError_t e;
+    if ((e = upload_pairs<R>(M, Lv.shift, &D.shift)) != cudaSuccess) return e;
+    auto pack = [](const Stencil &st) {
+        std::vector<Tap<R>> t(st.idx.size());
+        for (size_t i = 0; i < t.size(); ++i) {
+            t[i].i = st.idx[i] | ((!st.refl.empty() && st.refl[i]) ? kTapRefl : 0);
+            t[i].c = (R)st.coef[i];
+        }
+        return t;
+    };
+    if ((e = M.upload(pack(Lv.th_up), &D.thu)) != cudaSuccess) return e;
+    D.up_order = H.order;
+    if ((e = M.upload(pack(Lv.ph_up), &D.phu)) != cudaSuccess) return e;
+    if ((e = M.upload(pack(Lv.th_dn), &D.thd)) != cudaSuccess) return e;
+    if ((e = M.upload(pack(Lv.ph_dn), &D.phd)) != cudaSuccess) return e;
+    int longest = 0;
+    for (const Stencil *st : {&Lv.th_dn, &Lv.ph_dn})
+        for (size_t r = 0; r + 1 < st->ptr.size(); ++r) longest = std::max(longest, st->ptr[r + 1] - st->ptr[r]);
+    D.dn_taps = 0;
+    for (int tm : {16, 20, 24, 32})
+        if (!D.dn_taps && longest <= tm) D.dn_taps = tm;
+    if (!D.dn_taps) return cudaErrorInvalidValue;   // needs interpolation order <= 12
+    auto pad = [&](const Stencil &st) {
+        const int rows = (int)st.ptr.size() - 1;
+        std::vector<Tap<R>> t((size_t)rows * D.dn_taps, Tap<R>{0, (R)0});
+        for (int r = 0; r < rows; ++r)
+            for (int e2 = st.ptr[r]; e2 < st.ptr[r + 1]; ++e2) {
+                Tap<R> &tp = t[(size_t)r * D.dn_taps + (e2 - st.ptr[r])];
+                tp.i = st.idx[e2] | ((!st.refl.empty() && st.refl[e2]) ? kTapRefl : 0);
+                tp.c = (R)st.coef[e2];
+            }
+        return t;
+    };
+    if ((e = M.upload(pad(Lv.th_dn), &D.thd_pad)) != cudaSuccess) return e;
+    return M.upload(pad(Lv.ph_dn), &D.phd_pad);
+}
 
 template <class R>
 cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *near64, const double2 *V64,
@@ -159,7 +216,6 @@ cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *ne
     a.xp = static_cast<R *>(d);
     if ((e = M.alloc(&d, (size_t)H.N * Bmax * 2 * sizeof(R))) != cudaSuccess) return e;
     a.yp = static_cast<R *>(d);
-    int64_t scratch = 16;
     const double cfar = -H.k * H.k * H.eta / (4.0 * M_PI);
     for (int l = 2; l <= H.leaf; ++l) {
         const Level &Lv = H.lv[l];
@@ -178,53 +234,9 @@ cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *ne
         D.phu_ptr = ip[9]; D.phu_idx = ip[10];
         D.thd_ptr = ip[11]; D.thd_idx = ip[12]; D.thd_refl = ip[13];
         D.phd_ptr = ip[14]; D.phd_idx = ip[15];
-        std::vector<R> tmp(2 * Lv.alpha.size());
-        for (size_t i = 0; i < Lv.alpha.size(); ++i) { tmp[2 * i] = (R)Lv.alpha[i].real(); tmp[2 * i + 1] = (R)Lv.alpha[i].imag(); }
-        if ((e = M.upload(tmp, &D.alpha)) != cudaSuccess) return e;
+        if ((e = upload_pairs<R>(M, Lv.alpha, &D.alpha)) != cudaSuccess) return e;
         if (l < H.leaf) {
-            tmp.resize(2 * Lv.shift.size());
-            for (size_t i = 0; i < Lv.shift.size(); ++i) { tmp[2 * i] = (R)Lv.shift[i].real(); tmp[2 * i + 1] = (R)Lv.shift[i].imag(); }
-            if ((e = M.upload(tmp, &D.shift)) != cudaSuccess) return e;
-            auto cast = [](const std::vector<double> &v) { return std::vector<R>(v.begin(), v.end()); };
-            if ((e = M.upload(cast(Lv.th_up.coef), &D.thu_c)) != cudaSuccess) return e;
-            if ((e = M.upload(cast(Lv.ph_up.coef), &D.phu_c)) != cudaSuccess) return e;
-            if ((e = M.upload(cast(Lv.th_dn.coef), &D.thd_c)) != cudaSuccess) return e;
-            if ((e = M.upload(cast(Lv.ph_dn.coef), &D.phd_c)) != cudaSuccess) return e;
-            auto pack = [](const Stencil &st) {
-                std::vector<Tap<R>> t(st.idx.size());
-                for (size_t i = 0; i < t.size(); ++i) {
-                    t[i].i = st.idx[i] | ((!st.refl.empty() && st.refl[i]) ? kTapRefl : 0);
-                    t[i].c = (R)st.coef[i];
-                }
-                return t;
-            };
-            if ((e = M.upload(pack(Lv.th_up), &D.thu)) != cudaSuccess) return e;
-            D.up_order = H.order;
-            if ((e = M.upload(pack(Lv.ph_up), &D.phu)) != cudaSuccess) return e;
-            if ((e = M.upload(pack(Lv.th_dn), &D.thd)) != cudaSuccess) return e;
-            if ((e = M.upload(pack(Lv.ph_dn), &D.phd)) != cudaSuccess) return e;
-            int longest = 0;
-            for (const Stencil *st : {&Lv.th_dn, &Lv.ph_dn})
-                for (size_t r = 0; r + 1 < st->ptr.size(); ++r) longest = std::max(longest, st->ptr[r + 1] - st->ptr[r]);
-            D.dn_taps = 0;
-            for (int tm : {16, 20, 24, 32})
-                if (!D.dn_taps && longest <= tm) D.dn_taps = tm;
-            if (!D.dn_taps) return cudaErrorInvalidValue;   // needs interpolation order <= 12
-            auto pad = [&](const Stencil &st) {
-                const int rows = (int)st.ptr.size() - 1;
-                std::vector<Tap<R>> t((size_t)rows * D.dn_taps, Tap<R>{0, (R)0});
-                for (int r = 0; r < rows; ++r)
-                    for (int e2 = st.ptr[r]; e2 < st.ptr[r + 1]; ++e2) {
-                        Tap<R> &tp = t[(size_t)r * D.dn_taps + (e2 - st.ptr[r])];
-                        tp.i = st.idx[e2] | ((!st.refl.empty() && st.refl[e2]) ? kTapRefl : 0);
-                        tp.c = (R)st.coef[e2];
-                    }
-                return t;
-            };
-            if ((e = M.upload(pad(Lv.th_dn), &D.thd_pad)) != cudaSuccess) return e;
-            if ((e = M.upload(pad(Lv.ph_dn), &D.phd_pad)) != cudaSuccess) return e;
-            const Level &C = H.lv[l + 1];
-            scratch = std::max<int64_t>(scratch, (int64_t)C.nbox() * 2 * Lv.nth * C.nph * Bmax);
+            if ((e = upload_parent_tables<R>(M, H, Lv, D)) != cudaSuccess) return e;
         }
         std::vector<R> w(Lv.K);
         for (int q = 0; q < Lv.K; ++q)
@@ -236,8 +248,6 @@ cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *ne
         if ((e = M.alloc(&d, fsz)) != cudaSuccess) return e;
         D.G = static_cast<R *>(d);
     }
-    if ((e = M.alloc(&d, (size_t)scratch * 2 * sizeof(R))) != cudaSuccess) return e;
-    a.scratch = static_cast<R *>(d);
     return cudaSuccess;
 }
 
@@ -447,6 +457,97 @@ cudaError_t setup_dk(mlfma_plan_t p, ProductArgs<R> &a)
     return cudaSuccess;
 }
 
+// FP64 near values of a strip structure, reduced to one part and stored as
+// (value, 0) in precision R.
+template <class R>
+cudaError_t near_part(mlfma_plan_t p, const DevNear &nr, int64_t nnz, int part, const R **out)
+{
+    DevMem &M = p->mem;
+    cudaError_t e;
+    void *full, *dst;
+    if ((e = M.alloc(&full, (size_t)nnz * 16)) != cudaSuccess) return e;
+    if ((e = launch_near_fill(p->dm, nr, p->host.k, p->host.eta, (double2 *)full, 0)) != cudaSuccess) return e;
+    if ((e = M.alloc(&dst, (size_t)nnz * 2 * sizeof(R))) != cudaSuccess) return e;
+    e = sizeof(R) == 8 ? launch_part_c64((const double2 *)full, (double2 *)dst, nnz, part, 0)
+                       : launch_part_c32((const double2 *)full, (float2 *)dst, nnz, part, 0);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    M.release(full);
+    *out = static_cast<const R *>(dst);
+    return cudaSuccess;
+}
+
+// X u (Eq. (XI)): the standard tree, near blocks Im Z, translation table
+// sum i^l (2l+1) y_l P_l (Eq. (CosKer)'s alpha times -i, so that the far
+// constant -k^2 eta / 4 pi of the Z product carries over).
+template <class R>
+cudaError_t setup_x(mlfma_plan_t p, const ProductArgs<R> &a, ProductArgs<R> &ax)
+{
+    const PlanHost &H = p->host;
+    cudaError_t e;
+    ax = a;
+    if ((e = near_part<R>(p, a.nr, H.nnz, 1, &ax.near_val)) != cudaSuccess) return e;
+    for (int l = 2; l <= H.leaf; ++l)
+        if ((e = upload_pairs<R>(p->mem, H.lv[l].alpha_y, &ax.lv[l].alpha)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// R u (Eq. (RI)): near part the leaf box itself; every other pair of leaf
+// boxes translated once, at the level where their ancestors are siblings
+// (coarsest level 1), with sum i^l (2l+1) j_l P_l (Eq. (SinKer)'s alpha
+// times i).  Levels >= 2 share the fields, grids and stencils of the
+// standard tree; level 1 gets its own.
+template <class R>
+cudaError_t setup_r(mlfma_plan_t p, const ProductArgs<R> &a, ProductArgs<R> &ar)
+{
+    const PlanHost &H = p->host;
+    DevMem &M = p->mem;
+    const int Bmax = p->opts.max_batch;
+    cudaError_t e;
+    ar = a;
+    DevNear sn = a.nr;
+    if ((e = M.upload(H.self_off, &sn.strip_off)) != cudaSuccess) return e;
+    if ((e = M.upload(H.self_col_ptr, &sn.col_ptr)) != cudaSuccess) return e;
+    if ((e = M.upload(H.self_col, &sn.strip_col)) != cudaSuccess) return e;
+    sn.max_cols = H.max_leaf;
+    ar.nr = sn;
+    if ((e = near_part<R>(p, sn, H.self_nnz, 0, &ar.near_val)) != cudaSuccess) return e;
+    ar.coarsest = 1;
+    for (int l = 1; l <= H.leaf; ++l) {
+        const Level &Lv = H.lv[l];
+        const SibLevel &S = H.sib[l];
+        DevLevel<R> &D = ar.lv[l];
+        if (l == 1) {
+            D = DevLevel<R>();
+            D.nbox = Lv.nbox();
+            D.L = Lv.L; D.nth = Lv.nth; D.nph = Lv.nph; D.K = Lv.K;
+            if ((e = M.upload(Lv.parent, &D.parent)) != cudaSuccess) return e;
+            if ((e = M.upload(Lv.octant, &D.octant)) != cudaSuccess) return e;
+            if ((e = M.upload(Lv.child_ptr, &D.child_ptr)) != cudaSuccess) return e;
+            if ((e = M.upload(H.lv[0].child_ptr, &D.pchild_ptr)) != cudaSuccess) return e;
+            if ((e = upload_parent_tables<R>(M, H, Lv, D)) != cudaSuccess) return e;
+            std::vector<R> w(Lv.K);
+            for (int q = 0; q < Lv.K; ++q) w[q] = (R)(Lv.wt[q / Lv.nph] * 2.0 * M_PI / Lv.nph);
+            if ((e = M.upload(w, &D.wq)) != cudaSuccess) return e;
+            void *d;
+            const size_t fsz = (size_t)D.nbox * 2 * Lv.K * Bmax * 2 * sizeof(R);
+            if ((e = M.alloc(&d, fsz)) != cudaSuccess) return e;
+            D.S = static_cast<R *>(d);
+            if ((e = M.alloc(&d, fsz)) != cudaSuccess) return e;
+            D.G = static_cast<R *>(d);
+        }
+        D.nparent = H.lv[l - 1].nbox();
+        D.ntype = S.ntype;
+        D.max_grp = S.max_grp;
+        if ((e = M.upload(S.grp_ptr, &D.grp_ptr)) != cudaSuccess) return e;
+        if ((e = M.upload(S.grp_src, &D.grp_src)) != cudaSuccess) return e;
+        if ((e = M.upload(S.grp_ty, &D.grp_ty)) != cudaSuccess) return e;
+        D.lty_ptr = nullptr; D.lty = nullptr; D.grp_lty = nullptr; D.max_lty = 0;
+        if ((e = upload_pairs<R>(M, S.alpha, &D.alpha)) != cudaSuccess) return e;
+    }
+    return cudaDeviceSynchronize();
+}
+
 mlfma_status check_plan(mlfma_plan_t p)
 {
     if (!p) return fail(MLFMA_EINVAL, "plan is NULL");
@@ -469,10 +570,13 @@ void release_streams(mlfma_plan_t p)
 
 // The core pass (near field and far pass) for (precision, columns), captured
 // once into a CUDA graph on the plan's streams and replayed afterwards.
+enum { KIND_Z = 0, KIND_DK = 1, KIND_X = 2, KIND_R = 3 };
+
 template <class R>
-mlfma_status core_graph(mlfma_plan_t p, const ProductArgs<R> &a, int prec, int dk, cudaGraphExec_t *out)
+mlfma_status core_graph(mlfma_plan_t p, const ProductArgs<R> &a, int prec, int kind, cudaGraphExec_t *out)
 {
-    auto key = std::make_pair(prec + 2 * dk, a.B);
+    const int dk = kind == KIND_DK;
+    auto key = std::make_pair(prec + 2 * kind, a.B);
     auto it = p->graphs.find(key);
     if (it != p->graphs.end()) {
         *out = it->second;
@@ -499,8 +603,9 @@ mlfma_status core_graph(mlfma_plan_t p, const ProductArgs<R> &a, int prec, int d
 
 template <class R>
 mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int xc, void *yd, int Bu, int adjoint,
-                 int dk, cudaStream_t s, double *stage_ms)
+                 int kind, cudaStream_t s, double *stage_ms)
 {
+    const int dk = kind == KIND_DK;
     cudaError_t e;
     if (stage_ms) {
         StageClock &clk = p->clock;
@@ -529,7 +634,7 @@ mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int
     }
     if ((e = launch_prepare<R>(a, xd, xc, Bu, adjoint, s)) != cudaSuccess) return cuda_fail(e, "prepare");
     cudaGraphExec_t ex;
-    mlfma_status st = core_graph<R>(p, a, prec, dk, &ex);
+    mlfma_status st = core_graph<R>(p, a, prec, kind, &ex);
     if (st != MLFMA_OK) return st;
     if ((e = cudaGraphLaunch(ex, s)) != cudaSuccess) return cuda_fail(e, "graph launch");
     if ((e = launch_finalize<R>(a, yd, xc, Bu, adjoint, s)) != cudaSuccess) return cuda_fail(e, "finalize");
@@ -537,8 +642,9 @@ mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int
 }
 
 mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream, int adjoint,
-                     bool host, double *stage_ms = nullptr, int dk = 0)
+                     bool host, double *stage_ms = nullptr, int kind = KIND_Z)
 {
+    const int dk = kind == KIND_DK;
     if (check_plan(p)) return MLFMA_EINVAL;
     if (!p->on_device) return fail(MLFMA_EINVAL, "plan was built host-only; products need a device plan");
     if (!x || !y) return fail(MLFMA_EINVAL, "x or y is NULL");
@@ -558,6 +664,18 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
         if (e0 != cudaSuccess) return cuda_fail(e0, "dZ/dk tables");
         p->dk_ready[prec] = true;
     }
+    if (kind == KIND_R && p->host.leaf < 2)
+        return fail(MLFMA_ENOTSUP, "the sin-kernel product needs a plan with at least 3 levels");
+    if (kind == KIND_X && !p->x_ready[prec]) {
+        cudaError_t e0 = prec == MLFMA_FP64 ? setup_x<double>(p, p->a64, p->ax64) : setup_x<float>(p, p->a32, p->ax32);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "cos-kernel tables");
+        p->x_ready[prec] = true;
+    }
+    if (kind == KIND_R && !p->r_ready[prec]) {
+        cudaError_t e0 = prec == MLFMA_FP64 ? setup_r<double>(p, p->a64, p->ar64) : setup_r<float>(p, p->a32, p->ar32);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "sin-kernel tables");
+        p->r_ready[prec] = true;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t rsz = prec == MLFMA_FP64 ? 8 : 4;
     const size_t xbytes = (size_t)p->host.N * B * (xc ? 2 : 1) * rsz;
@@ -573,13 +691,13 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
     }
     mlfma_status st;
     if (prec == MLFMA_FP64) {
-        ProductArgs<double> a = p->a64;
+        ProductArgs<double> a = kind == KIND_X ? p->ax64 : kind == KIND_R ? p->ar64 : p->a64;
         a.B = (int)Bi;
-        st = run<double>(p, a, prec, xd, xc, yd, (int)B, adjoint, dk, s, stage_ms);
+        st = run<double>(p, a, prec, xd, xc, yd, (int)B, adjoint, kind, s, stage_ms);
     } else {
-        ProductArgs<float> a = p->a32;
+        ProductArgs<float> a = kind == KIND_X ? p->ax32 : kind == KIND_R ? p->ar32 : p->a32;
         a.B = (int)Bi;
-        st = run<float>(p, a, prec, xd, xc, yd, (int)B, adjoint, dk, s, stage_ms);
+        st = run<float>(p, a, prec, xd, xc, yd, (int)B, adjoint, kind, s, stage_ms);
     }
     if (st != MLFMA_OK) return st;
     if (host) {
@@ -725,13 +843,23 @@ mlfma_status mlfma_matvec_host(mlfma_plan_t p, const void *x, int xc, void *y, i
 
 mlfma_status mlfma_matvec_dk(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)
 {
-    return product(p, x, xc, y, B, prec, stream, 0, false, nullptr, 1);
+    return product(p, x, xc, y, B, prec, stream, 0, false, nullptr, KIND_DK);
 }
 
 mlfma_status mlfma_matvec_dk_adjoint(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec,
                                      void *stream)
 {
-    return product(p, x, xc, y, B, prec, stream, 1, false, nullptr, 1);
+    return product(p, x, xc, y, B, prec, stream, 1, false, nullptr, KIND_DK);
+}
+
+mlfma_status mlfma_matvec_x(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)
+{
+    return product(p, x, xc, y, B, prec, stream, 0, false, nullptr, KIND_X);
+}
+
+mlfma_status mlfma_matvec_r(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)
+{
+    return product(p, x, xc, y, B, prec, stream, 0, false, nullptr, KIND_R);
 }
 
 mlfma_status mlfma_profile_stages(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream,
@@ -798,7 +926,7 @@ mlfma_status mlfma_export(mlfma_plan_t p, int what, int level, void *dst, int64_
         put(H.lv[level].center.data(), H.lv[level].center.size() * sizeof(double));
         break;
     case MLFMA_X_GRID: {
-        if (!far_level) return fail(MLFMA_EINVAL, "level has no far work");
+        if (!(far_level || (level == 1 && H.leaf >= 1))) return fail(MLFMA_EINVAL, "level has no far work");
         const Level &Lv = H.lv[level];
         std::vector<double> g(4 * (size_t)Lv.K);
         for (int q = 0; q < Lv.K; ++q) {
@@ -817,6 +945,21 @@ mlfma_status mlfma_export(mlfma_plan_t p, int what, int level, void *dst, int64_
     case MLFMA_X_ALPHA_OFFS:
         if (!far_level) return fail(MLFMA_EINVAL, "level has no far work");
         put(H.lv[level].type_off.data(), H.lv[level].type_off.size() * sizeof(int32_t));
+        break;
+    case MLFMA_X_ALPHA_J:
+    case MLFMA_X_ALPHA_Y: {
+        if (!far_level) return fail(MLFMA_EINVAL, "level has no far work");
+        const std::vector<cd> &t = what == MLFMA_X_ALPHA_J ? H.lv[level].alpha_j : H.lv[level].alpha_y;
+        put(t.data(), t.size() * sizeof(cd));
+        break;
+    }
+    case MLFMA_X_SIB_ALPHA:
+    case MLFMA_X_SIB_OFFS:
+        if (!(level >= 1 && level <= H.leaf)) return fail(MLFMA_EINVAL, "no sibling translations at this level");
+        if (what == MLFMA_X_SIB_ALPHA)
+            put(H.sib[level].alpha.data(), H.sib[level].alpha.size() * sizeof(cd));
+        else
+            put(H.sib[level].type_off.data(), H.sib[level].type_off.size() * sizeof(int32_t));
         break;
     case MLFMA_X_INTERP: {
         if (!(level >= 2 && level < H.leaf)) return fail(MLFMA_EINVAL, "no interpolation into this level");

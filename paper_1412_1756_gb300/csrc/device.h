@@ -92,13 +92,17 @@ cudaError_t launch_leaf_patterns(const DevMesh &m, const int32_t *ubox, const do
                                  const double *grid /* [K][9]: khat, theta-hat, phi-hat */, double k, double2 *V, cudaStream_t s,
                                  int mode = 0);
 cudaError_t launch_cast_c64_to_c32(const double2 *src, float2 *dst, int64_t n, cudaStream_t s);
+// dst[i] = (Re src[i], 0) (part 0) or (Im src[i], 0) (part 1)
+cudaError_t launch_part_c64(const double2 *src, double2 *dst, int64_t n, int part, cudaStream_t s);
+cudaError_t launch_part_c32(const double2 *src, float2 *dst, int64_t n, int part, cudaStream_t s);
 
 // ------------------------------------------------------------ product ---
 template <class R>
 struct ProductArgs {
     int64_t n = 0;
     int B = 0;                 // internal real columns
-    int leaf = 0, levels = 0;  // levels with far work: 2..leaf
+    int leaf = 0, levels = 0;  // levels with far work: coarsest..leaf
+    int coarsest = 2;          // 2 for the standard tree, 1 for the sibling scheme
     DevNear nr;
     const R *near_val = nullptr;    // complex, strip layout
     const R *V = nullptr;           // leaf patterns [N][K][2] complex
@@ -110,7 +114,6 @@ struct ProductArgs {
     const int64_t *perm = nullptr;  // [N]
     R *xp = nullptr;                // [N][B] real
     R *yp = nullptr;                // [N][B] complex
-    R *scratch = nullptr;           // interpolation scratch
     DevLevel<R> lv[22];
 };
 

@@ -71,7 +71,6 @@ size_t carve(ProductArgs<R> &a, int B, unsigned char *base)
         a.lv[l].S = take(f);
         a.lv[l].G = take(f);
     }
-    a.scratch = nullptr;   // the fused interpolation kernels stage in shared memory
     return off;
 }
 

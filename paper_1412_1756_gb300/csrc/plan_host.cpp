@@ -236,6 +236,8 @@ static void translation_table(Level &Lv, double k)
 {
     Lv.alpha.assign((size_t)Lv.ntype * Lv.K, cd(0, 0));
     Lv.alpha_dk.assign((size_t)Lv.ntype * Lv.K, cd(0, 0));
+    Lv.alpha_j.assign((size_t)Lv.ntype * Lv.K, cd(0, 0));
+    Lv.alpha_y.assign((size_t)Lv.ntype * Lv.K, cd(0, 0));
     std::vector<double> jn, yn, jd, yd, P(Lv.L + 1);
     for (int t = 0; t < Lv.ntype; ++t) {
         double r[3] = {Lv.a * Lv.type_off[3 * t], Lv.a * Lv.type_off[3 * t + 1], Lv.a * Lv.type_off[3 * t + 2]};
@@ -245,10 +247,12 @@ static void translation_table(Level &Lv, double k)
         sph_bessel_y(Lv.L, x, yn);
         sph_bessel_j(Lv.L + 1, x, jd);
         sph_bessel_y(Lv.L + 1, x, yd);
-        std::vector<cd> coef(Lv.L + 1), coefd(Lv.L + 1);
+        std::vector<cd> coef(Lv.L + 1), coefd(Lv.L + 1), coefj(Lv.L + 1), coefy(Lv.L + 1);
         cd il(1, 0);
         for (int n = 0; n <= Lv.L; ++n) {
             coef[n] = il * (2.0 * n + 1.0) * cd(jn[n], yn[n]);
+            coefj[n] = il * (2.0 * n + 1.0) * jn[n];
+            coefy[n] = il * (2.0 * n + 1.0) * yn[n];
             const cd hd = n == 0 ? -cd(jd[1], yd[1])
                                  : cd(jd[n - 1], yd[n - 1]) - (n + 1.0) / x * cd(jd[n], yd[n]);
             coefd[n] = il * (2.0 * n + 1.0) * rn * hd;
@@ -258,7 +262,7 @@ static void translation_table(Level &Lv, double k)
             double kh[3];
             khat(Lv, q, kh);
             double c = (kh[0] * r[0] + kh[1] * r[1] + kh[2] * r[2]) / rn;
-            cd s(0, 0), sd(0, 0);
+            cd s(0, 0), sd(0, 0), sj(0, 0), sy(0, 0);
             double p0 = 1.0, p1 = c;
             for (int n = 0; n <= Lv.L; ++n) {
                 double pn;
@@ -271,9 +275,51 @@ static void translation_table(Level &Lv, double k)
                 }
                 s += coef[n] * pn;
                 sd += coefd[n] * pn;
+                sj += coefj[n] * pn;
+                sy += coefy[n] * pn;
             }
             Lv.alpha[(size_t)t * Lv.K + q] = s;
             Lv.alpha_dk[(size_t)t * Lv.K + q] = sd;
+            Lv.alpha_j[(size_t)t * Lv.K + q] = sj;
+            Lv.alpha_y[(size_t)t * Lv.K + q] = sy;
+        }
+    }
+}
+
+// Eq. (SinKer)'s table up to its factor -i: sum_{l=0}^{L} i^l (2l+1)
+// j_l(k r) P_l(khat . rhat) for the sibling offsets of one level.
+static void sibling_table(const Level &Lv, SibLevel &S, double k)
+{
+    S.alpha.assign((size_t)S.ntype * Lv.K, cd(0, 0));
+    std::vector<double> jn;
+    for (int t = 0; t < S.ntype; ++t) {
+        double r[3] = {Lv.a * S.type_off[3 * t], Lv.a * S.type_off[3 * t + 1], Lv.a * S.type_off[3 * t + 2]};
+        double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        sph_bessel_j(Lv.L, k * rn, jn);
+        std::vector<cd> coef(Lv.L + 1);
+        cd il(1, 0);
+        for (int n = 0; n <= Lv.L; ++n) {
+            coef[n] = il * (2.0 * n + 1.0) * jn[n];
+            il *= cd(0, 1);
+        }
+        for (int q = 0; q < Lv.K; ++q) {
+            double kh[3];
+            khat(Lv, q, kh);
+            double c = (kh[0] * r[0] + kh[1] * r[1] + kh[2] * r[2]) / rn;
+            cd s(0, 0);
+            double p0 = 1.0, p1 = c;
+            for (int n = 0; n <= Lv.L; ++n) {
+                double pn;
+                if (n == 0) pn = p0;
+                else if (n == 1) pn = p1;
+                else {
+                    pn = ((2.0 * n - 1.0) * c * p1 - (n - 1.0) * p0) / n;
+                    p0 = p1;
+                    p1 = pn;
+                }
+                s += coef[n] * pn;
+            }
+            S.alpha[(size_t)t * Lv.K + q] = s;
         }
     }
 }
@@ -467,6 +513,53 @@ std::string build_plan_host(PlanHost &P, const double *verts, int64_t nv, const 
         }
         P.nnz = P.strip_off.back();
         if (P.strip_col.size() > (size_t)INT32_MAX) return "near structure too large";
+        P.self_off.assign(1, 0);
+        P.self_col_ptr.assign(1, 0);
+        P.self_col.clear();
+        for (int b = 0; b < Lf.nbox(); ++b) {
+            const int64_t nr = P.box_ptr[b + 1] - P.box_ptr[b];
+            for (int32_t u = P.box_ptr[b]; u < P.box_ptr[b + 1]; ++u) P.self_col.push_back(u);
+            P.self_col_ptr.push_back((int32_t)P.self_col.size());
+            P.self_off.push_back(P.self_off.back() + nr * nr);
+        }
+        P.self_nnz = P.self_off.back();
+    }
+
+    // --- sibling translations (sin-kernel product): level 1 .. leaf
+    P.sib.assign(levels, SibLevel());
+    if (leaf >= 1) make_grid(P.lv[1], k, digits);
+    for (int l = 1; l <= leaf; ++l) {
+        const Level &Lv = P.lv[l], &Pa = P.lv[l - 1];
+        SibLevel &S = P.sib[l];
+        std::vector<int> type_of(27, -1);
+        S.grp_ptr.assign(1, 0);
+        for (int pb = 0; pb < Pa.nbox(); ++pb) {
+            const int c0 = Pa.child_ptr[pb], nc = Pa.child_ptr[pb + 1] - c0;
+            for (int s = c0; s < c0 + nc; ++s) {
+                int64_t X, Y, Z;
+                unmorton(Lv.code[s], X, Y, Z);
+                int16_t ty[8];
+                for (int c = 0; c < 8; ++c) ty[c] = -1;
+                for (int c = 0; c < nc; ++c) {
+                    if (c0 + c == s) continue;
+                    int64_t x, y, z;
+                    unmorton(Lv.code[c0 + c], x, y, z);
+                    const int dx = (int)(x - X), dy = (int)(y - Y), dz = (int)(z - Z);   // r_m - r_m'
+                    const int key = (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
+                    if (type_of[key] < 0) {
+                        type_of[key] = S.ntype++;
+                        S.type_off.push_back(dx);
+                        S.type_off.push_back(dy);
+                        S.type_off.push_back(dz);
+                    }
+                    ty[c] = (int16_t)type_of[key];
+                }
+                S.grp_src.push_back(s);
+                for (int c = 0; c < 8; ++c) S.grp_ty.push_back(ty[c]);
+            }
+            S.grp_ptr.push_back((int32_t)S.grp_src.size());
+            S.max_grp = std::max(S.max_grp, nc);
+        }
     }
 
     // --- far levels: grids, interaction lists, translation tables
@@ -567,8 +660,11 @@ std::string build_plan_host(PlanHost &P, const double *verts, int64_t nv, const 
         translation_table(Lv, k);
     }
 
-    // --- interpolation (child l+1 -> parent l) and phase shifts, 2 <= l < leaf
-    for (int l = 2; l < leaf; ++l) {
+    for (int l = 1; l <= leaf; ++l) sibling_table(P.lv[l], P.sib[l], k);
+
+    // --- interpolation (child l+1 -> parent l) and phase shifts, 1 <= l < leaf
+    // (level 1 serves the sibling scheme only)
+    for (int l = 1; l < leaf; ++l) {
         Level &Pa = P.lv[l];
         const Level &C = P.lv[l + 1];
         theta_stencil(C.th, Pa.th, order, Pa.th_up);

@@ -57,12 +57,28 @@ struct Level {
     int ntype = 0;
     std::vector<cd> alpha;          // [ntype][K]
     std::vector<cd> alpha_dk;       // [ntype][K]: d alpha / dk
+    // alpha = alpha_j + i alpha_y: the j_l and y_l halves of Eq. (8),
+    // sum i^l (2l+1) j_l P_l and sum i^l (2l+1) y_l P_l (translation of the
+    // sin(kR)/R and cos(kR)/R kernels, Eqs. (SinKer), (CosKer), up to -i, i)
+    std::vector<cd> alpha_j, alpha_y;
     // to/from children (2 <= l < leaf)
     std::vector<cd> shift;          // [8][K]: exp(i k khat.(r_parent - r_child))
     std::vector<cd> shift_dk;       // [8][K]: d shift / dk = i khat.(r_parent - r_child) shift
     Stencil th_up, ph_up;           // child grid -> this grid (rows: nth / nph of this level)
     Stencil ph_dn, th_dn;           // weighted transposes (rows: child nph / child nth)
     int nbox() const { return (int)code.size(); }
+};
+
+// Translations between sibling boxes at one level (the sin-kernel product
+// of Eq. (RI): every pair of distinct leaf boxes is translated once, at the
+// level where their ancestors are siblings; coarsest level 1).
+struct SibLevel {
+    int ntype = 0;
+    std::vector<int32_t> type_off;           // [ntype][3] r_m - r_m' in boxes
+    std::vector<int32_t> grp_ptr, grp_src;   // per parent (level l-1): its children as sources
+    std::vector<int16_t> grp_ty;             // [entries][8] type per child slot or -1 (itself)
+    int max_grp = 0;
+    std::vector<cd> alpha;                   // [ntype][K] sum i^l (2l+1) j_l(k r) P_l
 };
 
 struct PlanHost {
@@ -78,13 +94,18 @@ struct PlanHost {
     std::vector<int64_t> perm;      // leaf-order position -> canonical index
     std::vector<int32_t> leaf_box;  // canonical index -> leaf box
     std::vector<int32_t> box_ptr;   // [nleaf+1] positions in leaf order
-    std::vector<Level> lv;          // [levels]
+    std::vector<Level> lv;          // [levels]; level 1 carries a grid and stencils for the sibling scheme
+    std::vector<SibLevel> sib;      // [levels], used for 1 <= l <= leaf
     // near field: per leaf box, a dense strip [rows of the box] x
     // [columns of all neighbour boxes], column-major
     std::vector<int32_t> nb_ptr, nb_box;
     std::vector<int64_t> strip_off; // [nleaf+1] element offsets
     std::vector<int32_t> col_ptr;   // [nleaf+1] into strip_col
     std::vector<int32_t> strip_col; // leaf-order unknown of each strip column
+    // self strips (the leaf box's own columns): the near part of Eq. (RI)
+    std::vector<int64_t> self_off;  // [nleaf+1]
+    std::vector<int32_t> self_col_ptr, self_col;
+    int64_t self_nnz = 0;
     int64_t nnz = 0;
     int max_leaf = 0;
 };

@@ -1416,7 +1416,7 @@ inline cudaError_t tick(StageClock *clk, int stage, cudaStream_t s)
 template <class R>
 cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClock *clk)
 {
-    const int B = a.B, leaf = a.leaf;
+    const int B = a.B, leaf = a.leaf, top = a.coarsest;
     const bool serial = clk != nullptr || cs.far == nullptr;
     cudaStream_t s0 = cs.main;
     cudaStream_t sf = serial ? s0 : cs.far;
@@ -1430,7 +1430,7 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
     }
     TRY(launch_near<R>(a, s0));
     TRY(tick(clk, STAGE_NEAR, s0));
-    if (leaf >= 2) {
+    if (leaf >= top) {
         TRY(launch_radiate<R>(a, B, sf));
         TRY(tick(clk, STAGE_RADIATE, sf));
         if (!serial) {
@@ -1439,10 +1439,10 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
         }
         TRY(launch_translate<R>(a.lv[leaf], B, B, 0, st));
         TRY(tick(clk, STAGE_TRANSLATE + leaf, st));
-        for (int l = leaf - 1; l >= 2; --l) {
+        for (int l = leaf - 1; l >= top; --l) {
             TRY(launch_up<R>(a.lv[l], a.lv[l + 1], B, B, 0, sf));
             TRY(tick(clk, STAGE_UP + l, sf));
-            if (l == 2) {
+            if (l == top) {
                 TRY(launch_translate<R>(a.lv[l], B, B, 0, sf));
                 TRY(tick(clk, STAGE_TRANSLATE + l, sf));
             } else {
@@ -1458,7 +1458,7 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
             TRY(cudaEventRecord(cs.ev[2], st));
             TRY(cudaStreamWaitEvent(sf, cs.ev[2], 0));
         }
-        for (int l = 2; l < leaf; ++l) {
+        for (int l = top; l < leaf; ++l) {
             TRY(launch_down<R>(a.lv[l], a.lv[l + 1], B, B, sf));
             TRY(tick(clk, STAGE_DOWN + l, sf));
         }

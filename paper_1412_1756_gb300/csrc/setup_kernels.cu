@@ -360,6 +360,16 @@ __global__ void k_cast(const double2 *src, float2 *dst, int64_t n)
     }
 }
 
+template <class C>
+__global__ void k_part(const double2 *src, C *dst, int64_t n, int part)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = src[i];
+        using T = decltype(C::x);
+        dst[i] = C{(T)(part ? v.y : v.x), (T)0};
+    }
+}
+
 cudaError_t upload_rule()
 {
     // seven-point degree-5 rule (Cowper / Dunavant), weights relative to area
@@ -419,6 +429,22 @@ cudaError_t launch_leaf_patterns(const DevMesh &m, const int32_t *ubox, const do
     case 2: k_leaf_patterns<2><<<blocks, 256, 0, s>>>(m, ubox, box_center, K, grid, k, V); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part_c64(const double2 *src, double2 *dst, int64_t n, int part, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_part<double2><<<blocks, 256, 0, s>>>(src, dst, n, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part_c32(const double2 *src, float2 *dst, int64_t n, int part, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_part<float2><<<blocks, 256, 0, s>>>(src, dst, n, part);
     return cudaGetLastError();
 }
 

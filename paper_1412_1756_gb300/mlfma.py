@@ -17,12 +17,14 @@ FP64 = 0
 FP32 = 1
 MAX_LEVELS = 22
 
-X_PERM, X_LEAF_BOX, X_GRID, X_ALPHA, X_ALPHA_OFFS, X_INTERP, X_BOX_CENTERS, X_NEAR_COUNT, X_ANTERP = range(1, 10)
+(X_PERM, X_LEAF_BOX, X_GRID, X_ALPHA, X_ALPHA_OFFS, X_INTERP, X_BOX_CENTERS, X_NEAR_COUNT, X_ANTERP, X_ALPHA_J,
+ X_ALPHA_Y, X_SIB_ALPHA, X_SIB_OFFS) = range(1, 14)
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ENOTSUP"}
 
 EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg_edges", "mlfma_matvec",
-            "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
+            "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint", "mlfma_matvec_x",
+            "mlfma_matvec_r", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
             "mlfma_profile_stages", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
             "mlfma_destroy", "mlfma_last_error"]
 CM_ZINV_R, CM_XINV_R = 0, 1
@@ -87,7 +89,7 @@ def load(build_if_missing: bool = False):
     L.mlfma_num_unknowns.argtypes = [P, ctypes.POINTER(I64)]
     L.mlfma_rwg_edges.argtypes = [P, P, P]
     for f in ("mlfma_matvec", "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint",
-              "mlfma_matvec_host", "mlfma_matvec_noalloc"):
+              "mlfma_matvec_x", "mlfma_matvec_r", "mlfma_matvec_host", "mlfma_matvec_noalloc"):
         getattr(L, f).argtypes = [P, P, I, P, I64, I, P]
     L.mlfma_sync.argtypes = [P, P]
     L.mlfma_profile_stages.argtypes = [P, P, I, P, I64, I, P, P]
@@ -179,11 +181,11 @@ class MlfmaPlan:
             return buf.view(np.int32)
         if what == X_NEAR_COUNT:
             return buf.view(np.int64)
-        if what == X_ALPHA_OFFS:
+        if what in (X_ALPHA_OFFS, X_SIB_OFFS):
             return buf.view(np.int32).reshape(-1, 3)
         if what == X_GRID:
             return buf.view(np.float64).reshape(-1, 4)
-        if what == X_ALPHA:
+        if what in (X_ALPHA, X_ALPHA_J, X_ALPHA_Y, X_SIB_ALPHA):
             return buf.view(np.complex128)
         if what == X_BOX_CENTERS:
             return buf.view(np.float64).reshape(-1, 3)
@@ -252,6 +254,14 @@ class MlfmaPlan:
     def matvec_dk_adjoint(self, x, y=None, stream=None):
         """y = (dZ/dk)^H x."""
         return self._dk_product(self._lib.mlfma_matvec_dk_adjoint, x, y, stream)
+
+    def matvec_x(self, x, y=None, stream=None):
+        """y = X x, X = Im Z, by the cos-kernel product (include/mlfma.h: mlfma_matvec_x)."""
+        return self._product(self._lib.mlfma_matvec_x, x, y, stream)
+
+    def matvec_r(self, x, y=None, stream=None):
+        """y = R x, R = Re Z, by the sin-kernel sibling product (mlfma_matvec_r)."""
+        return self._product(self._lib.mlfma_matvec_r, x, y, stream)
 
     def matvec_host(self, x: np.ndarray, prec: int = FP32, y: np.ndarray = None, stream=None) -> np.ndarray:
         """y = Z x for HOST arrays (copies inside the call; waits for completion)."""

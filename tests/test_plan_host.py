@@ -102,19 +102,31 @@ def test_grid_integrates_band_limited_exactly():
     assert abs(val - 4 * math.pi * math.sin(x) / x) < 1e-12
 
 
-def _point_test(a, d0, ri, rm, rj, rmp, offset=(2, 0, 0)):
+def _point_test(a, d0, ri, rm, rj, rmp, offset=(2, 0, 0), kernel="exp"):
+    """Relative error of the plane-wave form of one kernel between two points
+    through the library's own translation table at level 2:
+    exp(ikr)/r by Eq. (7) with Eq. (8) ("exp"); cos(kr)/r by Eq. (CosKer)
+    ("cos"), whose alpha is i x the exported y_l table, so the prefactor
+    ik/4pi becomes -k/4pi; sin(kr)/r by Eq. (SinKer) ("sin"), alpha = -i x the
+    exported j_l table, prefactor k/4pi; "sin-sib" uses the sibling table of
+    Eq. (RI) (nearby offsets)."""
     k = 2 * math.pi
     v, t = workloads.cube(4 * a, 8)
     P = M.MlfmaPlan(v, t, k, 3, d0, host_only=True)
     g, kh, _, _ = _grid(P, 2)
-    al = P.export(M.X_ALPHA, 2).reshape(-1, g.shape[0])
-    offs = P.export(M.X_ALPHA_OFFS, 2)
+    what, offs_what, pref = {"exp": (M.X_ALPHA, M.X_ALPHA_OFFS, 1j * k / (4 * math.pi)),
+                             "cos": (M.X_ALPHA_Y, M.X_ALPHA_OFFS, -k / (4 * math.pi)),
+                             "sin": (M.X_ALPHA_J, M.X_ALPHA_OFFS, k / (4 * math.pi)),
+                             "sin-sib": (M.X_SIB_ALPHA, M.X_SIB_OFFS, k / (4 * math.pi))}[kernel]
+    al = P.export(what, 2).reshape(-1, g.shape[0])
+    offs = P.export(offs_what, 2)
     ti = [i for i, o in enumerate(offs) if tuple(o) == offset][0]
     ri, rm, rj, rmp = (np.asarray(z) * a for z in (ri, rm, rj, rmp))
     assert np.allclose(rm - rmp, np.array(offset) * a)
     r = np.linalg.norm(ri - rj)
-    exact = np.exp(1j * k * r) / r
-    approx = 1j * k / (4 * math.pi) * np.sum(g[:, 2] * np.exp(1j * k * (kh @ ((ri - rm) + (rmp - rj)))) * al[ti])
+    exact = {"exp": np.exp(1j * k * r), "cos": np.cos(k * r), "sin": np.sin(k * r),
+             "sin-sib": np.sin(k * r)}[kernel] / r
+    approx = pref * np.sum(g[:, 2] * np.exp(1j * k * (kh @ ((ri - rm) + (rmp - rj)))) * al[ti])
     return abs(approx - exact) / abs(exact)
 
 
@@ -137,6 +149,38 @@ def test_e1_point_test_case1():
         errs.append(_point_test(a, 3.0, (2.9999, 0, 1.0), (2.5, 0.5, 0.5), (0.9999, 1.0, 0.0), (0.5, 0.5, 0.5)))
     assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:])), errs
     assert errs[0] < 1e-2 and errs[1] < 3e-3 and max(errs[2:]) < 1e-3, errs
+
+
+CASE1 = ((2.9999, 0, 1.0), (2.5, 0.5, 0.5), (0.9999, 1.0, 0.0), (0.5, 0.5, 0.5))
+CASE2 = ((1.0001, 0, 0), (1.5, 0.5, 0.5), (0.9999, 1.0, 0.0), (0.5, 0.5, 0.5))
+
+
+def test_e1_point_test_cos_sin_case1():
+    """Section V, Case 1 (the addition theorem holds): the sin(kr)/r kernel
+    is reproduced at every box size; the cos(kr)/r kernel only from about
+    half a wavelength up, its error growing as the box shrinks (the y_l
+    terms of Eq. (CosKer)); both halves add up to the exp kernel's table."""
+    es, ec = [], []
+    for a in (0.125, 0.25, 0.5, 1.0, 2.0):
+        es.append(_point_test(a, 3.0, *CASE1, kernel="sin"))
+        ec.append(_point_test(a, 3.0, *CASE1, kernel="cos"))
+    assert max(es) < 1e-8, es
+    assert ec[0] > ec[2] and ec[1] > ec[3], ec
+    assert max(ec[3:]) < 1e-3, ec
+    v, t = workloads.cube(2.0, 8)
+    P = M.MlfmaPlan(v, t, 2 * math.pi, 3, 3.0, host_only=True)
+    al, aj, ay = (P.export(w, 2) for w in (M.X_ALPHA, M.X_ALPHA_J, M.X_ALPHA_Y))
+    assert np.abs(al - (aj + 1j * ay)).max() < 1e-12 * np.abs(al).max()
+
+
+def test_e1_point_test_sin_case2_nearby_groups():
+    """Section V, Case 2: observer and source in touching groups (the
+    addition theorem for exp(ikr)/r is violated, |r_im + r_m'j| > |r_mm'|);
+    the regular sin(kr)/r kernel is still reproduced, through the sibling
+    table that Eq. (RI) uses for nearby groups."""
+    for a in (0.25, 0.5, 1.0, 2.0):
+        err = _point_test(a, 3.0, *CASE2, offset=(1, 0, 0), kernel="sin-sib")
+        assert err < 1e-6, (a, err)
 
 
 @pytest.mark.parametrize("order,tol", [(6, 3e-3), (8, 1e-3), (10, 5e-4)])
