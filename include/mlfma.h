@@ -370,6 +370,49 @@ mlfma_status mlfma_export(mlfma_plan_t plan, int what, int level, void *dst, int
 /* Release everything the plan owns (waits for its work).  NULL is a no-op. */
 void mlfma_destroy(mlfma_plan_t plan);
 
+/*
+ * Frequency sweeps (Section V sweeps frequencies one after another; here
+ * the plans of a sweep share the GPU).  A set holds one plan per wavenumber
+ * ks[0..nk-1] on one mesh (levels, digits and opts as mlfma_plan; each plan
+ * has its own grids and tables).  Memory admission: the host tables of every
+ * plan are built first and give an estimate of its peak device bytes; the
+ * plans are grouped, in wavenumber order, into waves whose estimates fit
+ * `budget_bytes` (<= 0: 90 % of the device's free memory), and the first
+ * wave is put on the device.  A plan larger than the budget is MLFMA_ENOMEM.
+ */
+typedef struct mlfma_set_s *mlfma_set_t;
+mlfma_status mlfma_set_create(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                              const double *ks, int nk, int levels, double digits,
+                              const mlfma_opts *opts, int64_t budget_bytes, mlfma_set_t *out);
+
+/*
+ * y_f = Z(k_f) x_f for every wavenumber of the set.
+ *  x  device: [nk][N][B] (x_shared = 0) or one [N][B] block for all
+ *     (x_shared = 1); real or, with x_is_complex, interleaved complex
+ *  y  device: [nk][N][B] interleaved complex
+ * Types, B and prec as mlfma_matvec (prec must be in opts.precisions).  The
+ * far and near passes of all plans of a wave run as parallel branches of one
+ * CUDA graph, captured on first use per (wave, precision, columns) and
+ * replayed; with one wave nothing is rebuilt between calls.  With several
+ * waves each call waits for a wave's work, releases its plans' device memory
+ * and builds the next wave's (near fields and patterns are recomputed):
+ * that is the price of a budget smaller than the sweep.
+ */
+mlfma_status mlfma_set_matvec(mlfma_set_t set, const void *x, int x_shared, int x_is_complex,
+                              void *y, int64_t B, int prec, void *stream);
+
+/* Per wavenumber (arrays of nk, each may be NULL): admission wave, estimated
+ * peak device bytes, device bytes now held (0 when not admitted). */
+mlfma_status mlfma_set_info(mlfma_set_t set, int *nk, int *waves, int *wave_of,
+                            int64_t *est_bytes, int64_t *device_bytes);
+
+/* The set's plan for ks[f] (owned by the set; a device plan while its wave is
+ * admitted, host-only otherwise). */
+mlfma_status mlfma_set_plan(mlfma_set_t set, int f, mlfma_plan_t *plan);
+
+/* Release the set and its plans (waits for their work).  NULL is a no-op. */
+void mlfma_set_destroy(mlfma_set_t set);
+
 /* Message of the last failure on this thread ("" if none). */
 const char *mlfma_last_error(void);
 

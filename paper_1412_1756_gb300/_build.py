@@ -17,7 +17,8 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB_NAME = "libmlfma_gb300.so"
 LIB = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan_host.cpp", "setup_kernels.cu", "product_kernels.cu", "capi.cu", "noalloc.cu", "cm_solver.cpp"]
+SOURCES = ["plan_host.cpp", "setup_kernels.cu", "product_kernels.cu", "capi.cu", "noalloc.cu", "cm_solver.cpp",
+           "plan_set.cu"]
 
 
 def _nvcc():

@@ -548,6 +548,57 @@ cudaError_t setup_r(mlfma_plan_t p, const ProductArgs<R> &a, ProductArgs<R> &ar)
     return cudaDeviceSynchronize();
 }
 
+void release_streams(mlfma_plan_t p);
+
+// Device half of a plan (tables, fields, streams) for the host tables it
+// already holds; on failure everything it allocated is released.
+mlfma_status attach_device(mlfma_plan_s *p)
+{
+    if ((p->opts.precisions & 3) == 0) return fail(MLFMA_EINVAL, "no precision requested");
+    int dev = p->opts.device;
+    if (dev < 0) {
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    }
+    p->device = dev;
+    DeviceGuard g(dev);
+    mlfma_status st;
+    try {
+        st = setup_device(p);
+    } catch (const std::bad_alloc &) {
+        st = fail(MLFMA_ENOMEM, "host allocation failed during device setup");
+    }
+    if (st != MLFMA_OK) {
+        cudaDeviceSynchronize();
+        release_streams(p);
+        p->mem.free_all();
+        return st;
+    }
+    p->on_device = true;
+    return MLFMA_OK;
+}
+
+// Back to a host-only plan: waits for the plan's work and frees its device
+// memory, streams, events and graphs.
+void detach_device(mlfma_plan_s *p)
+{
+    if (!p->on_device && !p->cs.main) return;
+    DeviceGuard g(p->device);
+    cudaDeviceSynchronize();
+    release_streams(p);
+    p->mem.free_all();
+    p->mem.bytes = 0;
+    p->cs = CoreStreams();
+    p->ev_in = p->ev_out = nullptr;
+    p->clock = StageClock();
+    p->a32 = ProductArgs<float>(); p->ax32 = ProductArgs<float>(); p->ar32 = ProductArgs<float>();
+    p->a64 = ProductArgs<double>(); p->ax64 = ProductArgs<double>(); p->ar64 = ProductArgs<double>();
+    p->has32 = p->has64 = false;
+    for (int i = 0; i < 2; ++i) p->dk_ready[i] = p->x_ready[i] = p->r_ready[i] = false;
+    p->stage_x = p->stage_y = nullptr;
+    p->on_device = false;
+}
+
 mlfma_status check_plan(mlfma_plan_t p)
 {
     if (!p) return fail(MLFMA_EINVAL, "plan is NULL");
@@ -729,6 +780,116 @@ bool plan_product_view(mlfma_plan_t p, int prec, ProductArgs<float> *a32, Produc
 
 void set_last_error(const std::string &msg) { g_err = msg; }
 
+// Peak device bytes that mlfma_plan's device setup allocates for these host
+// tables and options (every table, both FP64 setup tables, fields sized for
+// max_batch, staging), used to admit plans before building them.
+int64_t plan_device_bytes_estimate(const PlanHost &H, const mlfma_opts &o)
+{
+    const int64_t nt = (int64_t)(H.T.size() / 3), N = H.N, Bmax = o.max_batch;
+    int64_t b = (int64_t)H.V.size() * 8 + (int64_t)H.T.size() * 4 + nt * (21 + 9 + 1 + 3 + 1) * 8;
+    b += N * (2 * 4 + 6 * 8 + 8 + 4 + 8);
+    b += (int64_t)(H.box_ptr.size() + H.col_ptr.size()) * 4 + (int64_t)H.strip_off.size() * 8 +
+         (int64_t)H.strip_col.size() * 4;
+    b += H.nnz * 16;
+    const int64_t Kl = H.leaf >= 2 ? H.lv[H.leaf].K : 0;
+    b += N * Kl * 2 * 16;
+    int64_t per_prec_fields = 0, per_prec_tables = 0, ints = 0;
+    for (int l = 2; l <= H.leaf; ++l) {
+        const Level &Lv = H.lv[l];
+        per_prec_fields += 2 * (int64_t)Lv.nbox() * 2 * Lv.K * Bmax * 2;   // S and G, complex
+        per_prec_tables += (int64_t)Lv.ntype * Lv.K * 2 + 8 * (int64_t)Lv.K * 2 + Lv.K;
+        ints += (int64_t)(Lv.grp_ptr.size() + Lv.grp_src.size() + Lv.il_ptr.size() + Lv.il_src.size() +
+                          Lv.il_type.size() + Lv.lty_ptr.size() + Lv.lty.size() + 3 * Lv.nbox()) * 4 +
+                (int64_t)(Lv.grp_ty.size() + Lv.grp_lty.size()) * 2;
+    }
+    b += ints;
+    for (int prec = 0; prec < 2; ++prec) {
+        if (!(o.precisions & (1 << prec))) continue;
+        const int64_t r = prec == MLFMA_FP64 ? 8 : 4;
+        if (prec == MLFMA_FP32) b += H.nnz * 8 + N * Kl * 2 * 8;
+        b += N * Bmax * r * 3 + (per_prec_fields + per_prec_tables) * r;
+    }
+    b += 2 * N * Bmax * 2 * 8;
+    return b + b / 16 + ((int64_t)64 << 20);   // allocation granularity and small tables
+}
+
+// Pieces of a Z product for callers that capture several plans into one
+// graph: the core pass forked from `fork` onto the plan's streams, its
+// completion recorded in the plan's own event (*done); and the input and
+// output reorderings on a stream.  The plan must be a device plan with the
+// precision set up; nothing here allocates.
+static mlfma_status check_branch(mlfma_plan_t p, int prec, int64_t Bi)
+{
+    if (!p || !p->on_device) return fail(MLFMA_EINVAL, "plan is NULL or host-only");
+    if (Bi < 1 || Bi > p->opts.max_batch) return fail(MLFMA_EINVAL, "columns exceed the plan's max_batch");
+    if ((prec == MLFMA_FP32 && !p->has32) || (prec == MLFMA_FP64 && !p->has64) || (prec != 0 && prec != 1))
+        return fail(MLFMA_EINVAL, "precision not set up in the plan");
+    return MLFMA_OK;
+}
+
+mlfma_status plan_enqueue_core(mlfma_plan_t p, int prec, int64_t Bi, cudaEvent_t fork, cudaEvent_t *done)
+{
+    mlfma_status st = check_branch(p, prec, Bi);
+    if (st != MLFMA_OK) return st;
+    DeviceGuard g(p->device);
+    cudaError_t e;
+    if ((e = cudaStreamWaitEvent(p->cs.main, fork, 0)) != cudaSuccess) return cuda_fail(e, "fork");
+    if (prec == MLFMA_FP64) {
+        ProductArgs<double> a = p->a64;
+        a.B = (int)Bi;
+        e = launch_core<double>(a, p->cs, nullptr);
+    } else {
+        ProductArgs<float> a = p->a32;
+        a.B = (int)Bi;
+        e = launch_core<float>(a, p->cs, nullptr);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "core pass");
+    if ((e = cudaEventRecord(p->ev_out, p->cs.main)) != cudaSuccess) return cuda_fail(e, "join");
+    *done = p->ev_out;
+    return MLFMA_OK;
+}
+
+mlfma_status plan_enqueue_io(mlfma_plan_t p, int prec, const void *x, int xc, void *y, int64_t B, int finalize,
+                             cudaStream_t s)
+{
+    mlfma_status st = check_branch(p, prec, B * (xc ? 2 : 1));
+    if (st != MLFMA_OK) return st;
+    DeviceGuard g(p->device);
+    cudaError_t e;
+    if (prec == MLFMA_FP64) {
+        ProductArgs<double> a = p->a64;
+        a.B = (int)(B * (xc ? 2 : 1));
+        e = finalize ? launch_finalize<double>(a, y, xc, (int)B, 0, s) : launch_prepare<double>(a, x, xc, (int)B, 0, s);
+    } else {
+        ProductArgs<float> a = p->a32;
+        a.B = (int)(B * (xc ? 2 : 1));
+        e = finalize ? launch_finalize<float>(a, y, xc, (int)B, 0, s) : launch_prepare<float>(a, x, xc, (int)B, 0, s);
+    }
+    return e == cudaSuccess ? MLFMA_OK : cuda_fail(e, finalize ? "finalize" : "prepare");
+}
+
+int64_t plan_device_bytes(mlfma_plan_t p) { return p ? p->mem.bytes : 0; }
+
+const PlanHost *plan_host(mlfma_plan_t p) { return p ? &p->host : nullptr; }
+
+mlfma_status plan_attach_device(mlfma_plan_t p, const mlfma_opts &o)
+{
+    if (!p) return fail(MLFMA_EINVAL, "plan is NULL");
+    if (p->on_device) return MLFMA_OK;
+    const int interp = p->opts.interp_order;
+    const double eta = p->opts.eta;
+    p->opts = o;
+    p->opts.host_only = 0;
+    p->opts.interp_order = interp;   // the host tables were built with these
+    p->opts.eta = eta;
+    return attach_device(p);
+}
+
+void plan_detach_device(mlfma_plan_t p)
+{
+    if (p) detach_device(p);
+}
+
 // Host copy of the near-field strips (leaf order, FP64 when the plan has
 // FP64 values, else widened from FP32) and the plan's host tables.
 bool plan_near_host(mlfma_plan_t p, std::vector<std::complex<double>> &vals, const PlanHost **host)
@@ -783,27 +944,8 @@ mlfma_status mlfma_plan(const double *verts, int64_t nv, const int32_t *tris, in
     }
     if (!err.empty()) return fail(MLFMA_EINVAL, err);
     if (!p->opts.host_only) {
-        if ((p->opts.precisions & 3) == 0) return fail(MLFMA_EINVAL, "no precision requested");
-        int dev = p->opts.device;
-        if (dev < 0) {
-            cudaError_t e = cudaGetDevice(&dev);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-        }
-        p->device = dev;
-        DeviceGuard g(dev);
-        mlfma_status st;
-        try {
-            st = setup_device(p.get());
-        } catch (const std::bad_alloc &) {
-            st = fail(MLFMA_ENOMEM, "host allocation failed during device setup");
-        }
-        if (st != MLFMA_OK) {
-            cudaDeviceSynchronize();
-            release_streams(p.get());
-            p->mem.free_all();
-            return st;
-        }
-        p->on_device = true;
+        mlfma_status st = attach_device(p.get());
+        if (st != MLFMA_OK) return st;
     }
     p->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = p.release();

@@ -26,6 +26,7 @@ EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg
             "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint", "mlfma_matvec_x",
             "mlfma_matvec_r", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
             "mlfma_profile_stages", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
+            "mlfma_set_create", "mlfma_set_matvec", "mlfma_set_info", "mlfma_set_plan", "mlfma_set_destroy",
             "mlfma_destroy", "mlfma_last_error"]
 CM_ZINV_R, CM_XINV_R = 0, 1
 STAGE_COUNT = 71
@@ -99,10 +100,17 @@ def load(build_if_missing: bool = False):
     L.mlfma_export.argtypes = [P, I, I, P, I64, ctypes.POINTER(I64)]
     L.mlfma_destroy.argtypes = [P]
     L.mlfma_destroy.restype = None
+    L.mlfma_set_create.argtypes = [P, I64, P, I64, P, I, I, ctypes.c_double, ctypes.POINTER(Opts), I64,
+                                   ctypes.POINTER(P)]
+    L.mlfma_set_matvec.argtypes = [P, P, I, I, P, I64, I, P]
+    L.mlfma_set_info.argtypes = [P, P, P, P, P, P]
+    L.mlfma_set_plan.argtypes = [P, I, ctypes.POINTER(P)]
+    L.mlfma_set_destroy.argtypes = [P]
+    L.mlfma_set_destroy.restype = None
     L.mlfma_last_error.argtypes = []
     L.mlfma_last_error.restype = ctypes.c_char_p
     for f in EXPORTED:
-        if f not in ("mlfma_destroy", "mlfma_last_error"):
+        if f not in ("mlfma_destroy", "mlfma_set_destroy", "mlfma_last_error"):
             getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -121,8 +129,16 @@ class MlfmaPlan:
     """A plan for y = Z x on one mesh at one wavenumber (include/mlfma.h)."""
 
     def __init__(self, verts, tris, k, levels, digits=3.0, interp_order=10, max_batch=64,
-                 precisions=(FP32, FP64), host_only=False, device=None, eta=None):
+                 precisions=(FP32, FP64), host_only=False, device=None, eta=None, _handle=None):
         L = load()
+        if _handle is not None:   # a plan owned by a MlfmaPlanSet
+            self._lib, self._h, self._owned = L, _handle, False
+            self.k, self.max_batch, self.host_only = float(k), int(max_batch), False
+            n = ctypes.c_int64()
+            _check(L.mlfma_num_unknowns(_handle, ctypes.byref(n)))
+            self.n = int(n.value)
+            return
+        self._owned = True
         self._lib = L
         v = np.ascontiguousarray(verts, dtype=np.float64)
         t = np.ascontiguousarray(tris, dtype=np.int32)
@@ -317,7 +333,8 @@ class MlfmaPlan:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.mlfma_destroy(self._h)
+            if getattr(self, "_owned", True):
+                self._lib.mlfma_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -376,3 +393,81 @@ def efie_product(plan: MlfmaPlan, x, k):
     if _MlfmaZ is None:
         _MlfmaZ = _autograd_function()
     return _MlfmaZ.apply(x, k, plan)
+
+
+class MlfmaPlanSet:
+    """One plan per wavenumber on one mesh, admitted by device memory, with
+    the products of a wave in one graph (include/mlfma.h: mlfma_set_*)."""
+
+    def __init__(self, verts, tris, ks, levels, digits=3.0, interp_order=10, max_batch=64,
+                 precisions=(FP32, FP64), device=None, budget_bytes=0):
+        L = load()
+        self._lib = L
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tris, dtype=np.int32)
+        kk = np.ascontiguousarray(np.asarray(ks, dtype=np.float64).reshape(-1))
+        o = Opts()
+        _check(L.mlfma_default_opts(ctypes.byref(o)))
+        o.interp_order, o.max_batch = int(interp_order), int(max_batch)
+        o.precisions = sum(1 << p for p in precisions)
+        if device is None:
+            import torch
+            device = torch.cuda.current_device()
+        o.device = int(device)
+        h = ctypes.c_void_p()
+        _check(L.mlfma_set_create(_np_ptr(v), v.shape[0], _np_ptr(t), t.shape[0], _np_ptr(kk), kk.shape[0],
+                                  int(levels), float(digits), ctypes.byref(o), int(budget_bytes), ctypes.byref(h)))
+        self._h = h
+        self.ks = kk.copy()
+        self.max_batch = int(max_batch)
+        p0 = ctypes.c_void_p()
+        _check(L.mlfma_set_plan(h, 0, ctypes.byref(p0)))
+        n = ctypes.c_int64()
+        _check(L.mlfma_num_unknowns(p0, ctypes.byref(n)))
+        self.n = int(n.value)
+
+    def info(self) -> dict:
+        nk = len(self.ks)
+        waves = ctypes.c_int()
+        wave_of = np.zeros(nk, np.int32)
+        est = np.zeros(nk, np.int64)
+        dev = np.zeros(nk, np.int64)
+        _check(self._lib.mlfma_set_info(self._h, None, ctypes.byref(waves), _np_ptr(wave_of), _np_ptr(est),
+                                        _np_ptr(dev)))
+        return {"waves": waves.value, "wave_of": wave_of.tolist(), "est_bytes": est.tolist(),
+                "device_bytes": dev.tolist()}
+
+    def plan(self, f: int) -> "MlfmaPlan":
+        h = ctypes.c_void_p()
+        _check(self._lib.mlfma_set_plan(self._h, int(f), ctypes.byref(h)))
+        return MlfmaPlan(None, None, self.ks[f], 0, max_batch=self.max_batch, _handle=h)
+
+    def matvec(self, x, y=None, stream=None):
+        """y[f] = Z(k_f) x[f] for x [nk, N, B] (or one [N, B] block for every
+        wavenumber); returns [nk, N, B] complex."""
+        import torch
+        nk = len(self.ks)
+        shared = x.dim() == 2 or (x.dim() == 1)
+        x3 = x.reshape(self.n, -1) if shared else x.reshape(nk, self.n, -1)
+        x3 = x3.contiguous()
+        prec = MlfmaPlan._prec_of(x3.dtype)
+        xc = 1 if x3.is_complex() else 0
+        cdt = torch.complex64 if prec == FP32 else torch.complex128
+        B = x3.shape[-1]
+        if y is None:
+            y = torch.empty((nk, self.n, B), dtype=cdt, device=x3.device)
+        s = torch.cuda.current_stream(x3.device).cuda_stream if stream is None else stream
+        _check(self._lib.mlfma_set_matvec(self._h, ctypes.c_void_p(x3.data_ptr()), 1 if shared else 0, xc,
+                                          ctypes.c_void_p(y.data_ptr()), B, prec, ctypes.c_void_p(s)))
+        return y
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mlfma_set_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
