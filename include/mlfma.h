@@ -308,6 +308,24 @@ mlfma_status mlfma_cm_default_opts(mlfma_cm_opts *opts);
 mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opts, double *lambda, double *J,
                           mlfma_cm_stats *stats);
 
+/*
+ * Wavenumber slopes of characteristic values, for tracking modes over
+ * frequency: for each pair (lambda_m, J_m) of X J = lambda R J (R = -Re Z,
+ * X = Im Z, J real, e.g. from cm_ira_solve), by first-order perturbation of
+ * the pencil,  dlambda_m/dk = J^T (X' - lambda R') J / (J^T R J)  with
+ * X' = Im dZ/dk, R' = -Re dZ/dk.  Each column costs one mlfma_matvec and
+ * one mlfma_matvec_dk in `prec` (the first dZ/dk call builds its tables);
+ * the dot products are FP64 on the host.  Within a degenerate cluster the
+ * individual slopes depend on the basis the eigensolver returned; their sum
+ * over the cluster does not.
+ *  lambda  host [nev]       J  host [N][nev] (the layout cm_ira_solve writes)
+ *  dlambda host [nev] out
+ * Synchronous.  Allocates device buffers for min(nev, max_batch/2) columns.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+mlfma_status cm_eig_derivatives(mlfma_plan_t plan, int nev, const double *lambda, const double *J,
+                                int prec, double *dlambda);
+
 /* Summary of a plan (host copy; all fields filled). */
 #define MLFMA_MAX_LEVELS 22
 typedef struct {

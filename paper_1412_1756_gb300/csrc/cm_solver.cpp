@@ -17,6 +17,8 @@
 #include "../../include/mlfma.h"
 #include "plan_host.h"
 
+#include <cuda_runtime.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -666,4 +668,79 @@ extern "C" mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opt
     }
     if (!converged) return fail(MLFMA_ENOTCONV, "Arnoldi did not converge within max_restarts");
     return MLFMA_OK;
+}
+
+// ----------------------------------------- characteristic-value slopes ---
+namespace mlfma {
+template <class R> struct ProductArgs;
+bool plan_product_view(mlfma_plan_t p, int prec, ProductArgs<float> *a32, ProductArgs<double> *a64, int *device,
+                       int *max_batch, int64_t *n);
+}  // namespace mlfma
+
+// d lambda / dk of characteristic pairs (Section II, Eq. (GEP), with the
+// pencil's k-derivative): for X J = lambda R J with R = -Re Z, X = Im Z and
+// a real J,  d lambda/dk = J^T (X' - lambda R') J / (J^T R J),  where
+// X' J = Im(Z' J), R' J = -Re(Z' J) and R J = -Re(Z J) come from one
+// mlfma_matvec_dk and one mlfma_matvec per column (GPU, `prec`); the dot
+// products are FP64 on the host.
+extern "C" mlfma_status cm_eig_derivatives(mlfma_plan_t plan, int nev, const double *lambda, const double *J,
+                                           int prec, double *dlambda)
+{
+    if (!plan || !lambda || !J || !dlambda || nev < 1) return fail(MLFMA_EINVAL, "NULL argument or nev < 1");
+    int dev = 0, max_batch = 0;
+    int64_t n = 0;
+    if (!plan_product_view(plan, prec, nullptr, nullptr, &dev, &max_batch, &n))
+        return fail(MLFMA_EINVAL, "plan is host-only or the precision is not set up");
+    const int chunk = std::max(1, max_batch / 2);
+    const size_t rsz = prec == MLFMA_FP64 ? 8 : 4;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+    void *dx = nullptr, *dz = nullptr, *dd = nullptr;
+    mlfma_status st = MLFMA_OK;
+    cudaError_t e = cudaMalloc(&dx, (size_t)n * chunk * rsz);
+    if (e == cudaSuccess) e = cudaMalloc(&dz, (size_t)n * chunk * 2 * rsz);
+    if (e == cudaSuccess) e = cudaMalloc(&dd, (size_t)n * chunk * 2 * rsz);
+    if (e != cudaSuccess) st = fail(MLFMA_ENOMEM, "cm_eig_derivatives: device buffers");
+    std::vector<char> hx((size_t)n * chunk * rsz), hz((size_t)n * chunk * 2 * rsz), hd(hz.size());
+    for (int c0 = 0; c0 < nev && st == MLFMA_OK; c0 += chunk) {
+        const int cb = std::min(chunk, nev - c0);
+        for (int64_t r = 0; r < n; ++r)
+            for (int c = 0; c < cb; ++c) {
+                const double v = J[r * nev + c0 + c];
+                if (prec == MLFMA_FP64) reinterpret_cast<double *>(hx.data())[r * cb + c] = v;
+                else reinterpret_cast<float *>(hx.data())[r * cb + c] = (float)v;
+            }
+        if ((e = cudaMemcpy(dx, hx.data(), (size_t)n * cb * rsz, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            st = fail(MLFMA_ECUDA, std::string("cm_eig_derivatives: ") + cudaGetErrorString(e));
+            break;
+        }
+        if ((st = mlfma_matvec(plan, dx, 0, dz, cb, prec, nullptr)) != MLFMA_OK) break;
+        if ((st = mlfma_matvec_dk(plan, dx, 0, dd, cb, prec, nullptr)) != MLFMA_OK) break;
+        if ((e = cudaMemcpy(hz.data(), dz, (size_t)n * cb * 2 * rsz, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(hd.data(), dd, (size_t)n * cb * 2 * rsz, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            st = fail(MLFMA_ECUDA, std::string("cm_eig_derivatives: ") + cudaGetErrorString(e));
+            break;
+        }
+        auto val = [&](const std::vector<char> &h, int64_t r, int c, int part) -> double {
+            const size_t i = ((size_t)r * cb + c) * 2 + part;
+            return prec == MLFMA_FP64 ? reinterpret_cast<const double *>(h.data())[i]
+                                      : (double)reinterpret_cast<const float *>(h.data())[i];
+        };
+        for (int c = 0; c < cb; ++c) {
+            double jrj = 0, jxd = 0, jrd = 0;
+            for (int64_t r = 0; r < n; ++r) {
+                const double j = J[r * nev + c0 + c];
+                jrj -= j * val(hz, r, c, 0);
+                jxd += j * val(hd, r, c, 1);
+                jrd -= j * val(hd, r, c, 0);
+            }
+            dlambda[c0 + c] = (jxd - lambda[c0 + c] * jrd) / jrj;
+        }
+    }
+    cudaFree(dx);
+    cudaFree(dz);
+    cudaFree(dd);
+    if (prev != dev) cudaSetDevice(prev);
+    return st;
 }

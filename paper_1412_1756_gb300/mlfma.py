@@ -26,6 +26,7 @@ EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg
             "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint", "mlfma_matvec_x",
             "mlfma_matvec_r", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
             "mlfma_profile_stages", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
+            "cm_eig_derivatives",
             "mlfma_set_create", "mlfma_set_matvec", "mlfma_set_info", "mlfma_set_plan", "mlfma_set_destroy",
             "mlfma_destroy", "mlfma_last_error"]
 CM_ZINV_R, CM_XINV_R = 0, 1
@@ -96,6 +97,7 @@ def load(build_if_missing: bool = False):
     L.mlfma_profile_stages.argtypes = [P, P, I, P, I64, I, P, P]
     L.mlfma_cm_default_opts.argtypes = [ctypes.POINTER(CmOpts)]
     L.cm_ira_solve.argtypes = [P, ctypes.POINTER(CmOpts), P, P, ctypes.POINTER(CmStats)]
+    L.cm_eig_derivatives.argtypes = [P, I, P, P, I, P]
     L.mlfma_plan_info.argtypes = [P, ctypes.POINTER(Info)]
     L.mlfma_export.argtypes = [P, I, I, P, I64, ctypes.POINTER(I64)]
     L.mlfma_destroy.argtypes = [P]
@@ -327,6 +329,15 @@ class MlfmaPlan:
                                       ctypes.byref(st)))
         stats = {f: getattr(st, f) for f, _ in CmStats._fields_}
         return lam, J, stats
+
+    def cm_derivatives(self, lam, J, prec=FP64) -> np.ndarray:
+        """d lambda / dk of characteristic pairs (include/mlfma.h: cm_eig_derivatives)."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(-1)
+        J = np.ascontiguousarray(J, dtype=np.float64).reshape(self.n, lam.shape[0])
+        out = np.zeros(lam.shape[0])
+        _check(self._lib.cm_eig_derivatives(self._h, lam.shape[0], _np_ptr(lam), _np_ptr(J), int(prec),
+                                            _np_ptr(out)))
+        return out
 
     def sync(self, stream=None):
         _check(self._lib.mlfma_sync(self._h, ctypes.c_void_p(stream or 0)))
