@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip mlfma_tune (built-in launch shapes)")
     ap.add_argument("--stages-only", action="store_true",
                     help="build the plan and run one serial per-stage pass (for profilers), print stage times")
     return ap.parse_args()
@@ -300,6 +302,14 @@ def main():
         ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
         return reduce_max(ms, dist, "cuda")
 
+    # --- launch shapes tuned for both timed products before any timing
+    tuned = None
+    if not a.no_tune:
+        d32, t32 = plan.tune(B, FP32)
+        d64, t64 = plan.tune(1, FP64)
+        tuned = {"fp32_b%d_stage_sum_ms" % B: [round(d32, 4), round(t32, 4)],
+                 "fp64_b1_stage_sum_ms": [round(d64, 4), round(t64, 4)]}
+
     # --- mixed precision, batched (the headline)
     with ClockSampler(local) as clk:
         ms = timed(lambda: plan.matvec(x32, y32), a.steps, a.warmup)
@@ -383,7 +393,9 @@ def main():
             "dtype": "c64", "data": "synthetic",
             "config": {"workload": wl.name, "N": n, "levels": wl.levels, "digits": wl.digits, "batch": B,
                        "interp_order": 10, "k": wl.k, "l2": "flushed between timed steps (256 MB write)",
-                       "mesh": "icosphere subdivision 5, radius 2 m"},
+                       "mesh": "icosphere subdivision 5, radius 2 m",
+                       "launch_shapes": ("mlfma_tune before timing; serial stage-time sums [built-in, tuned] ms: %s"
+                                         % json.dumps(tuned)) if tuned else "built-in"},
             "fp64_single_vector": {"value": fp64_rate * world, "unit": UNIT, "ms_per_matvec": ms64 / steps64,
                                    "speedup_of_mixed_batched": value / (fp64_rate * world)},
             "err_vs_oracle": {"fp32_batched": err, "fp64_single": err64 if rank == 0 else None,

@@ -209,6 +209,23 @@ mlfma_status mlfma_matvec_host(mlfma_plan_t plan, const void *x, int x_is_comple
                                int64_t B, int prec, void *stream);
 
 /*
+ * Autotuning of the launch choices (no counterpart in the paper): for the
+ * product y = Z x with B columns (complex x: 2B internal columns) in `prec`,
+ * every stage's candidate launch shapes - near field (one CTA per strip with
+ * 8 or 16 columns per thread, or 16-column chunks), radiation and reception
+ * tile widths, per level the column chunk of the up and down passes and the
+ * translation's columns or lanes per output - are timed serially with CUDA
+ * events on `stream` (one warm-up launch, then three) after one full pass,
+ * and the fastest kept for later mlfma_matvec / adjoint / profile calls
+ * with the same (prec, columns); a captured graph for them is re-captured.
+ * ms_default / ms_tuned (may be NULL) receive the sums of the stage times
+ * with the built-in and with the chosen shapes.  Synchronous; overwrites the
+ * plan's internal buffers.  Errors: EINVAL, ECUDA.
+ */
+mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec, void *stream,
+                        double *ms_default, double *ms_tuned);
+
+/*
  * Measurement aid: the same product as mlfma_matvec, run serially on
  * `stream` (no graph, no overlap) with a CUDA event after every stage, then
  * waits for the stream.  stage_ms[MLFMA_STAGE_COUNT] receives the device

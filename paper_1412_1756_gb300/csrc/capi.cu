@@ -122,6 +122,7 @@ struct mlfma_plan_s {
     ProductArgs<float> ax32, ar32;
     ProductArgs<double> ax64, ar64;
     bool x_ready[2] = {false, false}, r_ready[2] = {false, false};
+    std::map<std::pair<int, int>, Tuning> tunes;   // (precision, internal columns) -> launch choices
 };
 
 namespace {
@@ -599,6 +600,74 @@ void detach_device(mlfma_plan_s *p)
     p->on_device = false;
 }
 
+// Times every candidate of every stage (serially, CUDA events on `s`,
+// after one warm-up launch) and keeps the fastest; *before / *after are the
+// sums of the stages' times with the built-in choices and with the chosen
+// ones.  Fields are filled by one full pass first; the contents of x do not
+// change the timing.
+template <class R>
+cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *before, double *after)
+{
+    cudaError_t e;
+    a.tune = Tuning();
+    best = Tuning();
+    if ((e = cudaMemsetAsync(a.xp, 0, (size_t)a.n * a.B * sizeof(R), s)) != cudaSuccess) return e;
+    CoreStreams serial{};
+    serial.main = s;
+    if ((e = launch_core<R>(a, serial, nullptr)) != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    auto time_stage = [&](int stage, int choice) -> double {
+        if (launch_stage<R>(a, stage, choice, s) != cudaSuccess) {
+            cudaGetLastError();
+            return -1.0;
+        }
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch_stage<R>(a, stage, choice, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / 3.0;
+    };
+    double tb = 0, ta = 0;
+    auto pick = [&](int stage, std::initializer_list<int> choices, int &slot) {
+        const double t0 = time_stage(stage, 0);
+        double tmin = t0;
+        slot = 0;
+        for (int c : choices) {
+            const double t = time_stage(stage, c);
+            if (t > 0 && t < tmin * 0.98) {   // keep the built-in choice unless clearly slower
+                tmin = t;
+                slot = c;
+            }
+        }
+        tb += t0;
+        ta += tmin;
+    };
+    pick(STAGE_NEAR, {1, 2, 3}, best.near);
+    if (a.leaf >= a.coarsest) {
+        pick(STAGE_RADIATE, {1, 2, 3, 4}, best.radiate);
+        pick(STAGE_RECEIVE, {1, 2, 3}, best.receive);
+        for (int l = a.coarsest; l <= a.leaf; ++l) {
+            pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6}, best.tr[l]);
+            if (l < a.leaf) {
+                pick(STAGE_UP + l, {1, 2, 4, 8, 16}, best.up_nb[l]);
+                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16}, best.down_nb[l]);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (before) *before = tb;
+    if (after) *after = ta;
+    return cudaGetLastError();
+}
+
 mlfma_status check_plan(mlfma_plan_t p)
 {
     if (!p) return fail(MLFMA_EINVAL, "plan is NULL");
@@ -657,6 +726,10 @@ mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int
                  int kind, cudaStream_t s, double *stage_ms)
 {
     const int dk = kind == KIND_DK;
+    if (kind == KIND_Z) {
+        auto t = p->tunes.find(std::make_pair(prec, a.B));
+        if (t != p->tunes.end()) a.tune = t->second;
+    }
     cudaError_t e;
     if (stage_ms) {
         StageClock &clk = p->clock;
@@ -992,6 +1065,38 @@ mlfma_status mlfma_matvec_dk_adjoint(mlfma_plan_t p, const void *x, int xc, void
                                      void *stream)
 {
     return product(p, x, xc, y, B, prec, stream, 1, false, nullptr, KIND_DK);
+}
+
+mlfma_status mlfma_tune(mlfma_plan_t p, int64_t B, int xc, int prec, void *stream, double *ms_default,
+                        double *ms_tuned)
+{
+    if (check_plan(p)) return MLFMA_EINVAL;
+    if (!p->on_device) return fail(MLFMA_EINVAL, "plan was built host-only");
+    const int64_t Bi = B * (xc ? 2 : 1);
+    if (B < 1 || Bi > p->opts.max_batch) return fail(MLFMA_EINVAL, "B must be in 1..max_batch");
+    if ((prec == MLFMA_FP32 && !p->has32) || (prec == MLFMA_FP64 && !p->has64) || (prec != 0 && prec != 1))
+        return fail(MLFMA_EINVAL, "precision not set up in this plan");
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Tuning t;
+    cudaError_t e;
+    if (prec == MLFMA_FP64) {
+        ProductArgs<double> a = p->a64;
+        a.B = (int)Bi;
+        e = tune_args<double>(a, s, t, ms_default, ms_tuned);
+    } else {
+        ProductArgs<float> a = p->a32;
+        a.B = (int)Bi;
+        e = tune_args<float>(a, s, t, ms_default, ms_tuned);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mlfma_tune");
+    p->tunes[std::make_pair(prec, (int)Bi)] = t;
+    auto it = p->graphs.find(std::make_pair(prec + 2 * KIND_Z, (int)Bi));   // recapture with the choices
+    if (it != p->graphs.end()) {
+        cudaGraphExecDestroy(it->second);
+        p->graphs.erase(it);
+    }
+    return MLFMA_OK;
 }
 
 mlfma_status mlfma_matvec_x(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)

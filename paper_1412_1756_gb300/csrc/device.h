@@ -97,12 +97,24 @@ cudaError_t launch_part_c64(const double2 *src, double2 *dst, int64_t n, int par
 cudaError_t launch_part_c32(const double2 *src, float2 *dst, int64_t n, int part, cudaStream_t s);
 
 // ------------------------------------------------------------ product ---
+// Launch choices of one product, 0 = the built-in heuristic; mlfma_tune
+// picks them per (precision, columns) by timing the candidates.
+struct Tuning {
+    int near = 0;          // 1 / 2: one CTA per strip, 8 / 16 columns per thread; 3: 16-column chunks
+    int radiate = 0;       // 1: one CTA per box; 2, 3, 4: 32, 16, 8 columns per CTA
+    int receive = 0;       // 1, 2, 3: 32, 16, 8 columns per CTA
+    int up_nb[22] = {};    // columns per CTA of the up pass into level l: 1, 2, 4, 8, 16
+    int down_nb[22] = {};  // columns per CTA of the down pass from level l
+    int tr[22] = {};       // translation at level l: 1 two columns per thread; 2..6 1, 2, 4, 8, 16 lanes per output
+};
+
 template <class R>
 struct ProductArgs {
     int64_t n = 0;
     int B = 0;                 // internal real columns
     int leaf = 0, levels = 0;  // levels with far work: coarsest..leaf
     int coarsest = 2;          // 2 for the standard tree, 1 for the sibling scheme
+    Tuning tune;
     DevNear nr;
     const R *near_val = nullptr;    // complex, strip layout
     const R *V = nullptr;           // leaf patterns [N][K][2] complex
@@ -161,5 +173,12 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
 // with clk.
 template <class R>
 cudaError_t launch_core_dk(const ProductArgs<R> &a, cudaStream_t s, StageClock *clk);
+
+// One stage of the core pass with a given choice (mlfma_tune): stage is
+// STAGE_NEAR, STAGE_RADIATE, STAGE_RECEIVE, STAGE_UP + l, STAGE_TRANSLATE + l
+// or STAGE_DOWN + l; `choice` as the matching Tuning field.  Returns an
+// error for a choice that does not apply (the tuner skips it).
+template <class R>
+cudaError_t launch_stage(const ProductArgs<R> &a, int stage, int choice, cudaStream_t s);
 
 }  // namespace mlfma

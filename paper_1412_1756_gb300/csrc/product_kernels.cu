@@ -1125,11 +1125,15 @@ cudaError_t launch_near_wide(const ProductArgs<R> &a, cudaStream_t s)
 }
 
 template <class R>
-cudaError_t launch_near(const ProductArgs<R> &a, cudaStream_t s)
+cudaError_t launch_near(const ProductArgs<R> &a, cudaStream_t s, int choice = 0)
 {
+    const bool wide_ok = a.B % 16 == 0 && a.nr.nleaf > 0 && a.B <= 512 &&
+                         (size_t)2 * 32 * (a.B * sizeof(R) + a.nr.max_rows * sizeof(typename Cx<R>::T)) <= (size_t)kStageCap;
+    if (choice == 1) return wide_ok ? launch_near_wide<R, 8>(a, s) : cudaErrorInvalidConfiguration;
+    if (choice == 2) return wide_ok ? launch_near_wide<R, 16>(a, s) : cudaErrorInvalidConfiguration;
+    if (choice == 3) return a.B >= 16 ? launch_near_bt<R, 16>(a, s) : cudaErrorInvalidConfiguration;
     // wide path: all columns per strip pass (B a multiple of 16 bytes of R and BPT)
-    if (a.B >= 32 && a.B % 16 == 0 && a.nr.nleaf > 0 &&
-        (size_t)2 * 32 * (a.B * sizeof(R) + a.nr.max_rows * sizeof(typename Cx<R>::T)) <= (size_t)kStageCap) {
+    if (a.B >= 32 && wide_ok) {
         if (a.B <= 256) return launch_near_wide<R, 8>(a, s);   // 8 columns x rows per thread; row tiles of 256 / (B/8)
         return launch_near_wide<R, 16>(a, s);
     }
@@ -1156,12 +1160,19 @@ cudaError_t launch_radiate_tiled(const ProductArgs<R> &a, int Bs, cudaStream_t s
 
 // Bs: row stride of the outgoing field in columns (>= a.B)
 template <class R>
-cudaError_t launch_radiate(const ProductArgs<R> &a, int Bs, cudaStream_t s)
+cudaError_t launch_radiate(const ProductArgs<R> &a, int Bs, cudaStream_t s, int choice = 0)
 {
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
     const DevLevel<R> &Lf = a.lv[a.leaf];
-    if (a.B % 4 == 0 && a.B >= 16 && a.B <= 256 && (a.B * sizeof(R)) % 16 == 0) {
+    if (choice >= 2 && choice <= 4) {
+        const int nb = choice == 2 ? 32 : choice == 3 ? 16 : 8;
+        if (a.B < nb || (size_t)a.nr.max_rows * nb * sizeof(R) > (size_t)kStageCap) return cudaErrorInvalidConfiguration;
+        return nb == 32 ? launch_radiate_tiled<R, 32, 4>(a, Bs, s)
+                        : nb == 16 ? launch_radiate_tiled<R, 16, 4>(a, Bs, s) : launch_radiate_tiled<R, 8, 4>(a, Bs, s);
+    }
+    if (choice == 1 || choice == 0) {
+      if (a.B % 4 == 0 && a.B >= 16 && a.B <= 256 && (a.B * sizeof(R)) % 16 == 0) {
         const int QT = 256 / (a.B / 4);
         const size_t smem = (size_t)2 * a.nr.max_rows * QT * sizeof(C4) + (size_t)a.nr.max_rows * a.B * sizeof(R);
         if (smem <= (size_t)kStageCap) {
@@ -1169,6 +1180,8 @@ cudaError_t launch_radiate(const ProductArgs<R> &a, int Bs, cudaStream_t s)
                                                          reinterpret_cast<C *>(Lf.S), Lf.K, a.B, Bs, a.nr.max_rows);
             return cudaGetLastError();
         }
+      }
+      if (choice == 1) return cudaErrorInvalidConfiguration;
     }
     if (a.B >= 32 && (size_t)a.nr.max_rows * 32 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 32, 4>(a, Bs, s);
     if (a.B >= 16 && (size_t)a.nr.max_rows * 16 * sizeof(R) <= (size_t)kStageCap) return launch_radiate_tiled<R, 16, 4>(a, Bs, s);
@@ -1211,9 +1224,12 @@ cudaError_t launch_receive_tiled(const ProductArgs<R> &a, int Bs, cudaStream_t s
 
 // Bs: row stride of the incoming field in columns (>= a.B)
 template <class R>
-cudaError_t launch_receive(const ProductArgs<R> &a, int Bs, cudaStream_t s)
+cudaError_t launch_receive(const ProductArgs<R> &a, int Bs, cudaStream_t s, int choice = 0)
 {
     using C = typename Cx<R>::T;
+    if (choice == 1) return a.B >= 32 ? launch_receive_tiled<R, 32>(a, Bs, s) : cudaErrorInvalidConfiguration;
+    if (choice == 2) return a.B >= 16 ? launch_receive_tiled<R, 16>(a, Bs, s) : cudaErrorInvalidConfiguration;
+    if (choice == 3) return a.B >= 8 ? launch_receive_tiled<R, 8>(a, Bs, s) : cudaErrorInvalidConfiguration;
     if (a.B >= 32 && sizeof(R) == 4) return launch_receive_tiled<R, 32>(a, Bs, s);
     if (a.B >= 16) return launch_receive_tiled<R, 16>(a, Bs, s);
     if (a.B >= 8) return launch_receive_tiled<R, 8>(a, Bs, s);
@@ -1271,11 +1287,17 @@ int column_chunk(int B, size_t per_col_bytes)
 
 // B columns of fields with row stride Bs; acc: add into the parent field
 template <class R>
-cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, int acc, cudaStream_t s)
+cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, int acc, cudaStream_t s,
+                      int nb_choice = 0)
 {
     using C = typename Cx<R>::T;
     const int order = P.up_order;
-    switch (column_chunk<R>(B, ((size_t)Ch.K + (size_t)P.nth * (Ch.nph + P.nph)) * sizeof(C))) {
+    int nb = column_chunk<R>(B, ((size_t)Ch.K + (size_t)P.nth * (Ch.nph + P.nph)) * sizeof(C));
+    if (nb_choice) {
+        if (nb_choice > 16 || (nb_choice & (nb_choice - 1)) || nb_choice > std::max(1, B)) return cudaErrorInvalidConfiguration;
+        nb = nb_choice;
+    }
+    switch (nb) {
     case 1: return launch_up_po<R, 1>(P, Ch, B, Bs, acc, order, s);
     case 2: return launch_up_po<R, 2>(P, Ch, B, Bs, acc, order, s);
     case 4: return launch_up_po<R, 4>(P, Ch, B, Bs, acc, order, s);
@@ -1303,8 +1325,17 @@ cudaError_t launch_translate_es(const DevLevel<R> &Lv, int B, int Bs, int acc, c
 // Two columns per thread when B is even and there is enough parallelism;
 // lanes per output grow until the level offers ~16 warps per SM.
 template <class R>
-cudaError_t launch_translate(const DevLevel<R> &Lv, int B, int Bs, int acc, cudaStream_t s)
+cudaError_t launch_translate(const DevLevel<R> &Lv, int B, int Bs, int acc, cudaStream_t s, int choice = 0)
 {
+    switch (choice) {
+    case 1: return B % 2 == 0 ? launch_translate_es<R, 1, 2>(Lv, B, Bs, acc, s) : cudaErrorInvalidConfiguration;
+    case 2: return launch_translate_es<R, 1, 1>(Lv, B, Bs, acc, s);
+    case 3: return launch_translate_es<R, 2, 1>(Lv, B, Bs, acc, s);
+    case 4: return launch_translate_es<R, 4, 1>(Lv, B, Bs, acc, s);
+    case 5: return launch_translate_es<R, 8, 1>(Lv, B, Bs, acc, s);
+    case 6: return launch_translate_es<R, 16, 1>(Lv, B, Bs, acc, s);
+    default: break;
+    }
     const bool pair = (B % 2 == 0) && (int64_t)Lv.nparent * ((Lv.K * (B / 2) + 31) / 32) >= 16 * 152;
     if (pair) return launch_translate_es<R, 1, 2>(Lv, B, Bs, acc, s);
     const int64_t warps1 = (int64_t)Lv.nparent * ((Lv.K * B + 31) / 32);
@@ -1342,11 +1373,15 @@ cudaError_t launch_down_tm(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, i
 
 // B columns of fields with row stride Bs, added into the child's incoming field
 template <class R>
-cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, cudaStream_t s)
+cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, cudaStream_t s, int nb_choice = 0)
 {
     using C = typename Cx<R>::T;
     const size_t per_col = ((size_t)P.K + (size_t)P.nth + (size_t)P.nth * Ch.nph + (size_t)Ch.K) * sizeof(C);
-    const int nb = column_chunk<R>(B, per_col);
+    int nb = column_chunk<R>(B, per_col);
+    if (nb_choice) {
+        if (nb_choice > 16 || (nb_choice & (nb_choice - 1)) || nb_choice > std::max(1, B)) return cudaErrorInvalidConfiguration;
+        nb = nb_choice;
+    }
     const size_t smem = per_col * nb;
     if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
     switch (nb) {
@@ -1428,29 +1463,30 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
         TRY(cudaEventRecord(cs.ev[0], s0));
         TRY(cudaStreamWaitEvent(sf, cs.ev[0], 0));
     }
-    TRY(launch_near<R>(a, s0));
+    const Tuning &tu = a.tune;
+    TRY(launch_near<R>(a, s0, tu.near));
     TRY(tick(clk, STAGE_NEAR, s0));
     if (leaf >= top) {
-        TRY(launch_radiate<R>(a, B, sf));
+        TRY(launch_radiate<R>(a, B, sf, tu.radiate));
         TRY(tick(clk, STAGE_RADIATE, sf));
         if (!serial) {
             TRY(cudaEventRecord(cs.ev[3 + leaf], sf));
             TRY(cudaStreamWaitEvent(st, cs.ev[3 + leaf], 0));
         }
-        TRY(launch_translate<R>(a.lv[leaf], B, B, 0, st));
+        TRY(launch_translate<R>(a.lv[leaf], B, B, 0, st, tu.tr[leaf]));
         TRY(tick(clk, STAGE_TRANSLATE + leaf, st));
         for (int l = leaf - 1; l >= top; --l) {
-            TRY(launch_up<R>(a.lv[l], a.lv[l + 1], B, B, 0, sf));
+            TRY(launch_up<R>(a.lv[l], a.lv[l + 1], B, B, 0, sf, tu.up_nb[l]));
             TRY(tick(clk, STAGE_UP + l, sf));
             if (l == top) {
-                TRY(launch_translate<R>(a.lv[l], B, B, 0, sf));
+                TRY(launch_translate<R>(a.lv[l], B, B, 0, sf, tu.tr[l]));
                 TRY(tick(clk, STAGE_TRANSLATE + l, sf));
             } else {
                 if (!serial) {
                     TRY(cudaEventRecord(cs.ev[3 + l], sf));
                     TRY(cudaStreamWaitEvent(st, cs.ev[3 + l], 0));
                 }
-                TRY(launch_translate<R>(a.lv[l], B, B, 0, st));
+                TRY(launch_translate<R>(a.lv[l], B, B, 0, st, tu.tr[l]));
                 TRY(tick(clk, STAGE_TRANSLATE + l, st));
             }
         }
@@ -1459,14 +1495,14 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
             TRY(cudaStreamWaitEvent(sf, cs.ev[2], 0));
         }
         for (int l = top; l < leaf; ++l) {
-            TRY(launch_down<R>(a.lv[l], a.lv[l + 1], B, B, sf));
+            TRY(launch_down<R>(a.lv[l], a.lv[l + 1], B, B, sf, tu.down_nb[l]));
             TRY(tick(clk, STAGE_DOWN + l, sf));
         }
         if (!serial) {
             TRY(cudaEventRecord(cs.ev[1], sf));
             TRY(cudaStreamWaitEvent(s0, cs.ev[1], 0));
         }
-        TRY(launch_receive<R>(a, B, s0));
+        TRY(launch_receive<R>(a, B, s0, tu.receive));
         TRY(tick(clk, STAGE_RECEIVE, s0));
     }
 #undef TRY
@@ -1547,6 +1583,31 @@ cudaError_t launch_core_dk(const ProductArgs<R> &a, cudaStream_t s, StageClock *
     return cudaSuccess;
 }
 
+template <class R>
+cudaError_t launch_stage(const ProductArgs<R> &a, int stage, int choice, cudaStream_t s)
+{
+    const int B = a.B;
+    if (stage == STAGE_NEAR) return launch_near<R>(a, s, choice);
+    if (stage == STAGE_RADIATE) return launch_radiate<R>(a, B, s, choice);
+    if (stage == STAGE_RECEIVE) return launch_receive<R>(a, B, s, choice);
+    if (stage >= STAGE_UP && stage < STAGE_TRANSLATE) {
+        const int l = stage - STAGE_UP;
+        if (l < a.coarsest || l >= a.leaf) return cudaErrorInvalidValue;
+        return launch_up<R>(a.lv[l], a.lv[l + 1], B, B, 0, s, choice);
+    }
+    if (stage >= STAGE_TRANSLATE && stage < STAGE_DOWN) {
+        const int l = stage - STAGE_TRANSLATE;
+        if (l < a.coarsest || l > a.leaf) return cudaErrorInvalidValue;
+        return launch_translate<R>(a.lv[l], B, B, 0, s, choice);
+    }
+    if (stage >= STAGE_DOWN && stage < STAGE_RECEIVE) {
+        const int l = stage - STAGE_DOWN;
+        if (l < a.coarsest || l >= a.leaf) return cudaErrorInvalidValue;
+        return launch_down<R>(a.lv[l], a.lv[l + 1], B, B, s, choice);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template cudaError_t prime_kernels<float>();
 template cudaError_t prime_kernels<double>();
 template cudaError_t launch_prepare<float>(const ProductArgs<float> &, const void *, int, int, int, cudaStream_t);
@@ -1556,6 +1617,8 @@ template cudaError_t launch_finalize<double>(const ProductArgs<double> &, void *
 template cudaError_t launch_core<float>(const ProductArgs<float> &, const CoreStreams &, StageClock *);
 template cudaError_t launch_core<double>(const ProductArgs<double> &, const CoreStreams &, StageClock *);
 template cudaError_t launch_core_dk<float>(const ProductArgs<float> &, cudaStream_t, StageClock *);
+template cudaError_t launch_stage<float>(const ProductArgs<float> &, int, int, cudaStream_t);
+template cudaError_t launch_stage<double>(const ProductArgs<double> &, int, int, cudaStream_t);
 template cudaError_t launch_core_dk<double>(const ProductArgs<double> &, cudaStream_t, StageClock *);
 
 }  // namespace mlfma

@@ -25,7 +25,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIM
 EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg_edges", "mlfma_matvec",
             "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint", "mlfma_matvec_x",
             "mlfma_matvec_r", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
-            "mlfma_profile_stages", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
+            "mlfma_profile_stages", "mlfma_tune", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
             "cm_eig_derivatives",
             "mlfma_set_create", "mlfma_set_matvec", "mlfma_set_info", "mlfma_set_plan", "mlfma_set_destroy",
             "mlfma_destroy", "mlfma_last_error"]
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = False):
         getattr(L, f).argtypes = [P, P, I, P, I64, I, P]
     L.mlfma_sync.argtypes = [P, P]
     L.mlfma_profile_stages.argtypes = [P, P, I, P, I64, I, P, P]
+    L.mlfma_tune.argtypes = [P, I64, I, I, P, P, P]
     L.mlfma_cm_default_opts.argtypes = [ctypes.POINTER(CmOpts)]
     L.cm_ira_solve.argtypes = [P, ctypes.POINTER(CmOpts), P, P, ctypes.POINTER(CmStats)]
     L.cm_eig_derivatives.argtypes = [P, I, P, P, I, P]
@@ -295,6 +296,16 @@ class MlfmaPlan:
         _check(self._lib.mlfma_matvec_host(self._h, _np_ptr(x2), xc, _np_ptr(y), B, prec,
                                            ctypes.c_void_p(stream or 0)))
         return y.reshape(self.n) if squeeze else y
+
+    def tune(self, B, prec=FP32, complex_x=False, stream=None):
+        """Autotune the launch shapes for products of B columns; returns the
+        serial stage-time sums (ms) with the built-in and the chosen shapes."""
+        import torch
+        d, t = ctypes.c_double(), ctypes.c_double()
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(self._lib.mlfma_tune(self._h, int(B), 1 if complex_x else 0, int(prec), ctypes.c_void_p(s),
+                                    ctypes.byref(d), ctypes.byref(t)))
+        return d.value, t.value
 
     def profile_stages(self, x, y=None, stream=None) -> dict:
         """Serial per-stage device times (ms) of one product (measurement aid)."""

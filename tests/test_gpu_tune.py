@@ -1,0 +1,60 @@
+"""mlfma_tune: the tuned launch shapes change how the product is computed,
+not what it computes - tuned products agree with the built-in ones to
+rounding (FP32: 1e-5, FP64: 1e-12) and with the dense oracle to the product's
+bound; the chosen stage-time sum never exceeds the built-in one."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import efie
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1412_1756_gb300 import mlfma as M  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("dt,prec,tol", [(torch.float32, M.FP32, 1e-5), (torch.float64, M.FP64, 1e-12)])
+def test_tuned_product_matches_builtin(dt, prec, tol):
+    W = workloads.get("sphere-r0.5m-ico3")
+    v, t = W.mesh()
+    P = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=16)
+    x = workloads.rhs(P.n, 8, W.seed)
+    xd = torch.from_numpy(x).to("cuda", dt)
+    y0 = P.matvec(xd).cpu().numpy()
+    d, tt = P.tune(8, prec)
+    assert 0 < tt <= d
+    y1 = P.matvec(xd).cpu().numpy()
+    assert rel(y1, y0) < tol
+    Z = efie.Problem(v, t, W.k).dense()
+    assert rel(y1, Z @ x) < 1e-3
+    xc = workloads.rhs_complex(P.n, 4, W.seed)
+    cdt = torch.complex64 if prec == M.FP32 else torch.complex128
+    P.tune(4, prec, complex_x=True)
+    yc = P.matvec(torch.from_numpy(xc).to("cuda", cdt)).cpu().numpy()
+    assert rel(yc, Z @ xc) < 1e-3
+
+
+def test_tuned_full_size_rows():
+    W = workloads.get("sphere-r2m-ico5")
+    v, t = W.mesh()
+    P = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=64, precisions=(M.FP32,))
+    d, tt = P.tune(64, M.FP32)
+    assert tt <= d
+    x = workloads.rhs(P.n, 64, W.seed)
+    y = P.matvec(torch.from_numpy(x).to("cuda", torch.float32)).cpu().numpy()
+    idx = np.random.default_rng(5).choice(P.n, 8, replace=False)
+    ref = efie.Problem(v, t, W.k).matvec_rows(x, idx)
+    assert rel(y[idx], ref) < 1e-3
+
+
+def test_tune_rejects_bad_sizes():
+    W = workloads.get("sphere-r0.5m-ico2")
+    v, t = W.mesh()
+    P = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=8)
+    with pytest.raises(M.MlfmaError):
+        P.tune(9, M.FP32)
