@@ -140,6 +140,66 @@ cudaError_t upload_pairs(DevMem &M, const std::vector<cd> &v, const R **out)
 // Tables of a parent level l (to and from level l + 1): phase shifts, the
 // packed interpolation stencils and the anterpolation stencils zero-padded
 // to dn_taps taps per row.
+// Round an FP32 value to TF32 (10 explicit mantissa bits), to nearest with
+// ties away from zero, on its bit pattern (finite values).
+static float tf32_round(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+// Dense row-major A [m][k] (zero beyond its extent) in mma.m16n8k8 TF32
+// A-fragment order, hi and lo parts: lane (g = lane / 4, q = lane % 4) holds
+// A[g][q], A[g+8][q], A[g][q+4], A[g+8][q+4] of each 16 x 8 tile.
+static std::vector<float> tc_fragments(const std::vector<double> &A, int m, int k, int &mt, int &kt)
+{
+    mt = (m + 15) / 16;
+    kt = (k + 7) / 8;
+    std::vector<float> f((size_t)mt * kt * 32 * 8, 0.0f);
+    auto at = [&](int r, int c) { return (r < m && c < k) ? A[(size_t)r * k + c] : 0.0; };
+    for (int a = 0; a < mt; ++a)
+        for (int b = 0; b < kt; ++b)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = lane >> 2, q = lane & 3;
+                const double v[4] = {at(a * 16 + g, b * 8 + q), at(a * 16 + g + 8, b * 8 + q), at(a * 16 + g, b * 8 + q + 4),
+                                     at(a * 16 + g + 8, b * 8 + q + 4)};
+                float *dst = &f[(((size_t)a * kt + b) * 32 + lane) * 8];
+                for (int r = 0; r < 4; ++r) {
+                    const float x = (float)v[r];
+                    const float hi = tf32_round(x);
+                    dst[r] = hi;
+                    dst[4 + r] = tf32_round(x - hi);
+                }
+            }
+    return f;
+}
+
+template <class R>
+cudaError_t upload_tc_tables(DevMem &M, const PlanHost &H, const Level &Lv, DevLevel<R> &D)
+{
+    if (sizeof(R) != 4) return cudaSuccess;
+    const Level &C = H.lv[Lv.l + 1];
+    const int nthc = C.nth, nphc = C.nph;
+    std::vector<double> th((size_t)Lv.nth * 2 * nthc, 0.0), ph((size_t)Lv.nph * nphc, 0.0);
+    for (int t = 0; t < Lv.nth; ++t)
+        for (int e = Lv.th_up.ptr[t]; e < Lv.th_up.ptr[t + 1]; ++e)
+            th[(size_t)t * 2 * nthc + (Lv.th_up.refl[e] ? nthc : 0) + Lv.th_up.idx[e]] += Lv.th_up.coef[e];
+    for (int u = 0; u < Lv.nph; ++u)
+        for (int e = Lv.ph_up.ptr[u]; e < Lv.ph_up.ptr[u + 1]; ++e)
+            ph[(size_t)u * nphc + Lv.ph_up.idx[e]] += Lv.ph_up.coef[e];
+    cudaError_t e;
+    const float *p;
+    if ((e = M.upload(tc_fragments(th, Lv.nth, 2 * nthc, D.tc_mt_th, D.tc_kt_th), &p)) != cudaSuccess) return e;
+    D.tc_th = p;
+    if ((e = M.upload(tc_fragments(ph, Lv.nph, nphc, D.tc_mt_ph, D.tc_kt_ph), &p)) != cudaSuccess) return e;
+    D.tc_ph = p;
+    return cudaSuccess;
+}
+
 template <class R>
 cudaError_t upload_parent_tables(DevMem &M, const PlanHost &H, const Level &Lv, DevLevel<R> &D)
 {
@@ -177,7 +237,8 @@ cudaError_t upload_parent_tables(DevMem &M, const PlanHost &H, const Level &Lv, 
         return t;
     };
     if ((e = M.upload(pad(Lv.th_dn), &D.thd_pad)) != cudaSuccess) return e;
-    return M.upload(pad(Lv.ph_dn), &D.phd_pad);
+    if ((e = M.upload(pad(Lv.ph_dn), &D.phd_pad)) != cudaSuccess) return e;
+    return upload_tc_tables<R>(M, H, Lv, D);
 }
 
 template <class R>
@@ -656,7 +717,7 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
         for (int l = a.coarsest; l <= a.leaf; ++l) {
             pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6}, best.tr[l]);
             if (l < a.leaf) {
-                pick(STAGE_UP + l, {1, 2, 4, 8, 16}, best.up_nb[l]);
+                pick(STAGE_UP + l, {1, 2, 4, 8, 16, 100}, best.up_nb[l]);
                 pick(STAGE_DOWN + l, {1, 2, 4, 8, 16}, best.down_nb[l]);
             }
         }

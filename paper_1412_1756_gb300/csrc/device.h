@@ -73,6 +73,12 @@ struct DevLevel {
     // anterpolation stencils zero-padded to dn_taps taps per row (16, 20, 24 or 32)
     const Tap<R> *thd_pad = nullptr, *phd_pad = nullptr;
     int dn_taps = 0;
+    // FP32 parents: the interpolation steps as dense matrices for the tensor
+    // cores, in mma.m16n8k8 A-fragment order with a TF32 hi/lo split:
+    // [mtile][ktile][lane][hi a0..a3, lo a0..a3].  theta: [nth][2 child nth]
+    // (second half: samples taken at phi + pi); phi: [nph][child nph].
+    const float *tc_th = nullptr, *tc_ph = nullptr;
+    int tc_mt_th = 0, tc_kt_th = 0, tc_mt_ph = 0, tc_kt_ph = 0;
     int up_order = 0;           // taps per forward stencil row (the interpolation order)
     const R *wq = nullptr;               // [K] quadrature weight (leaf: times -k^2 eta / 4 pi)
     R *S = nullptr;                      // outgoing field [nbox][2][K][B]
