@@ -226,6 +226,28 @@ mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec
                         double *ms_default, double *ms_tuned);
 
 /*
+ * Read or pin the launch shapes used for (B, x_is_complex, prec) as
+ * MLFMA_TUNE_FIELDS int32 values (0 = the built-in choice):
+ *   [0] near field: 1 / 2 one CTA per strip with 8 / 16 columns per thread,
+ *       3 chunks of 16 columns
+ *   [1] radiation: 1 one CTA per box, 2 / 3 / 4 tiles of 32 / 16 / 8 columns
+ *   [2] reception: 1 / 2 / 3 tiles of 32 / 16 / 8 columns
+ *   [3 + l]       up pass into level l: columns per CTA 1..16, or 100 for the
+ *                 tensor-core (mma.sync 3xTF32, FP32 only) variant
+ *   [3 + 22 + l]  down pass from level l: columns per CTA 1..16
+ *   [3 + 44 + l]  translation at level l: 1 two columns per thread; 2..6 one
+ *                 column with 1, 2, 4, 8, 16 lanes per output; 7 / 8 one warp
+ *                 per (child, sample) with 2 / 1 columns per lane
+ * A pinned shape that does not apply to the plan makes the product fail
+ * with MLFMA_ECUDA (invalid configuration).  mlfma_tune_set drops a graph
+ * captured for the key (and waits for the device to do so).
+ */
+#define MLFMA_TUNE_FIELDS (3 + 3 * 22)
+mlfma_status mlfma_tune_get(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec, int32_t *choices);
+mlfma_status mlfma_tune_set(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec,
+                            const int32_t *choices);
+
+/*
  * Measurement aid: the same product as mlfma_matvec, run serially on
  * `stream` (no graph, no overlap) with a CUDA event after every stage, then
  * waits for the stream.  stage_ms[MLFMA_STAGE_COUNT] receives the device

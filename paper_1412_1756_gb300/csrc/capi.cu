@@ -605,6 +605,7 @@ cudaError_t setup_r(mlfma_plan_t p, const ProductArgs<R> &a, ProductArgs<R> &ar)
         if ((e = M.upload(S.grp_src, &D.grp_src)) != cudaSuccess) return e;
         if ((e = M.upload(S.grp_ty, &D.grp_ty)) != cudaSuccess) return e;
         D.lty_ptr = nullptr; D.lty = nullptr; D.grp_lty = nullptr; D.max_lty = 0;
+        D.il_ptr = nullptr; D.il_src = nullptr; D.il_type = nullptr;   // the standard lists do not apply
         if ((e = upload_pairs<R>(M, S.alpha, &D.alpha)) != cudaSuccess) return e;
     }
     return cudaDeviceSynchronize();
@@ -715,7 +716,7 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
         pick(STAGE_RADIATE, {1, 2, 3, 4}, best.radiate);
         pick(STAGE_RECEIVE, {1, 2, 3}, best.receive);
         for (int l = a.coarsest; l <= a.leaf; ++l) {
-            pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6}, best.tr[l]);
+            pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6, 7, 8}, best.tr[l]);
             if (l < a.leaf) {
                 pick(STAGE_UP + l, {1, 2, 4, 8, 16, 100}, best.up_nb[l]);
                 pick(STAGE_DOWN + l, {1, 2, 4, 8, 16}, best.down_nb[l]);
@@ -1154,6 +1155,48 @@ mlfma_status mlfma_tune(mlfma_plan_t p, int64_t B, int xc, int prec, void *strea
     p->tunes[std::make_pair(prec, (int)Bi)] = t;
     auto it = p->graphs.find(std::make_pair(prec + 2 * KIND_Z, (int)Bi));   // recapture with the choices
     if (it != p->graphs.end()) {
+        cudaGraphExecDestroy(it->second);
+        p->graphs.erase(it);
+    }
+    return MLFMA_OK;
+}
+
+static void tuning_to_array(const Tuning &t, int32_t *c)
+{
+    c[0] = t.near; c[1] = t.radiate; c[2] = t.receive;
+    for (int l = 0; l < MLFMA_MAX_LEVELS; ++l) {
+        c[3 + l] = t.up_nb[l];
+        c[3 + MLFMA_MAX_LEVELS + l] = t.down_nb[l];
+        c[3 + 2 * MLFMA_MAX_LEVELS + l] = t.tr[l];
+    }
+}
+
+mlfma_status mlfma_tune_get(mlfma_plan_t p, int64_t B, int xc, int prec, int32_t *choices)
+{
+    if (check_plan(p)) return MLFMA_EINVAL;
+    if (!choices) return fail(MLFMA_EINVAL, "choices is NULL");
+    auto it = p->tunes.find(std::make_pair(prec, (int)(B * (xc ? 2 : 1))));
+    tuning_to_array(it == p->tunes.end() ? Tuning() : it->second, choices);
+    return MLFMA_OK;
+}
+
+mlfma_status mlfma_tune_set(mlfma_plan_t p, int64_t B, int xc, int prec, const int32_t *choices)
+{
+    if (check_plan(p)) return MLFMA_EINVAL;
+    if (!choices) return fail(MLFMA_EINVAL, "choices is NULL");
+    const int Bi = (int)(B * (xc ? 2 : 1));
+    Tuning t;
+    t.near = choices[0]; t.radiate = choices[1]; t.receive = choices[2];
+    for (int l = 0; l < MLFMA_MAX_LEVELS; ++l) {
+        t.up_nb[l] = choices[3 + l];
+        t.down_nb[l] = choices[3 + MLFMA_MAX_LEVELS + l];
+        t.tr[l] = choices[3 + 2 * MLFMA_MAX_LEVELS + l];
+    }
+    p->tunes[std::make_pair(prec, Bi)] = t;
+    auto it = p->graphs.find(std::make_pair(prec + 2 * KIND_Z, Bi));
+    if (it != p->graphs.end()) {
+        DeviceGuard g(p->device);
+        cudaDeviceSynchronize();
         cudaGraphExecDestroy(it->second);
         p->graphs.erase(it);
     }

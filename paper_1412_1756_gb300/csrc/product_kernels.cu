@@ -472,6 +472,77 @@ __global__ void __launch_bounds__(128) k_translate(DevLevel<R> lv, int B, int Bs
         }
 }
 
+// Translation, one warp per (child, sample): the child's own interaction
+// list (no per-entry child decode), CB columns per lane and 32 CB columns
+// per pass; a CTA covers one parent's children at QC samples, so the
+// sources they share are read from memory once and from L1 afterwards.
+// The coefficients of every type of the level at the CTA's samples are
+// staged in shared memory.  A candidate of the autotuner.
+template <class R, int CB, int QC>
+__global__ void __launch_bounds__(256) k_translate_cw(DevLevel<R> lv, int B, int Bs, int accumulate)
+{
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s_al = reinterpret_cast<C *>(smem_raw);   // [type][QC]
+    const int P = blockIdx.x, q0 = blockIdx.y * QC, K = lv.K;
+    const int nq = min(QC, K - q0);
+    const int m0 = lv.pchild_ptr[P], nc = lv.pchild_ptr[P + 1] - m0;
+    const C *al = reinterpret_cast<const C *>(lv.alpha);
+    for (int i = threadIdx.x; i < lv.ntype * QC; i += blockDim.x) {
+        const int ty = i / QC, qq = i - ty * QC;
+        if (qq < nq) cp_async(s_al + i, al + (int64_t)ty * K + q0 + qq);
+        else s_al[i] = C{0, 0};
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const C *S = reinterpret_cast<const C *>(lv.S);
+    C *G = reinterpret_cast<C *>(lv.G);
+    const int64_t KB = (int64_t)K * Bs;
+    for (int pr = warp; pr < nc * QC; pr += blockDim.x >> 5) {
+        const int c = pr / QC, qq = pr - c * QC;
+        if (qq >= nq) continue;
+        const int m = m0 + c, q = q0 + qq;
+        const int e0 = lv.il_ptr[m], e1 = lv.il_ptr[m + 1];
+        for (int bp = 0; bp < B; bp += 32 * CB) {
+            const int b = bp + lane * CB;
+            if (b >= B) break;
+            C acc[2][CB];
+#pragma unroll
+            for (int k = 0; k < CB; ++k) acc[0][k] = acc[1][k] = C{0, 0};
+#pragma unroll 4
+            for (int e = e0; e < e1; ++e) {
+                const int src = lv.il_src[e], ty = lv.il_type[e];
+                const C a = s_al[ty * QC + qq];
+                const int64_t base = (int64_t)src * 2 * KB + (int64_t)q * Bs + b;
+#pragma unroll
+                for (int k = 0; k < CB; ++k) {
+                    if (b + k < B) {
+                        cfma(acc[0][k], a, S[base + k]);
+                        cfma(acc[1][k], a, S[base + KB + k]);
+                    }
+                }
+            }
+            const int64_t o = (int64_t)m * 2 * KB + (int64_t)q * Bs + b;
+#pragma unroll
+            for (int k = 0; k < CB; ++k) {
+                if (b + k >= B) break;
+                if (accumulate) {
+                    C g0 = G[o + k], g1 = G[o + KB + k];
+                    g0.x += acc[0][k].x; g0.y += acc[0][k].y;
+                    g1.x += acc[1][k].x; g1.y += acc[1][k].y;
+                    G[o + k] = g0;
+                    G[o + KB + k] = g1;
+                } else {
+                    G[o + k] = acc[0][k];
+                    G[o + KB + k] = acc[1][k];
+                }
+            }
+        }
+    }
+}
+
 // ----------------------------------------------------------- upward ---
 // CP adjacent columns per thread (2 for FP32: one 16-byte shared-memory
 // access moves both).
@@ -1532,6 +1603,17 @@ cudaError_t launch_translate_es(const DevLevel<R> &Lv, int B, int Bs, int acc, c
 template <class R>
 cudaError_t launch_translate(const DevLevel<R> &Lv, int B, int Bs, int acc, cudaStream_t s, int choice = 0)
 {
+    if (choice == 7 || choice == 8) {
+        using C = typename Cx<R>::T;
+        if (!Lv.il_ptr) return cudaErrorInvalidConfiguration;
+        constexpr int QC = 2;
+        const size_t smem = (size_t)Lv.ntype * QC * sizeof(C);
+        if (smem > (size_t)48 * 1024) return cudaErrorInvalidConfiguration;
+        dim3 grid(Lv.nparent, (Lv.K + QC - 1) / QC);
+        if (choice == 7) k_translate_cw<R, 2, QC><<<grid, 256, smem, s>>>(Lv, B, Bs, acc);
+        else k_translate_cw<R, 1, QC><<<grid, 256, smem, s>>>(Lv, B, Bs, acc);
+        return cudaGetLastError();
+    }
     switch (choice) {
     case 1: return B % 2 == 0 ? launch_translate_es<R, 1, 2>(Lv, B, Bs, acc, s) : cudaErrorInvalidConfiguration;
     case 2: return launch_translate_es<R, 1, 1>(Lv, B, Bs, acc, s);

@@ -25,12 +25,13 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIM
 EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg_edges", "mlfma_matvec",
             "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint", "mlfma_matvec_x",
             "mlfma_matvec_r", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
-            "mlfma_profile_stages", "mlfma_tune", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
+            "mlfma_profile_stages", "mlfma_tune", "mlfma_tune_get", "mlfma_tune_set", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
             "cm_eig_derivatives",
             "mlfma_set_create", "mlfma_set_matvec", "mlfma_set_info", "mlfma_set_plan", "mlfma_set_destroy",
             "mlfma_destroy", "mlfma_last_error"]
 CM_ZINV_R, CM_XINV_R = 0, 1
 STAGE_COUNT = 71
+TUNE_FIELDS = 3 + 3 * 22
 
 
 class MlfmaError(RuntimeError):
@@ -96,6 +97,8 @@ def load(build_if_missing: bool = False):
     L.mlfma_sync.argtypes = [P, P]
     L.mlfma_profile_stages.argtypes = [P, P, I, P, I64, I, P, P]
     L.mlfma_tune.argtypes = [P, I64, I, I, P, P, P]
+    L.mlfma_tune_get.argtypes = [P, I64, I, I, P]
+    L.mlfma_tune_set.argtypes = [P, I64, I, I, P]
     L.mlfma_cm_default_opts.argtypes = [ctypes.POINTER(CmOpts)]
     L.cm_ira_solve.argtypes = [P, ctypes.POINTER(CmOpts), P, P, ctypes.POINTER(CmStats)]
     L.cm_eig_derivatives.argtypes = [P, I, P, P, I, P]
@@ -306,6 +309,17 @@ class MlfmaPlan:
         _check(self._lib.mlfma_tune(self._h, int(B), 1 if complex_x else 0, int(prec), ctypes.c_void_p(s),
                                     ctypes.byref(d), ctypes.byref(t)))
         return d.value, t.value
+
+    def tune_get(self, B, prec=FP32, complex_x=False) -> np.ndarray:
+        """Launch shapes used for (B, prec) (include/mlfma.h: mlfma_tune_get)."""
+        c = np.zeros(TUNE_FIELDS, np.int32)
+        _check(self._lib.mlfma_tune_get(self._h, int(B), 1 if complex_x else 0, int(prec), _np_ptr(c)))
+        return c
+
+    def tune_set(self, B, choices, prec=FP32, complex_x=False):
+        """Pin launch shapes for (B, prec) (mlfma_tune_set)."""
+        c = np.ascontiguousarray(choices, dtype=np.int32).reshape(TUNE_FIELDS)
+        _check(self._lib.mlfma_tune_set(self._h, int(B), 1 if complex_x else 0, int(prec), _np_ptr(c)))
 
     def profile_stages(self, x, y=None, stream=None) -> dict:
         """Serial per-stage device times (ms) of one product (measurement aid)."""

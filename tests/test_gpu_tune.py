@@ -58,3 +58,35 @@ def test_tune_rejects_bad_sizes():
     P = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=8)
     with pytest.raises(M.MlfmaError):
         P.tune(9, M.FP32)
+
+
+@pytest.mark.parametrize("dt,prec,tol", [(torch.float32, M.FP32, 2e-5), (torch.float64, M.FP64, 1e-12)])
+def test_every_candidate_shape_computes_the_same_product(dt, prec, tol):
+    """Pin each candidate of every stage in turn (mlfma_tune_set) and check
+    the product against the built-in shapes: 5-level sphere (30,720
+    unknowns, levels 2..4), 32 columns."""
+    W = workloads.get("sphere-r2m-ico5")
+    v, t = W.mesh()
+    P = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=32, precisions=(prec,))
+    x = torch.from_numpy(workloads.rhs(P.n, 32, W.seed)).to("cuda", dt)
+    ref = P.matvec(x).cpu().numpy()
+    L = 22
+    cands = [(0, c) for c in (1, 2, 3)] + [(1, c) for c in (1, 2, 3, 4)] + [(2, c) for c in (1, 2, 3)]
+    for l in (2, 3, 4):
+        cands += [(3 + 2 * L + l, c) for c in range(1, 9)]
+        if l < 4:
+            cands += [(3 + l, c) for c in (1, 2, 4, 8, 16)] + [(3 + L + l, c) for c in (1, 2, 4, 8, 16)]
+            if prec == M.FP32:
+                cands.append((3 + l, 100))
+    for field, c in cands:
+        ch = np.zeros(M.TUNE_FIELDS, np.int32)
+        ch[field] = c
+        P.tune_set(32, ch, prec)
+        try:
+            y = P.matvec(x).cpu().numpy()
+        except M.MlfmaError:
+            torch.cuda.synchronize()
+            continue   # a shape that does not apply to this plan
+        assert rel(y, ref) < tol, (field, c, rel(y, ref))
+    P.tune_set(32, np.zeros(M.TUNE_FIELDS, np.int32), prec)
+    assert np.array_equal(P.matvec(x).cpu().numpy(), ref)
