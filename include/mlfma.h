@@ -234,7 +234,8 @@ mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec
  *   [2] reception: 1 / 2 / 3 tiles of 32 / 16 / 8 columns
  *   [3 + l]       up pass into level l: columns per CTA 1..16, or 100 for the
  *                 tensor-core (mma.sync 3xTF32, FP32 only) variant
- *   [3 + 22 + l]  down pass from level l: columns per CTA 1..16
+ *   [3 + 22 + l]  down pass from level l: columns per CTA 1..16 (one CTA per
+ *                 child), or 104 / 108 one CTA per parent with 4 / 8 columns
  *   [3 + 44 + l]  translation at level l: 1 two columns per thread; 2..6 one
  *                 column with 1, 2, 4, 8, 16 lanes per output; 7 / 8 one warp
  *                 per (child, sample) with 2 / 1 columns per lane

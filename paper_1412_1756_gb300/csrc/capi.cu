@@ -719,7 +719,7 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
             pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6, 7, 8}, best.tr[l]);
             if (l < a.leaf) {
                 pick(STAGE_UP + l, {1, 2, 4, 8, 16, 100}, best.up_nb[l]);
-                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16}, best.down_nb[l]);
+                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108}, best.down_nb[l]);
             }
         }
     }

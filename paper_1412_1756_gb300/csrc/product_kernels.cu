@@ -1053,6 +1053,126 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 && TM <= 20) ? 4 : 1) k_d
     }
 }
 
+// Per parent: one CTA per (parent box, component, chunk of NB columns)
+// loads the parent's incoming field once (cp.async) and loops over its
+// children - conjugate shift into H, phi and theta anterpolation as in
+// k_down, the child's own field prefetched during the stencil work - so
+// the parent load and the CTA overheads are shared by the children.  A
+// candidate of the autotuner.
+template <class R, int NB, int TM>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && TM <= 20) ? 2 : 1)
+    k_down_pp(DevLevel<R> P, DevLevel<R> Ch, int B, int Bs)
+{
+    using C = typename Cx<R>::T;
+    constexpr int CP = ColPair<R, NB>::CP, NL = NB / CP, PW = NB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph, Kp = P.K;
+    const int p = blockIdx.x, comp = blockIdx.y, b0 = blockIdx.z * NB;
+    const int nb = min(NB, B - b0);
+    const int hp = nphp + 1;
+    C *Gp = reinterpret_cast<C *>(smem_raw);   // [Kp][PW] the parent's field
+    C *H = Gp + (size_t)Kp * PW;                // [ntp][hp][PW]; later the child result [Kc][PW]
+    C *U = H + (size_t)ntp * hp * PW;          // [ntp * nphc][PW]
+    C *X = U + (size_t)ntp * nphc * PW;        // [Kc][PW] the child's incoming field
+    const int bb = threadIdx.x % NB, slot = threadIdx.x / NB, nslot = blockDim.x / NB;
+    const bool bok = bb < nb;
+    {
+        const C *g = reinterpret_cast<const C *>(P.G) + ((int64_t)p * 2 + comp) * Kp * Bs + b0 + bb;
+        for (int q = slot; q < Kp; q += nslot) {
+            if (bok) cp_async(Gp + q * PW + bb, g + (int64_t)q * Bs);
+            else Gp[q * PW + bb] = C{0, 0};
+        }
+        cp_async_commit();
+    }
+    const SplitIL sp(nphc, NL), st(nthc, NL);
+    const int c0 = P.child_ptr[p], c1 = P.child_ptr[p + 1];
+    for (int c = c0; c < c1; ++c) {
+        C *dst = reinterpret_cast<C *>(Ch.G) + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + bb;
+        if (bok)
+            for (int q = slot; q < Kc; q += nslot) cp_async(X + q * PW + bb, dst + (int64_t)q * Bs);
+        cp_async_commit();
+        cp_async_wait<1>();   // the parent's field (and any older group)
+        __syncthreads();
+        const C *sh = reinterpret_cast<const C *>(P.shift) + (int64_t)Ch.octant[c] * Kp;
+#pragma unroll 4
+        for (int q = slot; q < Kp; q += nslot) {
+            C h{0, 0};
+            cfmac(h, sh[q], Gp[q * PW + bb]);
+            H[(q + q / nphp) * PW + bb] = h;
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < sp.items; it += blockDim.x) {
+            int key, cg, ch;
+            sp.item(it, CP, key, cg, ch);
+            int pb[TM];
+            R pc[TM];
+#pragma unroll
+            for (int f = 0; f < TM; ++f) {
+                const Tap<R> tap = P.phd_pad[(size_t)key * TM + f];
+                pb[f] = tap.i * PW;
+                pc[f] = tap.c;
+            }
+            for (int tp = ch; tp < ntp; tp += sp.chunks) {
+                const C *hrow = H + tp * hp * PW + cg;
+                C s[CP];
+#pragma unroll
+                for (int k = 0; k < CP; ++k) s[k] = C{0, 0};
+#pragma unroll
+                for (int f = 0; f < TM; ++f) {
+                    C a[CP];
+                    lds_cols<C, CP>(hrow + pb[f], a);
+#pragma unroll
+                    for (int k = 0; k < CP; ++k) rfma(s[k], pc[f], a[k]);
+                }
+                sts_cols<C, CP>(U + (tp * nphc + key) * PW + cg, s);
+            }
+        }
+        __syncthreads();
+        C *W = H;
+        for (int it = threadIdx.x; it < st.items; it += blockDim.x) {
+            int key, cg, ch;
+            st.item(it, CP, key, cg, ch);
+            int tb[TM];
+            bool rf[TM];
+            R tc[TM];
+#pragma unroll
+            for (int f = 0; f < TM; ++f) {
+                const Tap<R> tap = P.thd_pad[(size_t)key * TM + f];
+                tb[f] = (tap.i & (kTapRefl - 1)) * nphc;
+                rf[f] = (tap.i & kTapRefl) != 0;
+                tc[f] = tap.c;
+            }
+            for (int v = ch; v < nphc; v += st.chunks) {
+                const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
+                C s[CP];
+#pragma unroll
+                for (int k = 0; k < CP; ++k) s[k] = C{0, 0};
+#pragma unroll
+                for (int f = 0; f < TM; ++f) {
+                    C a[CP];
+                    lds_cols<C, CP>(U + (tb[f] + (rf[f] ? vs : v)) * PW + cg, a);
+#pragma unroll
+                    for (int k = 0; k < CP; ++k) rfma(s[k], tc[f], a[k]);
+                }
+                sts_cols<C, CP>(W + (key * nphc + v) * PW + cg, s);
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+        if (bok) {
+#pragma unroll 8
+            for (int q = slot; q < Kc; q += nslot) {
+                C y = X[q * PW + bb];
+                const C w = W[q * PW + bb];
+                y.x += w.x;
+                y.y += w.y;
+                dst[(int64_t)q * Bs] = y;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------ receive ---
 // y_i += sum_q wq_q conj(V_s,mi(q)) . G_m(q).
 // Few columns: one CTA per (leaf box, chunk of LB columns) with the box's G
@@ -1658,10 +1778,28 @@ cudaError_t launch_down_tm(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, i
     }
 }
 
+template <class R, int NB>
+cudaError_t launch_down_pp(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, cudaStream_t s)
+{
+    using C = typename Cx<R>::T;
+    const size_t per_col = ((size_t)2 * P.K + (size_t)P.nth + (size_t)P.nth * Ch.nph + (size_t)Ch.K) * sizeof(C);
+    const size_t smem = per_col * NB;
+    if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
+    dim3 grid(P.nbox, 2, (B + NB - 1) / NB);
+    switch (P.dn_taps) {
+    case 16: k_down_pp<R, NB, 16><<<grid, 256, smem, s>>>(P, Ch, B, Bs); break;
+    case 20: k_down_pp<R, NB, 20><<<grid, 256, smem, s>>>(P, Ch, B, Bs); break;
+    default: return cudaErrorInvalidConfiguration;
+    }
+    return cudaGetLastError();
+}
+
 // B columns of fields with row stride Bs, added into the child's incoming field
 template <class R>
 cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, cudaStream_t s, int nb_choice = 0)
 {
+    if (nb_choice == 104) return launch_down_pp<R, 4>(P, Ch, B, Bs, s);
+    if (nb_choice == 108) return launch_down_pp<R, 8>(P, Ch, B, Bs, s);
     using C = typename Cx<R>::T;
     const size_t per_col = ((size_t)P.K + (size_t)P.nth + (size_t)P.nth * Ch.nph + (size_t)Ch.K) * sizeof(C);
     int nb = column_chunk<R>(B, per_col);
@@ -1696,6 +1834,7 @@ cudaError_t prime_kernels()
     ALLOW((k_near<R, 8, true>)); ALLOW((k_near<R, 16, true>));
     ALLOW((k_near_wide<R, 8>)); ALLOW((k_near_wide<R, 16>));
     if (sizeof(R) == 4) { ALLOW((k_up_tc<8>)); ALLOW((k_up_tc<16>)); ALLOW((k_up_tc<24>)); }
+    ALLOW((k_down_pp<R, 4, 16>)); ALLOW((k_down_pp<R, 4, 20>)); ALLOW((k_down_pp<R, 8, 16>)); ALLOW((k_down_pp<R, 8, 20>));
     ALLOW(k_radiate<R>);
     ALLOW(k_radiate_wide<R>);
     ALLOW((k_radiate_tiled<R, 8, 4>)); ALLOW((k_radiate_tiled<R, 16, 4>)); ALLOW((k_radiate_tiled<R, 32, 4>));

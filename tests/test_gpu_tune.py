@@ -75,7 +75,7 @@ def test_every_candidate_shape_computes_the_same_product(dt, prec, tol):
     for l in (2, 3, 4):
         cands += [(3 + 2 * L + l, c) for c in range(1, 9)]
         if l < 4:
-            cands += [(3 + l, c) for c in (1, 2, 4, 8, 16)] + [(3 + L + l, c) for c in (1, 2, 4, 8, 16)]
+            cands += [(3 + l, c) for c in (1, 2, 4, 8, 16)] + [(3 + L + l, c) for c in (1, 2, 4, 8, 16, 104, 108)]
             if prec == M.FP32:
                 cands.append((3 + l, 100))
     for field, c in cands:
