@@ -59,6 +59,46 @@ cd dotc(const cd *a, const cd *b, int64_t n)   // a^H b
     return s;
 }
 
+int host_threads() { return (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())); }
+
+// fn(t, i0, i1) on nt contiguous segments of [0, n), one thread each
+template <class F>
+void parallel_segments(int64_t n, F fn)
+{
+    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n / 4096));
+    if (nt == 1) {
+        fn(0, (int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&, t]() { fn(t, n * t / nt, n * (t + 1) / nt); });
+    for (auto &th : pool) th.join();
+}
+
+// One classical Gram-Schmidt pass of w against V[0..k]: h_j = V_j^H w for
+// all j in one sweep, then w -= sum_j h_j V_j; h is added to hcol.
+void cgs_pass(const std::vector<std::vector<cd>> &V, int k, std::vector<cd> &w, cd *hcol, int64_t stride)
+{
+    const int64_t n = (int64_t)w.size();
+    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n / 4096));
+    std::vector<cd> part((size_t)nt * (k + 1), 0.0);
+    parallel_segments(n, [&](int t, int64_t i0, int64_t i1) {
+        for (int j = 0; j <= k; ++j) part[(size_t)t * (k + 1) + j] = dotc(V[j].data() + i0, w.data() + i0, i1 - i0);
+    });
+    std::vector<cd> h(k + 1, 0.0);
+    for (int t = 0; t < nt; ++t)
+        for (int j = 0; j <= k; ++j) h[j] += part[(size_t)t * (k + 1) + j];
+    parallel_segments(n, [&](int, int64_t i0, int64_t i1) {
+        for (int j = 0; j <= k; ++j) {
+            const cd hj = h[j];
+            const cd *v = V[j].data();
+            for (int64_t i = i0; i < i1; ++i) w[i] -= hj * v[i];
+        }
+    });
+    for (int j = 0; j <= k; ++j) hcol[(int64_t)j * stride] += h[j];
+}
+
 // ------------------------------------------------- dense complex eigen ---
 // Givens rotation G = [c s; -conj(s) c] (c real) with G [x; y] = [r; 0].
 void givens(cd x, cd y, double &c, cd &s)
@@ -371,11 +411,13 @@ struct Sai {
                     const int r0 = H->box_ptr[a], na = H->box_ptr[a + 1] - r0;
                     const int c0 = H->col_ptr[a], nc = H->col_ptr[a + 1] - c0;
                     const cd *strip = vals.data() + H->strip_off[a];
-                    for (int i = 0; i < na; ++i) {
-                        cd s = 0;
-                        for (int c = 0; c < nc; ++c) s += strip[(size_t)c * na + i] * x[H->perm[H->strip_col[c0 + c]]];
-                        y[H->perm[r0 + i]] = s;
+                    std::vector<cd> acc(na, 0.0);
+                    for (int c = 0; c < nc; ++c) {          // column-major strip: contiguous reads
+                        const cd xv = x[H->perm[H->strip_col[c0 + c]]];
+                        const cd *col = strip + (size_t)c * na;
+                        for (int i = 0; i < na; ++i) acc[i] += col[i] * xv;
                     }
+                    for (int i = 0; i < na; ++i) y[H->perm[r0 + i]] = acc[i];
                 }
             });
         for (auto &th : pool) th.join();
@@ -431,11 +473,7 @@ struct Gmres {
                     ++used;
                     ++iterations;
                     for (int pass = 0; pass < 2; ++pass)   // classical Gram-Schmidt, twice
-                        for (int j = 0; j <= k; ++j) {
-                            const cd hj = dotc(V[j].data(), V[k + 1].data(), n);
-                            Hm[(size_t)j * m + k] += hj;
-                            for (int64_t i = 0; i < n; ++i) V[k + 1][i] -= hj * V[j][i];
-                        }
+                        cgs_pass(V, k, V[k + 1], &Hm[k], m);
                     const double hn = nrm2(V[k + 1]);
                     Hm[(size_t)(k + 1) * m + k] = hn;
                     if (hn > 0)
@@ -466,9 +504,14 @@ struct Gmres {
                     for (int j = i + 1; j < k; ++j) s -= Hm[(size_t)i * m + j] * y[j];
                     y[i] = s / Hm[(size_t)i * m + i];
                 }
-                std::fill(t.begin(), t.end(), 0.0);
-                for (int j = 0; j < k; ++j)
-                    for (int64_t i = 0; i < n; ++i) t[i] += y[j] * V[j][i];
+                parallel_segments(n, [&](int, int64_t i0, int64_t i1) {
+                    for (int64_t i = i0; i < i1; ++i) t[i] = 0.0;
+                    for (int j = 0; j < k; ++j) {
+                        const cd yj = y[j];
+                        const cd *v = V[j].data();
+                        for (int64_t i = i0; i < i1; ++i) t[i] += yj * v[i];
+                    }
+                });
                 if (sai) sai->apply(t.data(), z.data());
                 else z = t;
                 for (int64_t i = 0; i < n; ++i) d[i] += z[i];

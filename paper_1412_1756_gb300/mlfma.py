@@ -350,9 +350,13 @@ class MlfmaPlan:
         lam = np.zeros(nev)
         J = np.zeros((self.n, nev)) if vectors else None
         st = CmStats()
-        _check(self._lib.cm_ira_solve(self._h, ctypes.byref(o), _np_ptr(lam), _np_ptr(J) if vectors else None,
-                                      ctypes.byref(st)))
+        rc = self._lib.cm_ira_solve(self._h, ctypes.byref(o), _np_ptr(lam), _np_ptr(J) if vectors else None,
+                                    ctypes.byref(st))
         stats = {f: getattr(st, f) for f, _ in CmStats._fields_}
+        if rc != 0:
+            err = MlfmaError(rc, self._lib.mlfma_last_error().decode())
+            err.stats, err.values = stats, lam   # ENOTCONV: counters and the current Ritz values
+            raise err
         return lam, J, stats
 
     def cm_derivatives(self, lam, J, prec=FP64) -> np.ndarray:
