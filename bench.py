@@ -328,6 +328,26 @@ def main():
     ms64 = timed(lambda: plan.matvec(x64_1, y64), steps64, a.warmup)
     fp64_rate = replica_rate(1, steps64, ms64 / 1e3, 1)
 
+    # --- FP32 against FP64 stage by stage on the timed inputs: the outgoing
+    # field of every far level (aggregation and upward pass), the incoming
+    # field (translation and downward pass) and the product
+    stage_err = {}
+    if rank == 0:
+        y64b = plan.matvec(x32.to(torch.float64)).cpu().numpy()
+        fields = {}
+        for prec in (FP32, FP64):
+            plan.matvec(x32 if prec == FP32 else x32.to(torch.float64))
+            for l in range(2, info["leaf_level"] + 1):
+                for w, nm in ((0, "S"), (1, "G")):
+                    fields[(prec, nm, l)] = plan.export_field(prec, w, l, B)
+        for (prec, nm, l), f64 in list(fields.items()):
+            if prec != FP64:
+                continue
+            f32 = fields[(FP32, nm, l)].astype(np.complex128)
+            stage_err["%s%d" % (nm, l)] = float(np.linalg.norm(f32 - f64) / np.linalg.norm(f64))
+        y32b = plan.matvec(x32).cpu().numpy()
+        stage_err["y"] = float(np.linalg.norm(y32b - y64b) / np.linalg.norm(y64b))
+
     # --- error against the FP64 oracle on the timed inputs (sampled rows)
     y32_np = y32.cpu().numpy()
     y64_np = y64.cpu().numpy()
@@ -408,6 +428,7 @@ def main():
                                    "speedup_of_mixed_batched": value / (fp64_rate * world)},
             "err_vs_oracle": {"fp32_batched": err, "fp64_single": err64 if rank == 0 else None,
                               "rows": 16, "bound": 1e-3},
+            "err_fp32_vs_fp64_by_stage": stage_err,
             "roofline": roof,
             "hbm_frac_by_stage": hbm_stages,
             "fp32_alu_frac_by_stage": alu_stages,

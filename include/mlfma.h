@@ -425,6 +425,20 @@ enum {
 mlfma_status mlfma_export(mlfma_plan_t plan, int what, int level, void *dst, int64_t cap,
                           int64_t *needed);
 
+/*
+ * Copy a far level's field as the last Z product (mlfma_matvec, adjoint,
+ * host or profile variant) in `prec` left it, for per-stage error reports:
+ * which = 0 the outgoing field S (after aggregation, Eq. (11) and the upward
+ * pass), 1 the incoming field G (after translation, Eq. (8), and the
+ * downward pass), level 2..leaf, B = the internal real columns of that
+ * product (2 per complex column).  dst: host [boxes][2][K][B] interleaved
+ * complex of the precision's real type, in leaf (Morton) box order; *needed
+ * receives the byte count (dst may be NULL to ask).  Waits for the device.
+ * Errors: EINVAL, ECUDA.
+ */
+mlfma_status mlfma_export_field(mlfma_plan_t plan, int prec, int which, int level, int64_t B, void *dst,
+                                int64_t cap, int64_t *needed);
+
 /* Release everything the plan owns (waits for its work).  NULL is a no-op. */
 void mlfma_destroy(mlfma_plan_t plan);
 

@@ -1203,6 +1203,31 @@ mlfma_status mlfma_tune_set(mlfma_plan_t p, int64_t B, int xc, int prec, const i
     return MLFMA_OK;
 }
 
+mlfma_status mlfma_export_field(mlfma_plan_t p, int prec, int which, int level, int64_t B, void *dst, int64_t cap,
+                                int64_t *needed)
+{
+    if (check_plan(p)) return MLFMA_EINVAL;
+    if (!p->on_device) return fail(MLFMA_EINVAL, "plan was built host-only");
+    if ((prec == MLFMA_FP32 && !p->has32) || (prec == MLFMA_FP64 && !p->has64) || (prec != 0 && prec != 1))
+        return fail(MLFMA_EINVAL, "precision not set up in this plan");
+    if (which != 0 && which != 1) return fail(MLFMA_EINVAL, "which must be 0 (outgoing S) or 1 (incoming G)");
+    if (!(level >= 2 && level <= p->host.leaf)) return fail(MLFMA_EINVAL, "level has no far work");
+    if (B < 1 || B > p->opts.max_batch) return fail(MLFMA_EINVAL, "B must be in 1..max_batch");
+    const Level &Lv = p->host.lv[level];
+    const size_t rsz = prec == MLFMA_FP64 ? 8 : 4;
+    const size_t bytes = (size_t)Lv.nbox() * 2 * Lv.K * B * 2 * rsz;
+    if (needed) *needed = (int64_t)bytes;
+    if (!dst) return MLFMA_OK;
+    if (cap < (int64_t)bytes) return fail(MLFMA_EINVAL, "destination too small");
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "mlfma_export_field");
+    const void *src = prec == MLFMA_FP64 ? (const void *)(which ? p->a64.lv[level].G : p->a64.lv[level].S)
+                                         : (const void *)(which ? p->a32.lv[level].G : p->a32.lv[level].S);
+    e = cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MLFMA_OK : cuda_fail(e, "mlfma_export_field");
+}
+
 mlfma_status mlfma_matvec_x(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream)
 {
     return product(p, x, xc, y, B, prec, stream, 0, false, nullptr, KIND_X);

@@ -25,7 +25,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIM
 EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg_edges", "mlfma_matvec",
             "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint", "mlfma_matvec_x",
             "mlfma_matvec_r", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
-            "mlfma_profile_stages", "mlfma_tune", "mlfma_tune_get", "mlfma_tune_set", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
+            "mlfma_profile_stages", "mlfma_export_field", "mlfma_tune", "mlfma_tune_get", "mlfma_tune_set", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
             "cm_eig_derivatives",
             "mlfma_set_create", "mlfma_set_matvec", "mlfma_set_info", "mlfma_set_plan", "mlfma_set_destroy",
             "mlfma_destroy", "mlfma_last_error"]
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = False):
     L.mlfma_sync.argtypes = [P, P]
     L.mlfma_profile_stages.argtypes = [P, P, I, P, I64, I, P, P]
     L.mlfma_tune.argtypes = [P, I64, I, I, P, P, P]
+    L.mlfma_export_field.argtypes = [P, I, I, I, I64, P, I64, ctypes.POINTER(I64)]
     L.mlfma_tune_get.argtypes = [P, I64, I, I, P]
     L.mlfma_tune_set.argtypes = [P, I64, I, I, P]
     L.mlfma_cm_default_opts.argtypes = [ctypes.POINTER(CmOpts)]
@@ -309,6 +310,19 @@ class MlfmaPlan:
         _check(self._lib.mlfma_tune(self._h, int(B), 1 if complex_x else 0, int(prec), ctypes.c_void_p(s),
                                     ctypes.byref(d), ctypes.byref(t)))
         return d.value, t.value
+
+    def export_field(self, prec, which, level, B) -> np.ndarray:
+        """Field of a far level after the last product in `prec` (which 0 =
+        outgoing S, 1 = incoming G): complex [boxes, 2, K, B], leaf box order."""
+        need = ctypes.c_int64()
+        _check(self._lib.mlfma_export_field(self._h, int(prec), int(which), int(level), int(B), None, 0,
+                                            ctypes.byref(need)))
+        buf = np.zeros(need.value, np.uint8)
+        _check(self._lib.mlfma_export_field(self._h, int(prec), int(which), int(level), int(B), _np_ptr(buf),
+                                            need.value, ctypes.byref(need)))
+        cdt = np.complex64 if prec == FP32 else np.complex128
+        K = self.info()["samples_K"][level]
+        return buf.view(cdt).reshape(-1, 2, K, int(B))
 
     def tune_get(self, B, prec=FP32, complex_x=False) -> np.ndarray:
         """Launch shapes used for (B, prec) (include/mlfma.h: mlfma_tune_get)."""
