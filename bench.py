@@ -156,7 +156,16 @@ def kernel_digest():
 # DRAM bytes (read + write) per launch measured by ncu at this workload and
 # B = 64: {(stage, kernel source digest): bytes}.  Summaries in profiles/.
 NCU_TRAFFIC = {
-    ("translate4", "f0327da562854f52"): 193_558_016 + 156_430_336,
+    ("near", "53cc9ae71ce75206"): 108_645_632 + 4_603_904,
+    ("radiate", "53cc9ae71ce75206"): 90_378_752 + 133_051_904,
+    ("translate4", "53cc9ae71ce75206"): 193_549_056 + 156_163_328,
+    ("up3", "53cc9ae71ce75206"): 232_115_712 + 82_766_848,
+    ("translate3", "53cc9ae71ce75206"): 110_322_944 + 71_647_744,
+    ("up2", "53cc9ae71ce75206"): 111_794_176 + 25_882_880,
+    ("translate2", "53cc9ae71ce75206"): 52_891_904 + 7_876_864,
+    ("down2", "53cc9ae71ce75206"): 162_190_080 + 60_851_200,
+    ("down3", "53cc9ae71ce75206"): 301_853_440 + 143_796_992,
+    ("receive", "53cc9ae71ce75206"): 367_722_752 + 12_132_096,
 }
 
 
