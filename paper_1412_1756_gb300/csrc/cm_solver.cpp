@@ -15,6 +15,7 @@
 // product, R := -Re Zp and X := +Im Zp, so Z_H := R + iX = -conj(Zp) and
 // Z_H^-1 b = conj(Zp^-1 (-conj b)).
 #include "../../include/mlfma.h"
+#include "krylov.h"
 #include "plan_host.h"
 
 #include <cuda_runtime.h>
@@ -23,6 +24,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <memory>
 #include <cstring>
 #include <random>
 #include <string>
@@ -435,6 +437,7 @@ struct Gmres {
     Which which;
     int prec, restart, maxit, check_prec;
     double tol;
+    DeviceGmres *dev = nullptr;   // FP32 passes on the device when set
     int64_t iterations = 0;
 
     mlfma_status solve(const std::vector<cd> &b, std::vector<cd> &w, bool &converged)
@@ -457,6 +460,16 @@ struct Gmres {
             // a pass with FP32 products can lower its own residual by ~1e-5 at
             // most; the FP64 check and further passes do the rest
             const double target = std::max(0.5 * tol * bn, (prec == MLFMA_FP32 ? 1e-5 : 0.0) * rn);
+            if (dev && prec == MLFMA_FP32 && rn > target) {
+                std::string err;
+                const int it = device_gmres_run(dev, which == PROD_Z ? 0 : 1, r.data(), d.data(), target, maxit - used,
+                                                err);
+                if (it < 0) return fail(MLFMA_ECUDA, err);
+                used += it;
+                iterations += it;
+                prod->count += it;
+                rn = 0.0;   // the loop below is the host path
+            }
             while (used < maxit && rn > target) {
                 const int m = std::min(restart, maxit - used);
                 V.assign(m + 1, std::vector<cd>(n));
@@ -582,6 +595,13 @@ extern "C" mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opt
     near.shrink_to_fit();
     Gmres gm{&prod, o.use_sai ? &sai : nullptr, o.op == MLFMA_CM_ZINV_R ? PROD_Z : PROD_X, o.prec,
              o.gmres_restart, o.max_inner, has64 ? MLFMA_FP64 : o.prec, o.gmres_tol};
+    std::unique_ptr<DeviceGmres, void (*)(DeviceGmres *)> dgm(nullptr, device_gmres_destroy);
+    if (o.prec == MLFMA_FP32) {   // FP32 inner passes on the device
+        std::string err;
+        dgm.reset(device_gmres_create(plan, o.use_sai ? sai.vals.data() : nullptr, o.gmres_restart, err));
+        if (!dgm) return fail(MLFMA_ECUDA, err);
+        gm.dev = dgm.get();
+    }
 
     // the operator of Eq. (SEP1) or (SEP)
     std::vector<cd> tmp(n), rhs(n), sol(n);
