@@ -174,22 +174,24 @@ def test_far_pair_tiny_mesh():
         assert rel(y, Z[:, j]) < 1e-3
 
 
-def test_fields_per_stage_fp32_against_fp64():
+@pytest.mark.parametrize("name,B", [("sphere-r2m-ico5", 8), ("plate6m-strips", 16)])
+def test_fields_per_stage_fp32_against_fp64(name, B):
     """mlfma_export_field: the outgoing and incoming fields of every far level
     after a product, FP32 against FP64 on the same columns (the per-stage
-    error report of the mixed-precision path)."""
-    W, v, t, P = problem("sphere-r2m-ico5")
-    x = workloads.rhs(P.n, 8, W.seed)
+    error report of the mixed-precision path); also the product itself."""
+    W, v, t, P = problem(name)
+    x = workloads.rhs(P.n, B, W.seed)
     inf = P.info()
-    f = {}
+    f, y = {}, {}
     for dt, prec in ((torch.float32, M.FP32), (torch.float64, M.FP64)):
-        P.matvec(gpu(x, dt))
+        y[prec] = P.matvec(gpu(x, dt)).cpu().numpy()
         for l in range(2, inf["leaf_level"] + 1):
             for w in (0, 1):
-                f[(prec, w, l)] = P.export_field(prec, w, l, 8)
+                f[(prec, w, l)] = P.export_field(prec, w, l, B)
     for l in range(2, inf["leaf_level"] + 1):
         for w in (0, 1):
             a, b = f[(M.FP32, w, l)].astype(np.complex128), f[(M.FP64, w, l)]
-            assert a.shape == (inf["box_count"][l], 2, inf["samples_K"][l], 8)
+            assert a.shape == (inf["box_count"][l], 2, inf["samples_K"][l], B)
             assert np.linalg.norm(b) > 0
             assert rel(a, b) < 1e-4, (l, w, rel(a, b))
+    assert rel(y[M.FP32], y[M.FP64]) < 1e-5
