@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip mlfma_tune (built-in launch shapes)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of tuned launch shapes: reuse an entry for this GPU and tree, else tune and store")
     ap.add_argument("--stages-only", action="store_true",
                     help="build the plan and run one serial per-stage pass (for profilers), print stage times")
     return ap.parse_args()
@@ -283,7 +285,7 @@ def main():
     if a.stages_only:
         xs = torch.from_numpy(workloads.rhs(plan.n, B, wl.seed)).to("cuda", torch.float32)
         if not a.no_tune:
-            plan.tune(B, FP32)
+            plan.tune(B, FP32, cache=a.tune_cache)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("profile")   # profilers can select this pass (ncu --nvtx-include profile/)
         st = plan.profile_stages(xs)
@@ -320,10 +322,11 @@ def main():
     # --- launch shapes tuned for both timed products before any timing
     tuned = None
     if not a.no_tune:
-        d32, t32 = plan.tune(B, FP32)
-        d64, t64 = plan.tune(1, FP64)
-        tuned = {"fp32_b%d_stage_sum_ms" % B: [round(d32, 4), round(t32, 4)],
-                 "fp64_b1_stage_sum_ms": [round(d64, 4), round(t64, 4)]}
+        d32, t32 = plan.tune(B, FP32, cache=a.tune_cache)
+        d64, t64 = plan.tune(1, FP64, cache=a.tune_cache)
+        r4 = lambda v: None if v is None else round(v, 4)   # None: shapes taken from the cache
+        tuned = {"fp32_b%d_stage_sum_ms" % B: [r4(d32), r4(t32)],
+                 "fp64_b1_stage_sum_ms": [r4(d64), r4(t64)]}
 
     # --- mixed precision, batched (the headline)
     with ClockSampler(local) as clk:

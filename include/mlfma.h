@@ -239,9 +239,12 @@ mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec
  *   [3 + 44 + l]  translation at level l: 1 two columns per thread; 2..6 one
  *                 column with 1, 2, 4, 8, 16 lanes per output; 7 / 8 one warp
  *                 per (child, sample) with 2 / 1 columns per lane
- * A pinned shape that does not apply to the plan makes the product fail
- * with MLFMA_ECUDA (invalid configuration).  mlfma_tune_set drops a graph
- * captured for the key (and waits for the device to do so).
+ * Columns per CTA are powers of two (1, 2, 4, 8, 16).  mlfma_tune_set
+ * returns MLFMA_EINVAL, and pins nothing, for B outside 1..max_batch, an
+ * unknown prec or a value outside the sets above; a listed shape that does
+ * not apply to the plan makes the product fail with MLFMA_ECUDA (invalid
+ * configuration).  mlfma_tune_set drops a graph captured for the key (and
+ * waits for the device to do so).
  */
 #define MLFMA_TUNE_FIELDS (3 + 3 * 22)
 mlfma_status mlfma_tune_get(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec, int32_t *choices);

@@ -1184,6 +1184,19 @@ mlfma_status mlfma_tune_set(mlfma_plan_t p, int64_t B, int xc, int prec, const i
 {
     if (check_plan(p)) return MLFMA_EINVAL;
     if (!choices) return fail(MLFMA_EINVAL, "choices is NULL");
+    if (B < 1 || B > p->opts.max_batch) return fail(MLFMA_EINVAL, "B must be in 1..max_batch");
+    if (prec != MLFMA_FP32 && prec != MLFMA_FP64) return fail(MLFMA_EINVAL, "prec must be MLFMA_FP32 or MLFMA_FP64");
+    {
+        // every value must be 0 (built-in) or one of the documented shapes
+        auto pow2 = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
+        bool ok = choices[0] >= 0 && choices[0] <= 3 && choices[1] >= 0 && choices[1] <= 4 &&
+                  choices[2] >= 0 && choices[2] <= 3;
+        for (int l = 0; l < MLFMA_MAX_LEVELS && ok; ++l) {
+            const int u = choices[3 + l], d = choices[3 + MLFMA_MAX_LEVELS + l], r = choices[3 + 2 * MLFMA_MAX_LEVELS + l];
+            ok = (u == 0 || pow2(u) || u == 100) && (d == 0 || pow2(d) || d == 104 || d == 108) && r >= 0 && r <= 8;
+        }
+        if (!ok) return fail(MLFMA_EINVAL, "a launch-shape choice is outside its documented set");
+    }
     const int Bi = (int)(B * (xc ? 2 : 1));
     Tuning t;
     t.near = choices[0]; t.radiate = choices[1]; t.receive = choices[2];

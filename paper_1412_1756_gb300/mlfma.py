@@ -141,6 +141,7 @@ class MlfmaPlan:
         if _handle is not None:   # a plan owned by a MlfmaPlanSet
             self._lib, self._h, self._owned = L, _handle, False
             self.k, self.max_batch, self.host_only = float(k), int(max_batch), False
+            self.interp_order = int(interp_order)
             n = ctypes.c_int64()
             _check(L.mlfma_num_unknowns(_handle, ctypes.byref(n)))
             self.n = int(n.value)
@@ -169,6 +170,7 @@ class MlfmaPlan:
         self.k = float(k)
         self.max_batch = int(max_batch)
         self.host_only = bool(host_only)
+        self.interp_order = int(interp_order)
         n = ctypes.c_int64()
         _check(L.mlfma_num_unknowns(h, ctypes.byref(n)))
         self.n = int(n.value)
@@ -301,14 +303,31 @@ class MlfmaPlan:
                                            ctypes.c_void_p(stream or 0)))
         return y.reshape(self.n) if squeeze else y
 
-    def tune(self, B, prec=FP32, complex_x=False, stream=None):
+    def tune(self, B, prec=FP32, complex_x=False, stream=None, cache=None):
         """Autotune the launch shapes for products of B columns; returns the
-        serial stage-time sums (ms) with the built-in and the chosen shapes."""
+        serial stage-time sums (ms) with the built-in and the chosen shapes.
+        cache: path of a JSON file of earlier choices keyed by GPU, tree
+        geometry, columns and precision; a hit pins the stored shapes
+        (mlfma_tune_set) without timing and returns (None, None)."""
         import torch
+        key = None
+        if cache is not None:
+            key = tune_cache_key(torch.cuda.get_device_name(), self.info(), self.interp_order, B, prec, complex_x)
+            entry = _read_tune_cache(cache).get(key)
+            if isinstance(entry, list) and len(entry) == TUNE_FIELDS:
+                try:
+                    self.tune_set(B, entry, prec, complex_x)
+                    return None, None
+                except (MlfmaError, TypeError, ValueError):   # a damaged entry: tune again and replace it
+                    pass
         d, t = ctypes.c_double(), ctypes.c_double()
         s = torch.cuda.current_stream().cuda_stream if stream is None else stream
         _check(self._lib.mlfma_tune(self._h, int(B), 1 if complex_x else 0, int(prec), ctypes.c_void_p(s),
                                     ctypes.byref(d), ctypes.byref(t)))
+        if key is not None:
+            table = _read_tune_cache(cache)
+            table[key] = self.tune_get(B, prec, complex_x).tolist()
+            _write_tune_cache(cache, table)
         return d.value, t.value
 
     def export_field(self, prec, which, level, B) -> np.ndarray:
@@ -396,6 +415,34 @@ class MlfmaPlan:
             self.close()
         except Exception:
             pass
+
+
+def tune_cache_key(gpu_name, info, interp_order, B, prec, complex_x) -> str:
+    """Key of a tuned-shape entry: the GPU, the tree's geometry (boxes,
+    truncation numbers and samples per level, leaf sizes, near entries), the
+    interpolation order, the columns and the precision."""
+    geo = "/".join("%d:%d:%d" % (b, l, k) for b, l, k in zip(info["box_count"], info["trunc_L"], info["samples_K"]))
+    return "|".join([str(gpu_name), "n%d" % info["n"], geo, "leaf%d" % info["max_leaf_unknowns"],
+                     "nnz%d" % info["near_nnz"], "p%d" % interp_order, "B%d" % int(B),
+                     "fp64" if prec == FP64 else "fp32", "complex" if complex_x else "real"])
+
+
+def _read_tune_cache(path) -> dict:
+    import json
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        return t if isinstance(t, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def _write_tune_cache(path, table: dict):
+    import json
+    tmp = "%s.tmp.%d" % (path, os.getpid())
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 def _autograd_function():

@@ -90,3 +90,37 @@ def test_every_candidate_shape_computes_the_same_product(dt, prec, tol):
         assert rel(y, ref) < tol, (field, c, rel(y, ref))
     P.tune_set(32, np.zeros(M.TUNE_FIELDS, np.int32), prec)
     assert np.array_equal(P.matvec(x).cpu().numpy(), ref)
+
+
+def test_tune_cache_reuses_shapes(tmp_path):
+    """A second plan of the same tree takes its shapes from the cache file
+    (no timing) and computes the same product as the tuned first plan."""
+    W = workloads.get("sphere-r0.5m-ico3")
+    v, t = W.mesh()
+    path = str(tmp_path / "tune.json")
+    P1 = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=8, precisions=(M.FP32,))
+    d, tt = P1.tune(8, M.FP32, cache=path)
+    assert d is not None and tt <= d
+    stored = M._read_tune_cache(path)
+    assert len(stored) == 1
+    P2 = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=8, precisions=(M.FP32,))
+    assert P2.tune(8, M.FP32, cache=path) == (None, None)
+    assert np.array_equal(P2.tune_get(8, M.FP32), P1.tune_get(8, M.FP32))
+    x = torch.from_numpy(workloads.rhs(P1.n, 8, W.seed)).to("cuda", torch.float32)
+    assert rel(P2.matvec(x).cpu().numpy(), P1.matvec(x).cpu().numpy()) < 1e-6
+
+
+def test_tune_set_rejects_undocumented_shapes():
+    W = workloads.get("sphere-r0.5m-ico2")
+    v, t = W.mesh()
+    P = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=8)
+    good = P.tune_get(4, M.FP32)
+    for field, value in ((0, 4), (1, 5), (2, -1), (3 + 2, 3), (3 + 22 + 2, 100), (3 + 44 + 2, 9)):
+        bad = good.copy()
+        bad[field] = value
+        with pytest.raises(M.MlfmaError):
+            P.tune_set(4, bad, M.FP32)
+    with pytest.raises(M.MlfmaError):
+        P.tune_set(9, good, M.FP32)
+    P.tune_set(4, good, M.FP32)
+    assert np.array_equal(P.tune_get(4, M.FP32), good)

@@ -205,3 +205,25 @@ def test_interpolation_band_limited(order, tol):
                 fc = (tc @ pol) * np.exp(1j * W.k * (khc @ d))
                 fp = (tp @ pol) * np.exp(1j * W.k * (khp @ d))
                 assert np.abs(Mx @ fc - fp).max() < tol * np.abs(fp).max()
+
+
+def test_tune_cache_key_and_file(tmp_path):
+    """The tuned-shape cache: keys separate GPUs, trees, columns and
+    precisions; the file round-trips and a damaged file reads as empty."""
+    W, v, t, P = host_plan("sphere-r2m-ico5")
+    inf = P.info()
+    k1 = M.tune_cache_key("GPU A", inf, 10, 64, M.FP32, False)
+    assert k1 == M.tune_cache_key("GPU A", inf, 10, 64, M.FP32, False)
+    others = [M.tune_cache_key("GPU B", inf, 10, 64, M.FP32, False), M.tune_cache_key("GPU A", inf, 8, 64, M.FP32, False),
+              M.tune_cache_key("GPU A", inf, 10, 32, M.FP32, False), M.tune_cache_key("GPU A", inf, 10, 64, M.FP64, False),
+              M.tune_cache_key("GPU A", inf, 10, 64, M.FP32, True)]
+    assert len(set(others + [k1])) == 6
+    W2, v2, t2, P2 = host_plan("sphere-r0.5m-ico3")
+    assert M.tune_cache_key("GPU A", P2.info(), 10, 64, M.FP32, False) != k1
+    path = str(tmp_path / "tune.json")
+    assert M._read_tune_cache(path) == {}
+    M._write_tune_cache(path, {k1: list(range(M.TUNE_FIELDS))})
+    assert M._read_tune_cache(path)[k1] == list(range(M.TUNE_FIELDS))
+    with open(path, "w") as f:
+        f.write("{not json")
+    assert M._read_tune_cache(path) == {}
