@@ -352,6 +352,71 @@ mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opts, double *
                           mlfma_cm_stats *stats);
 
 /*
+ * Characteristic modes with a block of vectors (Section IV, Eq. (SEP), with
+ * the single Arnoldi vector replaced by a block): the nev characteristic
+ * values nearest zero of X J = lambda R J by shift-invert subspace iteration
+ * (simultaneous iteration, Rutishauser 1970) on T = X^-1 R.  opts->ncv is
+ * the block size p (nev <= p <= min(N, max_batch)); opts->op must be
+ * MLFMA_CM_XINV_R.  Each iteration
+ *   1. solves X W = R Y for all p columns together by restarted GMRES on the
+ *      device (opts->gmres_restart, opts->max_inner steps, relative residual
+ *      opts->gmres_tol per column), right-preconditioned by the sparse
+ *      approximate inverse of the near part of X (as cm_ira_solve); every
+ *      GMRES step is one MLFMA product of p real columns in FP32 with FP64
+ *      inner products; a column holding a Ritz pair (lambda, y) with
+ *      residual below 0.1 starts from y / lambda, the others from 0.  The
+ *      wanted modes are near-null vectors of X, which restarted GMRES
+ *      loses at each restart: a long restart (hundreds of steps; device
+ *      memory (restart + 1) N p 4 bytes) is the remedy;
+ *   2. takes the Ritz pairs of T on span Y in the R inner product
+ *      (cm_rayleigh_ritz, FP64 on the host; no further solve);
+ *   3. moves to the improved Ritz vectors Y' = W coef and applies Z to them
+ *      once in opts->prec (X Y' = Im Z Y', R Y' = -Re Z Y').
+ * The values are the Rayleigh quotients y^T X y / y^T R y of the vectors;
+ * converged when the nev pairs nearest zero have
+ *   ||X y - lambda R y|| / (||X y|| + |lambda| ||R y||) <= opts->tol.
+ * The residual cannot fall much below the inner tolerance (FP32 inner solves
+ * reach ~1e-6).  A degenerate cluster of values converges as a whole when
+ * it fits in the block; the rate for value i is |lambda_i| /
+ * |lambda_(p+1)| per iteration.  opts->max_restarts bounds the iterations.
+ * Needs a device plan with FP32 (and FP64 for prec = MLFMA_FP64).  With the
+ * environment variable MLFMA_CM_TRACE set, one line per iteration goes to
+ * stderr.
+ *  lambda  host [nev], sorted by |lambda|
+ *  J       host [N][nev] real currents, unit 2-norm, largest entry positive;
+ *          may be NULL
+ *  stats   restarts = iterations, inner_iterations = GMRES steps (each one
+ *          product of p columns), products = all block products,
+ *          inner_converged = every inner solve met gmres_tol; may be NULL
+ * Synchronous.  Errors: EINVAL, ENOTCONV (not converged within
+ * max_restarts: lambda holds the current values; or a singular near-field
+ * block of the preconditioner), ECUDA.
+ */
+mlfma_status cm_block_solve(mlfma_plan_t plan, const mlfma_cm_opts *opts, double *lambda, double *J,
+                            mlfma_cm_stats *stats);
+
+/*
+ * The Rayleigh-Ritz step of cm_block_solve, on host memory only (no device
+ * work): for a real basis Y, its product RY = R Y and W = X^-1 R Y (all
+ * [n][p] row-major FP64; X, R symmetric, R positive semidefinite), the
+ * Ritz pairs of T = X^-1 R on span Y in the R inner product, where T is
+ * self-adjoint: A c = mu B c with A = (R Y)^T W and B = Y^T R Y
+ * (symmetrised).  B = Ub D Ub^T; directions with D < 1e-9 max D carry no R
+ * energy (mu = 0) and are dropped; mu are the eigenvalues of
+ * D^-1/2 Ub^T A Ub D^-1/2 (cyclic Jacobi).  On the kept directions B is
+ * definite, so the Ritz values interlace the eigenvalues mu = 1 / lambda of
+ * T and none exceeds the largest |mu|, whatever the inertia of X.
+ *  mu      [p] out: the *rank Ritz values sorted by |mu| (largest first,
+ *          i.e. lambda = 1 / mu nearest zero first), 0 after
+ *  coef    [p][p] out: Ritz vectors Y coef (improved: W coef = T Y coef);
+ *          columns beyond *rank zero
+ *  rank    out: number of Ritz pairs
+ * Errors: EINVAL for NULL pointers or an empty block.
+ */
+mlfma_status cm_rayleigh_ritz(int64_t n, int p, const double *Y, const double *RY, const double *W, double *mu,
+                              double *coef, int *rank);
+
+/*
  * Wavenumber slopes of characteristic values, for tracking modes over
  * frequency: for each pair (lambda_m, J_m) of X J = lambda R J (R = -Re Z,
  * X = Im Z, J real, e.g. from cm_ira_solve), by first-order perturbation of

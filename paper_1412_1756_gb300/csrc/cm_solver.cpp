@@ -25,6 +25,8 @@
 #include <cmath>
 #include <complex>
 #include <memory>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <random>
 #include <string>
@@ -32,8 +34,11 @@
 #include <vector>
 
 namespace mlfma {
+template <class R> struct ProductArgs;
 bool plan_near_host(mlfma_plan_t p, std::vector<std::complex<double>> &vals, const PlanHost **host);
 void set_last_error(const std::string &msg);
+bool plan_product_view(mlfma_plan_t p, int prec, ProductArgs<float> *a32, ProductArgs<double> *a64, int *device,
+                       int *max_batch, int64_t *n);
 }  // namespace mlfma
 
 using namespace mlfma;
@@ -203,6 +208,161 @@ bool hessenberg_eig(int m, std::vector<cd> H, std::vector<cd> &w, std::vector<cd
         for (int i = 0; i < m; ++i) X[(size_t)i * m + j] /= nn;
     }
     return true;
+}
+
+// ---------------------------------------------- symmetric eigen (real) ---
+// Eigenvalues w and orthonormal eigenvectors (columns of U, row-major m x m)
+// of the symmetric m x m matrix A by cyclic Jacobi rotations (Jacobi 1846;
+// the threshold-free cyclic form of Rutishauser 1966): each rotation in the
+// (p, q) plane zeroes A_pq, sweeps repeat until the off-diagonal part is at
+// rounding level.
+void sym_eig(int m, std::vector<double> A, std::vector<double> &w, std::vector<double> &U)
+{
+    U.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) U[(size_t)i * m + i] = 1.0;
+    auto a = [&](int i, int j) -> double & { return A[(size_t)i * m + j]; };
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0, tot = 0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                tot += a(i, j) * a(i, j);
+                if (i != j) off += a(i, j) * a(i, j);
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int pp = 0; pp < m - 1; ++pp)
+            for (int q = pp + 1; q < m; ++q) {
+                const double apq = a(pp, q);
+                if (apq == 0) continue;
+                // tan of the angle that zeroes (p, q): the smaller root of
+                // t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq)
+                const double theta = (a(q, q) - a(pp, pp)) / (2 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::abs(theta) + std::sqrt(theta * theta + 1));
+                const double c = 1 / std::sqrt(t * t + 1), sn = t * c;
+                for (int k = 0; k < m; ++k) {   // A J (columns p, q)
+                    const double akp = a(k, pp), akq = a(k, q);
+                    a(k, pp) = c * akp - sn * akq;
+                    a(k, q) = sn * akp + c * akq;
+                }
+                for (int k = 0; k < m; ++k) {   // J^T A (rows p, q)
+                    const double apk = a(pp, k), aqk = a(q, k);
+                    a(pp, k) = c * apk - sn * aqk;
+                    a(q, k) = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < m; ++k) {   // U J
+                    double &ukp = U[(size_t)k * m + pp], &ukq = U[(size_t)k * m + q];
+                    const double x = ukp, y = ukq;
+                    ukp = c * x - sn * y;
+                    ukq = sn * x + c * y;
+                }
+            }
+    }
+    w.resize(m);
+    for (int i = 0; i < m; ++i) w[i] = a(i, i);
+}
+
+// out (p x q, row-major) = U^T V for host blocks U [n][p], V [n][q]
+void gram(int64_t n, int p, int q, const double *U, const double *V, std::vector<double> &out)
+{
+    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n / 1024));
+    std::vector<double> part((size_t)nt * p * q, 0.0);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&, t]() {
+            double *acc = part.data() + (size_t)t * p * q;
+            for (int64_t i = n * t / nt; i < n * (t + 1) / nt; ++i)
+                for (int a = 0; a < p; ++a) {
+                    const double u = U[i * p + a];
+                    if (u != 0)
+                        for (int b = 0; b < q; ++b) acc[(size_t)a * q + b] += u * V[i * q + b];
+                }
+        });
+    for (auto &th : pool) th.join();
+    out.assign((size_t)p * q, 0.0);
+    for (int t = 0; t < nt; ++t)
+        for (size_t e = 0; e < (size_t)p * q; ++e) out[e] += part[(size_t)t * p * q + e];
+}
+
+// out [n][q] = U [n][p] C (p x q, row-major)
+void right_multiply(int64_t n, int p, int q, const double *U, const std::vector<double> &C, double *out)
+{
+    parallel_segments(n, [&](int, int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i) {
+            double *o = out + i * q;
+            for (int b = 0; b < q; ++b) o[b] = 0;
+            for (int a = 0; a < p; ++a) {
+                const double u = U[i * p + a];
+                if (u != 0)
+                    for (int b = 0; b < q; ++b) o[b] += u * C[(size_t)a * q + b];
+            }
+        }
+    });
+}
+
+// Rayleigh-Ritz for T = X^-1 R in the R inner product on span Y, from Y, R Y
+// and W = T Y (so no further solve): T is self-adjoint there (R X^-1 R is
+// symmetric), the projected pencil is A c = mu B c with A = (R Y)^T W and
+// B = Y^T R Y (both symmetrised).  B = Ub D Ub^T; directions with D below
+// 1e-9 max D carry no R energy (mu = 0 there) and are dropped; mu are the
+// eigenvalues of D^-1/2 Ub^T A Ub D^-1/2 = E diag(mu) E^T (cyclic Jacobi),
+// coef = Ub D^-1/2 E.  With B definite on the kept directions the Ritz
+// values interlace the eigenvalues of T, so no Ritz value exceeds the
+// largest |mu| = 1 / |lambda| of the pencil, whatever the inertia of X (a
+// Rayleigh-Ritz step on the pencil (X, R) itself has no such bound when X is
+// indefinite).  Returns the count r; mu [r] and the columns of coef [p][r]
+// are sorted by |mu|, largest first.
+int ritz_shift_invert(int64_t n, int p, const double *Y, const double *RY, const double *W, std::vector<double> &mu,
+                      std::vector<double> &coef)
+{
+    std::vector<double> A, Bm;
+    gram(n, p, p, RY, W, A);
+    gram(n, p, p, Y, RY, Bm);
+    for (int i = 0; i < p; ++i)   // symmetric parts (exactly symmetric without rounding and solve errors)
+        for (int j = i + 1; j < p; ++j) {
+            const double a = 0.5 * (A[(size_t)i * p + j] + A[(size_t)j * p + i]);
+            const double b = 0.5 * (Bm[(size_t)i * p + j] + Bm[(size_t)j * p + i]);
+            A[(size_t)i * p + j] = A[(size_t)j * p + i] = a;
+            Bm[(size_t)i * p + j] = Bm[(size_t)j * p + i] = b;
+        }
+    std::vector<double> dv, Ub;
+    sym_eig(p, Bm, dv, Ub);
+    const double dmax = *std::max_element(dv.begin(), dv.end());
+    std::vector<int> keep;
+    for (int i = 0; i < p; ++i)
+        if (dmax > 0 && dv[i] > 1e-9 * dmax) keep.push_back(i);
+    const int r = (int)keep.size();
+    if (r == 0) return 0;
+    std::vector<double> S((size_t)p * r);   // p x r
+    for (int a = 0; a < p; ++a)
+        for (int j = 0; j < r; ++j) S[(size_t)a * r + j] = Ub[(size_t)a * p + keep[j]] / std::sqrt(dv[keep[j]]);
+    std::vector<double> AS((size_t)p * r, 0.0), C((size_t)r * r, 0.0);
+    for (int a = 0; a < p; ++a)
+        for (int b = 0; b < p; ++b) {
+            const double ab = A[(size_t)a * p + b];
+            for (int j = 0; j < r; ++j) AS[(size_t)a * r + j] += ab * S[(size_t)b * r + j];
+        }
+    for (int a = 0; a < p; ++a)
+        for (int i = 0; i < r; ++i)
+            for (int j = 0; j < r; ++j) C[(size_t)i * r + j] += S[(size_t)a * r + i] * AS[(size_t)a * r + j];
+    for (int i = 0; i < r; ++i)
+        for (int j = i + 1; j < r; ++j)
+            C[(size_t)i * r + j] = C[(size_t)j * r + i] = 0.5 * (C[(size_t)i * r + j] + C[(size_t)j * r + i]);
+    std::vector<double> ev, E;
+    sym_eig(r, C, ev, E);
+    std::vector<int> order(r);
+    for (int i = 0; i < r; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return std::abs(ev[x]) > std::abs(ev[y]); });
+    mu.resize(r);
+    coef.assign((size_t)p * r, 0.0);
+    for (int i = 0; i < r; ++i) {
+        const int e = order[i];
+        mu[i] = ev[e];
+        for (int a = 0; a < p; ++a) {
+            double sacc = 0;
+            for (int j = 0; j < r; ++j) sacc += S[(size_t)a * r + j] * E[(size_t)j * r + e];
+            coef[(size_t)a * r + i] = sacc;
+        }
+    }
+    return r;
 }
 
 // ------------------------------------------------------- products ---
@@ -733,12 +893,205 @@ extern "C" mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opt
     return MLFMA_OK;
 }
 
+// ------------------------------------------ block subspace iteration ---
+
+extern "C" mlfma_status cm_rayleigh_ritz(int64_t n, int p, const double *Y, const double *RY, const double *W,
+                                         double *mu, double *coef, int *rank)
+{
+    if (n < 1 || p < 1 || !Y || !RY || !W || !mu || !coef || !rank)
+        return fail(MLFMA_EINVAL, "cm_rayleigh_ritz: NULL argument or empty block");
+    std::vector<double> m, c;
+    const int r = ritz_shift_invert(n, p, Y, RY, W, m, c);
+    for (int i = 0; i < p; ++i) mu[i] = i < r ? m[i] : 0.0;
+    for (int a = 0; a < p; ++a)
+        for (int i = 0; i < p; ++i) coef[(size_t)a * p + i] = i < r ? c[(size_t)a * r + i] : 0.0;
+    *rank = r;
+    return MLFMA_OK;
+}
+
+// Eq. (SEP) with a block of ncv vectors: shift-invert subspace iteration
+// (simultaneous iteration, Rutishauser 1970) on T = X^-1 R.  Every
+// iteration solves X W = R Y for the whole block at once (block_gmres_run:
+// one product of ncv real columns per GMRES step), takes the Ritz pairs of T
+// on span Y in the R inner product (ritz_shift_invert: A = (R Y)^T W,
+// B = Y^T R Y), and moves to the improved vectors Y' = W coef, applying Z to
+// Y' once (X Y' and R Y' are its imaginary and negated real parts).  The
+// reported values are the Rayleigh quotients y^T X y / y^T R y of the final
+// vectors (second order in their error).  A degenerate cluster that fits in
+// the block converges as a whole, which a single-vector Krylov method
+// cannot resolve; errors of the inexact solves along near-null vectors of X
+// (interior resonances: currents that do not radiate) are filtered by R.
+// With MLFMA_CM_TRACE set in the environment, one line per iteration goes to
+// stderr.
+extern "C" mlfma_status cm_block_solve(mlfma_plan_t plan, const mlfma_cm_opts *opts, double *lambda, double *J,
+                                       mlfma_cm_stats *stats)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!plan || !opts || !lambda) return fail(MLFMA_EINVAL, "plan, opts and lambda are required");
+    const mlfma_cm_opts o = *opts;
+    int dev = 0, maxb = 0;
+    int64_t n = 0;
+    if (!plan_product_view(plan, MLFMA_FP32, nullptr, nullptr, &dev, &maxb, &n))
+        return fail(MLFMA_EINVAL, "cm_block_solve needs a device plan with FP32 products");
+    const int p = o.ncv, k = o.nev;
+    if (k < 1 || p < k || p > n || p > maxb) return fail(MLFMA_EINVAL, "need 1 <= nev <= ncv <= min(N, max_batch)");
+    if (o.op != MLFMA_CM_XINV_R) return fail(MLFMA_EINVAL, "the block solver works on X^-1 R (MLFMA_CM_XINV_R)");
+    if (o.prec != MLFMA_FP32 && o.prec != MLFMA_FP64) return fail(MLFMA_EINVAL, "unknown precision");
+    if (!(o.gmres_tol > 0) || !(o.tol > 0) || o.gmres_restart < 1 || o.max_inner < 1 || o.max_restarts < 1)
+        return fail(MLFMA_EINVAL, "bad tolerance or iteration limits");
+    const bool trace = std::getenv("MLFMA_CM_TRACE") != nullptr;
+    std::vector<cd> near;
+    const PlanHost *H = nullptr;
+    if (!plan_near_host(plan, near, &H)) return fail(MLFMA_EINVAL, "plan is host-only or its near field is unreadable");
+    Sai sai;
+    if (o.use_sai && !sai.build(H, near, true))
+        return fail(MLFMA_ENOTCONV, "sparse approximate inverse: a near-field block is singular");
+    near.clear();
+    near.shrink_to_fit();
+    std::string err;
+    std::unique_ptr<BlockGmres, void (*)(BlockGmres *)> bg(
+        block_gmres_create(plan, o.use_sai ? sai.vals.data() : nullptr, o.gmres_restart, p, err), block_gmres_destroy);
+    if (!bg) return fail(MLFMA_ECUDA, err);
+
+    const size_t np = (size_t)n * p;
+    int64_t nprod = 0, inner = 0;
+    std::vector<float> xf, yf;
+    std::vector<double> yd;
+    // X Y = Im(Zp Y), R Y = -Re(Zp Y) for the p real columns of Y (one product)
+    auto products = [&](const std::vector<double> &Yb, std::vector<double> &XY, std::vector<double> &RY) {
+        mlfma_status st;
+        if (o.prec == MLFMA_FP32) {
+            xf.resize(np);
+            yf.resize(2 * np);
+            for (size_t e = 0; e < np; ++e) xf[e] = (float)Yb[e];
+            if ((st = mlfma_matvec_host(plan, xf.data(), 0, yf.data(), p, MLFMA_FP32, nullptr))) return st;
+            for (size_t e = 0; e < np; ++e) {
+                XY[e] = yf[2 * e + 1];
+                RY[e] = -(double)yf[2 * e];
+            }
+        } else {
+            yd.resize(2 * np);
+            if ((st = mlfma_matvec_host(plan, Yb.data(), 0, yd.data(), p, MLFMA_FP64, nullptr))) return st;
+            for (size_t e = 0; e < np; ++e) {
+                XY[e] = yd[2 * e + 1];
+                RY[e] = -yd[2 * e];
+            }
+        }
+        ++nprod;
+        return MLFMA_OK;
+    };
+    auto normalise_columns = [&](std::vector<double> &Yb) {
+        std::vector<double> nn(p, 0.0);
+        for (size_t e = 0; e < np; ++e) nn[e % p] += Yb[e] * Yb[e];
+        for (int c = 0; c < p; ++c) nn[c] = nn[c] > 0 ? 1 / std::sqrt(nn[c]) : 0.0;
+        for (size_t e = 0; e < np; ++e) Yb[e] *= nn[e % p];
+    };
+    std::mt19937_64 rng(o.seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    std::vector<double> Y(np), XY(np), RY(np), W(np), Yn(np), mu, coef, relres(p);
+    for (auto &v : Y) v = nd(rng);
+    normalise_columns(Y);
+    mlfma_status st;
+    if ((st = products(Y, XY, RY))) return st;
+    std::vector<int> conv(p), order(p);
+    for (int c = 0; c < p; ++c) order[c] = c;
+    std::vector<double> lam(p, INFINITY), res(p, INFINITY);
+    bool converged = false, inner_ok = true;
+    int iters = 0;
+    while (iters < o.max_restarts) {
+        ++iters;
+        // initial guess X^-1 R y = y / lambda for the columns that hold
+        // Ritz pairs with residual below 0.1 (zero elsewhere and on the first
+        // iteration): it carries the large components along the wanted
+        // modes, the near-null vectors of X that GMRES resolves last; for a
+        // poor pair the guess's own residual (X y - lambda R y) / lambda
+        // would exceed that of zero
+        for (int64_t q = 0; q < n; ++q)
+            for (int c = 0; c < p; ++c) {
+                const size_t e = (size_t)q * p + c;
+                W[e] = std::isfinite(lam[c]) && lam[c] != 0 && res[c] < 0.1 ? Y[e] / lam[c] : 0.0;
+            }
+        const int used = block_gmres_run(bg.get(), RY.data(), W.data(), 1, o.gmres_tol, o.max_inner, conv.data(),
+                                         relres.data(), err);
+        if (used < 0) return fail(MLFMA_ECUDA, err);
+        inner += used;
+        nprod += used;
+        for (int c = 0; c < p; ++c) inner_ok = inner_ok && conv[c];
+        const int r = ritz_shift_invert(n, p, Y.data(), RY.data(), W.data(), mu, coef);
+        if (r < 1) return fail(MLFMA_ENOTCONV, "block solver: the block lost all R energy");
+        // next block: the r improved Ritz vectors W coef, random directions
+        // in the columns the block lost; one product gives X Y' and R Y'
+        right_multiply(n, p, r, W.data(), coef, XY.data());   // XY as scratch [n][r]
+        for (int64_t q = 0; q < n; ++q)
+            for (int c = 0; c < p; ++c) Yn[(size_t)q * p + c] = c < r ? XY[(size_t)q * r + c] : nd(rng);
+        normalise_columns(Yn);
+        Y.swap(Yn);
+        if ((st = products(Y, XY, RY))) return st;
+        // Rayleigh quotients lambda = y^T X y / y^T R y and residuals
+        // ||X y - lambda R y|| / (||X y|| + |lambda| ||R y||) of the columns
+        std::vector<double> yx(p, 0.0), yr(p, 0.0), xx(p, 0.0), rr2(p, 0.0), xr(p, 0.0);
+        for (int64_t q = 0; q < n; ++q)
+            for (int c = 0; c < p; ++c) {
+                const size_t e = (size_t)q * p + c;
+                yx[c] += Y[e] * XY[e];
+                yr[c] += Y[e] * RY[e];
+                xx[c] += XY[e] * XY[e];
+                rr2[c] += RY[e] * RY[e];
+                xr[c] += XY[e] * RY[e];
+            }
+        for (int c = 0; c < p; ++c) {
+            lam[c] = c < r && yr[c] > 0 ? yx[c] / yr[c] : INFINITY;
+            if (!std::isfinite(lam[c])) {
+                res[c] = INFINITY;
+                continue;
+            }
+            const double d2 = xx[c] - 2 * lam[c] * xr[c] + lam[c] * lam[c] * rr2[c];
+            res[c] = std::sqrt(std::max(0.0, d2)) / (std::sqrt(xx[c]) + std::abs(lam[c]) * std::sqrt(rr2[c]) + 1e-300);
+        }
+        // the nev pairs nearest zero (Ritz order is |mu| order; the
+        // quotients can swap neighbours)
+        for (int c = 0; c < p; ++c) order[c] = c;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return std::abs(lam[x]) < std::abs(lam[y]); });
+        converged = r >= k;
+        double worst = 0, worst_inner = 0;
+        for (int i = 0; i < k; ++i) {
+            worst = std::max(worst, res[order[i]]);
+            if (!(res[order[i]] <= o.tol)) converged = false;
+        }
+        for (int c = 0; c < p; ++c) worst_inner = std::max(worst_inner, relres[c]);
+        if (trace)
+            std::fprintf(stderr, "cm_block_solve: iteration %d  GMRES steps %d  max inner residual %.2e  rank %d  "
+                         "max residual of the %d wanted %.2e  lambda_1 %.8g  %.1f s\n", iters, used, worst_inner, r, k,
+                         worst, lam[order[0]], std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+        if (converged) break;
+    }
+    for (int i = 0; i < k; ++i) lambda[i] = std::isfinite(lam[order[i]]) ? lam[order[i]] : std::nan("");
+    if (J) {
+        for (int i = 0; i < k; ++i) {
+            const int c = order[i];
+            double nn = 0, big = 0;
+            for (int64_t q = 0; q < n; ++q) {
+                const double v = Y[(size_t)q * p + c];
+                nn += v * v;
+                if (std::abs(v) > std::abs(big)) big = v;
+            }
+            const double f = nn > 0 ? (big < 0 ? -1.0 : 1.0) / std::sqrt(nn) : 0.0;   // unit norm, largest entry > 0
+            for (int64_t q = 0; q < n; ++q) J[q * k + i] = f * Y[(size_t)q * p + c];
+        }
+    }
+    if (stats) {
+        stats->restarts = iters;
+        stats->inner_iterations = inner;
+        stats->products = nprod;
+        stats->converged = converged ? 1 : 0;
+        stats->inner_converged = inner_ok ? 1 : 0;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!converged) return fail(MLFMA_ENOTCONV, "block subspace iteration did not converge within max_restarts");
+    return MLFMA_OK;
+}
+
 // ----------------------------------------- characteristic-value slopes ---
-namespace mlfma {
-template <class R> struct ProductArgs;
-bool plan_product_view(mlfma_plan_t p, int prec, ProductArgs<float> *a32, ProductArgs<double> *a64, int *device,
-                       int *max_batch, int64_t *n);
-}  // namespace mlfma
 
 // d lambda / dk of characteristic pairs (Section II, Eq. (GEP), with the
 // pencil's k-derivative): for X J = lambda R J with R = -Re Z, X = Im Z and

@@ -25,4 +25,24 @@ void device_gmres_destroy(DeviceGmres *g);
 int device_gmres_run(DeviceGmres *g, int mode, const std::complex<double> *r, std::complex<double> *d,
                      double target, int maxit, std::string &err);
 
+// Block variant for real systems with X = Im Z: the p columns of B advance
+// together through one product of p real columns per step, each with its
+// own basis and least-squares problem (GMRES restarted every `restart`
+// steps, right-preconditioned by the real part of sai, nullptr for none).
+class BlockGmres;
+BlockGmres *block_gmres_create(mlfma_plan_t p, const std::complex<double> *sai, int restart, int cols,
+                               std::string &err);
+void block_gmres_destroy(BlockGmres *g);
+
+// X D = B for host blocks B, D [n][cols] (canonical order, row-major) in FP32
+// arithmetic with FP64 inner products, starting from D itself when guess is
+// non-zero (else from 0), until every column's residual is <= tol ||b_c||
+// or maxit steps were spent; conv[c] = 1 for columns that
+// got there; relres[c] (may be nullptr) receives each column's final
+// ||b - X d|| / ||b||.  Returns the steps used (one product of cols columns
+// each, plus one per restart for the true residual), or -1 on failure (err
+// set).
+int block_gmres_run(BlockGmres *g, const double *B, double *D, int guess, double tol, int maxit, int *conv,
+                    double *relres, std::string &err);
+
 }  // namespace mlfma

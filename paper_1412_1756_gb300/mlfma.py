@@ -25,7 +25,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIM
 EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg_edges", "mlfma_matvec",
             "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint", "mlfma_matvec_x",
             "mlfma_matvec_r", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
-            "mlfma_profile_stages", "mlfma_export_field", "mlfma_tune", "mlfma_tune_get", "mlfma_tune_set", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve",
+            "mlfma_profile_stages", "mlfma_export_field", "mlfma_tune", "mlfma_tune_get", "mlfma_tune_set", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve", "cm_block_solve", "cm_rayleigh_ritz",
             "cm_eig_derivatives",
             "mlfma_set_create", "mlfma_set_matvec", "mlfma_set_info", "mlfma_set_plan", "mlfma_set_destroy",
             "mlfma_destroy", "mlfma_last_error"]
@@ -102,6 +102,8 @@ def load(build_if_missing: bool = False):
     L.mlfma_tune_set.argtypes = [P, I64, I, I, P]
     L.mlfma_cm_default_opts.argtypes = [ctypes.POINTER(CmOpts)]
     L.cm_ira_solve.argtypes = [P, ctypes.POINTER(CmOpts), P, P, ctypes.POINTER(CmStats)]
+    L.cm_block_solve.argtypes = [P, ctypes.POINTER(CmOpts), P, P, ctypes.POINTER(CmStats)]
+    L.cm_rayleigh_ritz.argtypes = [I64, I, P, P, P, P, P, ctypes.POINTER(I)]
     L.cm_eig_derivatives.argtypes = [P, I, P, P, I, P]
     L.mlfma_plan_info.argtypes = [P, ctypes.POINTER(Info)]
     L.mlfma_export.argtypes = [P, I, I, P, I64, ctypes.POINTER(I64)]
@@ -392,6 +394,29 @@ class MlfmaPlan:
             raise err
         return lam, J, stats
 
+    def cm_block_solve(self, nev=10, block=32, prec=FP32, tol=1e-5, gmres_tol=1e-6, gmres_restart=200,
+                       max_inner=2000, max_iters=50, use_sai=True, seed=1412175602, vectors=True):
+        """Characteristic values nearest zero (and real currents) by block
+        shift-invert subspace iteration on X^-1 R (include/mlfma.h:
+        cm_block_solve): returns (lambda [nev], J [N, nev] or None, stats)."""
+        o = CmOpts()
+        _check(self._lib.mlfma_cm_default_opts(ctypes.byref(o)))
+        o.nev, o.ncv, o.op, o.prec = int(nev), int(block), CM_XINV_R, int(prec)
+        o.tol, o.gmres_tol = float(tol), float(gmres_tol)
+        o.gmres_restart, o.max_inner, o.max_restarts = int(gmres_restart), int(max_inner), int(max_iters)
+        o.use_sai, o.seed = 1 if use_sai else 0, int(seed)
+        lam = np.zeros(nev)
+        J = np.zeros((self.n, nev)) if vectors else None
+        st = CmStats()
+        rc = self._lib.cm_block_solve(self._h, ctypes.byref(o), _np_ptr(lam), _np_ptr(J) if vectors else None,
+                                      ctypes.byref(st))
+        stats = {f: getattr(st, f) for f, _ in CmStats._fields_}
+        if rc != 0:
+            err = MlfmaError(rc, self._lib.mlfma_last_error().decode())
+            err.stats, err.values = stats, lam
+            raise err
+        return lam, J, stats
+
     def cm_derivatives(self, lam, J, prec=FP64) -> np.ndarray:
         """d lambda / dk of characteristic pairs (include/mlfma.h: cm_eig_derivatives)."""
         lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(-1)
@@ -415,6 +440,22 @@ class MlfmaPlan:
             self.close()
         except Exception:
             pass
+
+
+def rayleigh_ritz(Y, RY, W):
+    """Ritz pairs of T = X^-1 R on span Y in the R inner product from Y,
+    R Y and W = T Y (include/mlfma.h: cm_rayleigh_ritz; host only): returns
+    (mu [r] sorted by |mu|, largest first, lambda = 1 / mu; coef [p, r] with
+    Ritz vectors Y coef)."""
+    L = load()
+    Y, RY, W = (np.ascontiguousarray(a, dtype=np.float64) for a in (Y, RY, W))
+    if Y.ndim != 2 or Y.shape != RY.shape or Y.shape != W.shape:
+        raise ValueError("Y, RY and W must be [n, p] arrays of one shape")
+    n, p = Y.shape
+    mu, coef, r = np.zeros(p), np.zeros((p, p)), ctypes.c_int(0)
+    _check(L.cm_rayleigh_ritz(n, p, _np_ptr(Y), _np_ptr(RY), _np_ptr(W), _np_ptr(mu), _np_ptr(coef),
+                              ctypes.byref(r)))
+    return mu[:r.value], coef[:, :r.value]
 
 
 def tune_cache_key(gpu_name, info, interp_order, B, prec, complex_x) -> str:
