@@ -381,7 +381,7 @@ mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opts, double *
  * |lambda_(p+1)| per iteration.  opts->max_restarts bounds the iterations.
  * Needs a device plan with FP32 (and FP64 for prec = MLFMA_FP64).  With the
  * environment variable MLFMA_CM_TRACE set, one line per iteration goes to
- * stderr.
+ * stderr (MLFMA_CM_TRACE=2: also one per wanted column).
  *  lambda  host [nev], sorted by |lambda|
  *  J       host [N][nev] real currents, unit 2-norm, largest entry positive;
  *          may be NULL

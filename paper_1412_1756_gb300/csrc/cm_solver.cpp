@@ -922,7 +922,7 @@ extern "C" mlfma_status cm_rayleigh_ritz(int64_t n, int p, const double *Y, cons
 // cannot resolve; errors of the inexact solves along near-null vectors of X
 // (interior resonances: currents that do not radiate) are filtered by R.
 // With MLFMA_CM_TRACE set in the environment, one line per iteration goes to
-// stderr.
+// stderr (MLFMA_CM_TRACE=2: also one per wanted column).
 extern "C" mlfma_status cm_block_solve(mlfma_plan_t plan, const mlfma_cm_opts *opts, double *lambda, double *J,
                                        mlfma_cm_stats *stats)
 {
@@ -939,7 +939,8 @@ extern "C" mlfma_status cm_block_solve(mlfma_plan_t plan, const mlfma_cm_opts *o
     if (o.prec != MLFMA_FP32 && o.prec != MLFMA_FP64) return fail(MLFMA_EINVAL, "unknown precision");
     if (!(o.gmres_tol > 0) || !(o.tol > 0) || o.gmres_restart < 1 || o.max_inner < 1 || o.max_restarts < 1)
         return fail(MLFMA_EINVAL, "bad tolerance or iteration limits");
-    const bool trace = std::getenv("MLFMA_CM_TRACE") != nullptr;
+    const char *trace_env = std::getenv("MLFMA_CM_TRACE");
+    const int trace = trace_env ? std::max(1, std::atoi(trace_env)) : 0;   // 2: every column as well
     std::vector<cd> near;
     const PlanHost *H = nullptr;
     if (!plan_near_host(plan, near, &H)) return fail(MLFMA_EINVAL, "plan is host-only or its near field is unreadable");
@@ -1048,10 +1049,14 @@ extern "C" mlfma_status cm_block_solve(mlfma_plan_t plan, const mlfma_cm_opts *o
             const double d2 = xx[c] - 2 * lam[c] * xr[c] + lam[c] * lam[c] * rr2[c];
             res[c] = std::sqrt(std::max(0.0, d2)) / (std::sqrt(xx[c]) + std::abs(lam[c]) * std::sqrt(rr2[c]) + 1e-300);
         }
-        // the nev pairs nearest zero (Ritz order is |mu| order; the
-        // quotients can swap neighbours)
+        // the wanted pairs are the first nev columns: Ritz order, largest
+        // |mu| first.  Interlacing makes that order safe; the Rayleigh
+        // quotient of an unconverged vector under an indefinite X is not
+        // (the block's last columns can have quotients near zero), so it
+        // reports values but does not select them.  Output in |lambda| order.
         for (int c = 0; c < p; ++c) order[c] = c;
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return std::abs(lam[x]) < std::abs(lam[y]); });
+        std::stable_sort(order.begin(), order.begin() + std::min(k, p),
+                         [&](int x, int y) { return std::abs(lam[x]) < std::abs(lam[y]); });
         converged = r >= k;
         double worst = 0, worst_inner = 0;
         for (int i = 0; i < k; ++i) {
@@ -1063,6 +1068,12 @@ extern "C" mlfma_status cm_block_solve(mlfma_plan_t plan, const mlfma_cm_opts *o
             std::fprintf(stderr, "cm_block_solve: iteration %d  GMRES steps %d  max inner residual %.2e  rank %d  "
                          "max residual of the %d wanted %.2e  lambda_1 %.8g  %.1f s\n", iters, used, worst_inner, r, k,
                          worst, lam[order[0]], std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+        if (trace >= 2)
+            for (int i = 0; i < std::min(p, k + 6); ++i) {
+                const int c = order[i];
+                std::fprintf(stderr, "  column %2d  Rayleigh quotient %+.8f  Ritz 1/mu %+.8f  residual %.2e  inner %.2e\n",
+                             c, lam[c], c < r ? 1.0 / mu[c] : INFINITY, res[c], relres[c]);
+            }
         if (converged) break;
     }
     for (int i = 0; i < k; ++i) lambda[i] = std::isfinite(lam[order[i]]) ? lam[order[i]] : std::nan("");
