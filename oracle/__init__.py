@@ -10,7 +10,9 @@ Modules
 - ``efie``    ctypes driver for ``efie_oracle.c``: dense symmetric Z, selected
               rows of Z, inner potential integrals (Section II, Eqs. (1)-(5)).
 - ``cm``      dense characteristic-mode eigensolve of X J = lambda R J
-              (Section II, Eq. (GEP)) with R = -Re Z and X = Im Z.
+              (Section II, Eq. (GEP)) with R = -Re Z and X = Im Z: QZ, LU +
+              Arnoldi, or (large N) the reduction to the symmetric L^T X^-1 L
+              with R = L L^T; eigenvalue slopes d lambda / dk.
 - ``build``   compiles ``efie_oracle.c`` with gcc + OpenMP.
 
 Parity status: every function here is pinned by a CPU test against

@@ -46,6 +46,32 @@ def cm_values_arnoldi(Z: np.ndarray, nev: int = 10, seed: int = 0) -> np.ndarray
     return lam[np.argsort(np.abs(lam))]
 
 
+def cm_values_symmetric(R: np.ndarray, X: np.ndarray, nev: int = 10, overwrite: bool = False) -> np.ndarray:
+    """Same selection as ``cm_values`` for large N, by reducing the pencil of
+    Eq. (GEP) to one dense symmetric eigenproblem (no iteration).
+
+    R is symmetric positive semidefinite, so R = L L^T with L = U D^1/2 from
+    its eigendecomposition R = U D U^T (rounding-level negative D taken as
+    0).  For mu != 0, X^-1 R J = mu J holds exactly when L^T X^-1 L u = mu u
+    with u = L^T J / mu: the nonzero eigenvalues mu = 1 / lambda of X^-1 R
+    are those of the symmetric matrix M = L^T X^-1 L, and the zero ones
+    (the null space of R, lambda infinite) are not wanted.  Returns the nev
+    values nearest zero (largest |mu|), sorted by magnitude.  With
+    overwrite, R and X are used as work space."""
+    d, U = scipy.linalg.eigh(R, overwrite_a=overwrite, check_finite=False)
+    del R
+    U *= np.sqrt(np.clip(d, 0.0, None))[None, :]            # L, in place
+    lu = scipy.linalg.lu_factor(X, overwrite_a=overwrite, check_finite=False)
+    del X
+    M = U.T @ scipy.linalg.lu_solve(lu, U, check_finite=False)
+    del lu, U
+    M = 0.5 * (M + M.T)
+    mu = scipy.linalg.eigh(M, eigvals_only=True, overwrite_a=True, check_finite=False)
+    mu = mu[np.argsort(-np.abs(mu))[:nev]]
+    lam = 1.0 / mu
+    return lam[np.argsort(np.abs(lam))]
+
+
 def cm_derivatives(Z: np.ndarray, dZ: np.ndarray, nev: int = 10, method: str = "dense", seed: int = 0):
     """Characteristic values nearest zero and their wavenumber derivatives.
 

@@ -19,6 +19,7 @@ import os
 
 import numpy as np
 import pytest
+import scipy.linalg
 from scipy.special import spherical_jn, spherical_yn
 
 import workloads
@@ -224,6 +225,32 @@ def test_sphere_cm_values_coarse(small_sphere):
     assert np.all(np.abs(lam - ref) < 0.12 * np.abs(ref)), (lam, ref)
     lam2 = cm.cm_values_arnoldi(Z, 15)
     assert np.allclose(np.sort(lam2), np.sort(lam), rtol=1e-8)
+
+
+def test_symmetric_reduction_equals_qz(small_sphere):
+    """cm_values_symmetric (R = L L^T, eigenvalues of L^T X^-1 L) selects
+    the same values as the QZ route of cm_values on the sphere pencil."""
+    _, Z = small_sphere
+    lam = cm.cm_values_symmetric(-Z.real, Z.imag.copy(), 15)
+    assert np.allclose(lam, cm.cm_values(Z, 15), rtol=1e-8)
+
+
+def test_symmetric_reduction_random_semidefinite_pencil():
+    """A random pencil with R of rank n - 3 (three infinite values) and X
+    indefinite: the reduction equals the finite generalized eigenvalues
+    nearest zero from a general eigensolver."""
+    rng = np.random.default_rng(7)
+    n = 70
+    A = rng.standard_normal((n, n))
+    X = A + A.T
+    Bf = rng.standard_normal((n, n - 3))
+    R = Bf @ Bf.T
+    mu = scipy.linalg.eigvals(R, X)
+    mu = mu[np.isfinite(mu)].real
+    lam_ref = 1.0 / mu[np.argsort(-np.abs(mu))[:12]]
+    lam_ref = lam_ref[np.argsort(np.abs(lam_ref))]
+    lam = cm.cm_values_symmetric(R.copy(), X.copy(), 12, overwrite=True)
+    assert np.allclose(lam, lam_ref, rtol=1e-7)
 
 
 @pytest.mark.slow
