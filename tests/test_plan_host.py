@@ -4,6 +4,7 @@ addition theorem (Section III-A, Eqs. (7)-(8)) and the E1 point test of
 Section V, and against exactness properties of the interpolation and
 anterpolation (Section III-C)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -227,3 +228,21 @@ def test_tune_cache_key_and_file(tmp_path):
     with open(path, "w") as f:
         f.write("{not json")
     assert M._read_tune_cache(path) == {}
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/mlfma.h is a C ABI: it compiles as strict C99 (no C++ in the
+    declarations) and as C++."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "mlfma.h"\nint main(void) { mlfma_cm_opts o; mlfma_info i; (void)o; (void)i; '
+                   'return (int)sizeof(&cm_block_solve) == 0; }\n')
+    for cmd in ([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                [gcc, "-x", "c++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)]):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
