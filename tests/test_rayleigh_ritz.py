@@ -86,3 +86,21 @@ def test_rank_loss_and_null_energy_are_dropped():
 def test_bad_arguments():
     with pytest.raises(ValueError):
         M.rayleigh_ritz(np.zeros((5, 2)), np.zeros((5, 3)), np.zeros((5, 2)))
+
+
+def test_degenerate_cluster_is_returned_whole():
+    """A 5-fold and a 3-fold eigenvalue of the pencil (the shape of the
+    sphere's clusters): a basis of their joint invariant subspace gives both
+    values with their multiplicities, and R-orthonormal Ritz vectors."""
+    rng = np.random.default_rng(9)
+    n = 50
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([[0.056] * 5, [-0.077] * 3, rng.uniform(0.5, 3.0, n - 8) * rng.choice([-1, 1], n - 8)])
+    d = rng.uniform(0.5, 2.0, n)                       # R = Q diag(d) Q^T, X = Q diag(lam d) Q^T
+    R = (Q * d) @ Q.T
+    X = (Q * (lam * d)) @ Q.T
+    Y, RY, W = ritz_inputs(X, R, Q[:, :8] @ rng.standard_normal((8, 8)))
+    mu, coef = M.rayleigh_ritz(Y, RY, W)
+    assert np.allclose(np.sort(1.0 / mu), np.sort(lam[:8]), rtol=1e-9)
+    Z = Y @ coef
+    assert np.allclose(Z.T @ R @ Z, np.eye(8), atol=1e-9)
