@@ -267,23 +267,26 @@ mlfma_status mlfma_profile_stages(mlfma_plan_t plan, const void *x, int x_is_com
 /*
  * y = Z x without allocating anything.  The paper has no counterpart: this
  * is a service for callers that cannot call cudaMalloc at the moment they
- * need a product - code running while a CUDA stream capture is open on the
- * thread (the runtime forbids allocation then), code whose device memory is
- * entirely reserved by another allocator, and real-time loops that must not
- * allocate.  It runs the same kernels as mlfma_matvec, in order on `stream`,
+ * need a product - code whose device memory is entirely reserved by another
+ * allocator (a framework's caching pool holding the whole GPU), and
+ * real-time loops that must not allocate or wait on the allocator.  It runs
+ * the same kernels as mlfma_matvec, with the launch shapes mlfma_matvec uses
+ * for the same columns (built-in, tuned or pinned), in order on `stream`,
  * but takes every per-call buffer (leaf-order columns, each level's outgoing
  * and incoming fields) from one static device array of
  * MLFMA_NOALLOC_SCRATCH_BYTES inside this library instead of the plan's own
- * buffers, and captures no graph.  The caller still passes x and y, with
- * the layouts and types of mlfma_matvec; the plan's tables must already
- * exist (mlfma_plan allocates them once, earlier).
+ * buffers.  The caller still passes x and y, with the layouts and types of
+ * mlfma_matvec (x and y must not share a byte: MLFMA_EINVAL); the plan's
+ * tables must already exist (mlfma_plan allocates them once, earlier).
  *
  * - A product needing more scratch than the array holds (columns x fields
  *   of all levels) is refused with MLFMA_EINVAL and a message giving the
  *   bytes needed; so is B > max_batch.
  * - The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture begins.
+ *   (cudaGetSymbolAddress) with that device current and keeps it for the
+ *   life of the process; make that first call before any stream capture
+ *   begins, and do not call this entry point across a cudaDeviceReset of
+ *   the device (the kept address belongs to the old context).
  * - Every call, on every plan, shares the one array and leaves its contents
  *   behind.  Nothing in it needs to start at zero: each pass writes every
  *   scratch value before reading it.  Calls whose work overlaps on the GPU

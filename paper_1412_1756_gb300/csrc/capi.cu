@@ -832,12 +832,16 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
 {
     const int dk = kind == KIND_DK;
     if (check_plan(p)) return MLFMA_EINVAL;
-    if (!p->on_device) return fail(MLFMA_EINVAL, "plan was built host-only; products need a device plan");
     if (!x || !y) return fail(MLFMA_EINVAL, "x or y is NULL");
-    if (x == y) return fail(MLFMA_EINVAL, "x and y must not overlap");
     if (B < 1) return fail(MLFMA_EINVAL, "B must be >= 1");
     const int64_t Bi = B * (xc ? 2 : 1);
     if (Bi > p->opts.max_batch) return fail(MLFMA_EINVAL, "B exceeds the plan's max_batch");
+    {
+        const int64_t rsz = prec == MLFMA_FP64 ? 8 : 4;
+        if (byte_ranges_overlap(x, p->host.N * Bi * rsz, y, p->host.N * B * 2 * rsz))
+            return fail(MLFMA_EINVAL, "x and y must not overlap");
+    }
+    if (!p->on_device) return fail(MLFMA_EINVAL, "plan was built host-only; products need a device plan");
     if (dk && 2 * Bi > p->opts.max_batch)
         return fail(MLFMA_EINVAL, "dZ/dk products carry value and tangent fields: 2 x B (x2 for complex x) must not "
                                   "exceed the plan's max_batch");
@@ -898,15 +902,23 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
 
 namespace mlfma {
 // Read-only view of a device plan's product arguments for entry points
-// defined in other translation units.
-bool plan_product_view(mlfma_plan_t p, int prec, ProductArgs<float> *a32, ProductArgs<double> *a64, int *device,
-                       int *max_batch, int64_t *n)
+// defined in other translation units.  With Bi >= 1 the view carries the
+// launch shapes mlfma_matvec uses for Bi internal columns (tuned or pinned,
+// else built-in); Bi = 0 gives the built-in shapes.
+bool plan_product_view(mlfma_plan_t p, int prec, int64_t Bi, ProductArgs<float> *a32, ProductArgs<double> *a64,
+                       int *device, int *max_batch, int64_t *n)
 {
     if (!p || !p->on_device) return false;
     if (prec == MLFMA_FP32 && !p->has32) return false;
     if (prec == MLFMA_FP64 && !p->has64) return false;
     if (prec == MLFMA_FP32 && a32) *a32 = p->a32;
     if (prec == MLFMA_FP64 && a64) *a64 = p->a64;
+    // the launch shapes mlfma_matvec uses for these columns (tuned or pinned)
+    auto t = p->tunes.find(std::make_pair(prec, (int)Bi));
+    if (t != p->tunes.end()) {
+        if (prec == MLFMA_FP32 && a32) a32->tune = t->second;
+        if (prec == MLFMA_FP64 && a64) a64->tune = t->second;
+    }
     *device = p->device;
     *max_batch = p->opts.max_batch;
     *n = p->host.N;

@@ -37,7 +37,7 @@ namespace mlfma {
 template <class R> struct ProductArgs;
 bool plan_near_host(mlfma_plan_t p, std::vector<std::complex<double>> &vals, const PlanHost **host);
 void set_last_error(const std::string &msg);
-bool plan_product_view(mlfma_plan_t p, int prec, ProductArgs<float> *a32, ProductArgs<double> *a64, int *device,
+bool plan_product_view(mlfma_plan_t p, int prec, int64_t Bi, ProductArgs<float> *a32, ProductArgs<double> *a64, int *device,
                        int *max_batch, int64_t *n);
 }  // namespace mlfma
 
@@ -931,7 +931,7 @@ extern "C" mlfma_status cm_block_solve(mlfma_plan_t plan, const mlfma_cm_opts *o
     const mlfma_cm_opts o = *opts;
     int dev = 0, maxb = 0;
     int64_t n = 0;
-    if (!plan_product_view(plan, MLFMA_FP32, nullptr, nullptr, &dev, &maxb, &n))
+    if (!plan_product_view(plan, MLFMA_FP32, 0, nullptr, nullptr, &dev, &maxb, &n))
         return fail(MLFMA_EINVAL, "cm_block_solve needs a device plan with FP32 products");
     const int p = o.ncv, k = o.nev;
     if (k < 1 || p < k || p > n || p > maxb) return fail(MLFMA_EINVAL, "need 1 <= nev <= ncv <= min(N, max_batch)");
@@ -1116,7 +1116,7 @@ extern "C" mlfma_status cm_eig_derivatives(mlfma_plan_t plan, int nev, const dou
     if (!plan || !lambda || !J || !dlambda || nev < 1) return fail(MLFMA_EINVAL, "NULL argument or nev < 1");
     int dev = 0, max_batch = 0;
     int64_t n = 0;
-    if (!plan_product_view(plan, prec, nullptr, nullptr, &dev, &max_batch, &n))
+    if (!plan_product_view(plan, prec, 0, nullptr, nullptr, &dev, &max_batch, &n))
         return fail(MLFMA_EINVAL, "plan is host-only or the precision is not set up");
     const int chunk = std::max(1, max_batch / 2);
     const size_t rsz = prec == MLFMA_FP64 ? 8 : 4;

@@ -6,6 +6,13 @@
 
 namespace mlfma {
 
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte.
+inline bool byte_ranges_overlap(const void *a, int64_t na, const void *b, int64_t nb)
+{
+    const uintptr_t pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+    return na > 0 && nb > 0 && pa < pb + (uintptr_t)nb && pb < pa + (uintptr_t)na;
+}
+
 // Mesh and RWG data used by the FP64 setup kernels (leaf order for RWGs).
 struct DevMesh {
     int nt = 0;

@@ -15,7 +15,7 @@
 #include <vector>
 
 namespace mlfma {
-bool plan_product_view(mlfma_plan_t p, int prec, ProductArgs<float> *a32, ProductArgs<double> *a64, int *device,
+bool plan_product_view(mlfma_plan_t p, int prec, int64_t Bi, ProductArgs<float> *a32, ProductArgs<double> *a64, int *device,
                        int *max_batch, int64_t *n);
 const PlanHost *plan_host(mlfma_plan_t p);
 
@@ -207,7 +207,7 @@ DeviceGmres *device_gmres_create(mlfma_plan_t p, const std::complex<double> *sai
     ProductArgs<float> a32;
     int dev = 0, maxb = 0;
     int64_t n = 0;
-    if (!plan_product_view(p, MLFMA_FP32, &a32, nullptr, &dev, &maxb, &n)) {
+    if (!plan_product_view(p, MLFMA_FP32, 0, &a32, nullptr, &dev, &maxb, &n)) {
         err = "device GMRES needs a device plan with FP32 set up";
         return nullptr;
     }

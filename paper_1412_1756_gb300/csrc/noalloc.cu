@@ -10,8 +10,8 @@
 #include <string>
 
 namespace mlfma {
-bool plan_product_view(mlfma_plan_t p, int prec, ProductArgs<float> *a32, ProductArgs<double> *a64, int *device,
-                       int *max_batch, int64_t *n);
+bool plan_product_view(mlfma_plan_t p, int prec, int64_t Bi, ProductArgs<float> *a32, ProductArgs<double> *a64,
+                       int *device, int *max_batch, int64_t *n);
 void set_last_error(const std::string &msg);
 }  // namespace mlfma
 
@@ -31,7 +31,9 @@ std::mutex g_addr_mutex;
 void *g_addr[kMaxDevices] = {};
 
 // Device address of the static scratch on `dev` (which must be current),
-// looked up once per device.
+// looked up once per device and kept for the life of the process: after a
+// cudaDeviceReset of that device (a new primary context) the kept address is
+// stale, so the entry point must not be called across a reset.
 cudaError_t scratch_address(int dev, void **out)
 {
     std::lock_guard<std::mutex> lock(g_addr_mutex);
@@ -102,16 +104,19 @@ extern "C" mlfma_status mlfma_matvec_noalloc(mlfma_plan_t plan, const void *x, i
 {
     if (!plan) return fail(MLFMA_EINVAL, "plan is NULL");
     if (!x || !y) return fail(MLFMA_EINVAL, "x or y is NULL");
-    if (x == y) return fail(MLFMA_EINVAL, "x and y must not overlap");
     if (B < 1) return fail(MLFMA_EINVAL, "B must be >= 1");
     if (prec != MLFMA_FP32 && prec != MLFMA_FP64) return fail(MLFMA_EINVAL, "unknown precision");
     ProductArgs<float> a32;
     ProductArgs<double> a64;
     int dev = -1, max_batch = 0;
     int64_t n = 0;
-    if (!plan_product_view(plan, prec, &a32, &a64, &dev, &max_batch, &n))
-        return fail(MLFMA_EINVAL, "plan is host-only or lacks this precision");
     const int64_t Bi = B * (x_is_complex ? 2 : 1);
+    if (mlfma_num_unknowns(plan, &n) != MLFMA_OK) return MLFMA_EINVAL;
+    const int64_t rsz = prec == MLFMA_FP64 ? 8 : 4;
+    if (byte_ranges_overlap(x, n * Bi * rsz, y, n * B * 2 * rsz))
+        return fail(MLFMA_EINVAL, "x and y must not overlap");
+    if (!plan_product_view(plan, prec, Bi, &a32, &a64, &dev, &max_batch, &n))
+        return fail(MLFMA_EINVAL, "plan is host-only or lacks this precision");
     if (Bi > max_batch) return fail(MLFMA_EINVAL, "B exceeds the plan's max_batch");
     if (dev < 0 || dev >= kMaxDevices) return fail(MLFMA_EINVAL, "device ordinal out of range");
     int prev = -1;

@@ -43,248 +43,281 @@ __device__ __forceinline__ P3 crossp(P3 a, P3 b)
 }
 __device__ __forceinline__ double lenp(P3 a) { return sqrt(dotp(a, a)); }
 
-struct Z1 {   // complex scalar
-    double re, im;
-};
-struct Z3 {   // complex 3-vector
+struct Z3 {   // complex 3-vector (real and imaginary parts)
     P3 re, im;
 };
 
-// ln((R+ + l+)/(R- + l-)) without cancellation: along an edge line
-// (R + l)(R - l) = R0^2.
-__device__ double edge_ln(double lp, double lm, double Rp, double Rm, double R0sq)
-{
-    if (lm >= 0.0) return log((Rp + lp) / (Rm + lm));
-    if (lp <= 0.0) return log((Rm - lm) / (Rp - lp));
-    return log((Rp + lp) * (Rm - lm) / R0sq);
-}
+// ------------------------------------------------------------ near field ---
+// The inner integral over a source triangle s, seen from an outer
+// quadrature point r, is carried as two complex quantities:
+//   psi0 = int_s g(|r - r'|) dS'          psi1 = int_s (r' - r) g(|r - r'|) dS'
+// (psi1 a complex 3-vector).  For an RWG half on s with free vertex v and
+// coefficient c = sign l / (2 A_s):  int f g = c (psi1 + (r - v) psi0) and
+// int (div f) g = 2 c psi0.
+struct SrcPot {
+    double2 s;
+    double2 v[3];
+};
 
-// int_T dS'/R and int_T (rho' - rho)/R dS' over the flat triangle v[0..2]
-// seen from r, by reduction to the three edges (in-plane divergence theorem).
-__device__ void static_terms(P3 r, const P3 *v, double &J0, P3 &J1, P3 &rho)
+// Static (1/R) potentials of the flat triangle p[0..2] at r, written in terms
+// of the distances from r to the vertices.
+//
+// With n the unit normal of p[0] p[1] p[2], h = n.(r - p[0]) and rho the foot
+// of r in the plane, the surface gradient of R = |r - r'| with respect to r'
+// is (rho' - rho) / R, and div'((rho' - rho)(R - |h|) / |rho' - rho|^2) = 1/R
+// in the plane.  The divergence and gradient theorems turn both surface
+// integrals into sums over the edges e = (a -> b), with outward in-plane
+// normal u_e = (b - a)/|b - a| x n and d_e = (a - r).u_e:
+//   int dS'/R                = sum_e d_e F_e - |h| Omega
+//   int (rho' - rho)/R dS'   = sum_e u_e int_e R dl
+// where F_e = int_e dl / R = ln((Ra + Rb + L) / (Ra + Rb - L)) with the
+// endpoint distances Ra, Rb and the edge length L, and Omega is the solid
+// angle of the triangle seen from r (van Oosterom and Strackee, IEEE TBME
+// 1983: tan(Omega/2) = A.(B x C) / (Ra Rb Rc + (A.B) Rc + (B.C) Ra +
+// (C.A) Rb), A, B, C the vertices relative to r).  Along the edge, with
+// p = (a - r).e the position of a relative to the foot of r on the edge line
+// and q the distance from r to that line,
+//   int_e R dl = ((L + p) Rb - p Ra + q^2 F_e) / 2.
+// (Ra + Rb)^2 - L^2 = 2 (Ra Rb + A.B) is formed without cancellation: for
+// A.B < 0 as 2 |A x B|^2 / (Ra Rb - A.B).  A point on the edge segment itself
+// (q = 0, where F_e diverges) contributes nothing: d_e = 0 and q = 0 there.
+// Returns int dS'/R and int (r' - r)/R dS' = int (rho' - rho)/R dS' - h n int dS'/R.
+__device__ void flat_static(P3 r, const P3 p[3], double &s0, P3 &s1)
 {
-    P3 nrm = crossp(v[1] - v[0], v[2] - v[0]);
-    nrm = (1.0 / lenp(nrm)) * nrm;
-    const double h = dotp(nrm, r - v[0]);
-    const double ah = fabs(h);
-    rho = r - h * nrm;
-    J0 = 0.0;
-    J1 = {0.0, 0.0, 0.0};
+    P3 n = crossp(p[1] - p[0], p[2] - p[0]);
+    n = (1.0 / lenp(n)) * n;
+    const double h = dotp(n, r - p[0]);
+    const P3 A[3] = {p[0] - r, p[1] - r, p[2] - r};
+    const double Rv[3] = {lenp(A[0]), lenp(A[1]), lenp(A[2])};
+    double lin = 0.0;                 // sum_e d_e F_e
+    P3 grad = {0.0, 0.0, 0.0};        // sum_e u_e int_e R dl
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        const P3 a = v[e], b = v[(e + 1) % 3];
-        const P3 ed = b - a;
-        const double el = lenp(ed);
-        const P3 s = (1.0 / el) * ed;
-        const P3 u = crossp(s, nrm);
-        const double lp = dotp(b - rho, s), lm = dotp(a - rho, s);
-        const double t = dotp(a - rho, u);
-        const double R0sq = t * t + h * h;
-        const double Rp = sqrt(R0sq + lp * lp), Rm = sqrt(R0sq + lm * lm);
-        double f = 0.0, beta = 0.0;
-        if (R0sq > 1e-28 * el * el) {
-            f = edge_ln(lp, lm, Rp, Rm, R0sq);
-            beta = atan2(t * lp, R0sq + ah * Rp) - atan2(t * lm, R0sq + ah * Rm);
-        }
-        J0 += t * f - ah * beta;
-        J1 = J1 + (0.5 * (R0sq * f + lp * Rp - lm * Rm)) * u;
+        const int b = e == 2 ? 0 : e + 1;
+        const P3 Ae = A[e], Be = A[b];
+        const double Ra = Rv[e], Rb = Rv[b];
+        const P3 ab = Be - Ae;
+        const double L = lenp(ab);
+        const P3 et = (1.0 / L) * ab;
+        const P3 ue = crossp(et, n);
+        const double dot = dotp(Ae, Be);
+        const P3 cr = crossp(Ae, Be);
+        const double cr2 = dotp(cr, cr);
+        const double Q = dot >= 0.0 ? Ra * Rb + dot : cr2 / (Ra * Rb - dot);
+        const double sum = Ra + Rb + L;
+        const double pe = dotp(Ae, et);
+        const double q2 = cr2 / (L * L);
+        double Fe = 0.0;
+        if (Q > 1e-30 * L * L) Fe = log(sum * sum / (2.0 * Q));
+        lin += dotp(Ae, ue) * Fe;
+        grad = grad + (0.5 * ((L + pe) * Rb - pe * Ra + q2 * Fe)) * ue;
     }
+    const double num = dotp(A[0], crossp(A[1], A[2]));
+    const double den = Rv[0] * Rv[1] * Rv[2] + dotp(A[0], A[1]) * Rv[2] + dotp(A[1], A[2]) * Rv[0] +
+                       dotp(A[2], A[0]) * Rv[1];
+    const double omega = fabs(2.0 * atan2(num, den));
+    s0 = lin - fabs(h) * omega;
+    s1 = grad - (h * s0) * n;
 }
 
-// P0 = int_s g dS', P1 = int_s r' g dS' at point r.
-__device__ void inner_potentials(const DevMesh &m, P3 r, int s, double k, bool singular, Z1 &P0, Z3 &P1)
+// The kernel and its smooth remainder.  exp(ikR)/R; with the static part
+// taken out, (exp(ikR) - 1)/R = i k exp(ikR/2) sin(kR/2)/(kR/2), which is
+// bounded (i k at R = 0) and is evaluated without a difference of close
+// numbers.
+__device__ __forceinline__ double2 kernel_full(double k, double R)
 {
-    const double A = m.area[s];
-    P0 = {0.0, 0.0};
-    P1 = {{0, 0, 0}, {0, 0, 0}};
+    double sn, cs;
+    sincos(k * R, &sn, &cs);
+    return make_double2(cs / R, sn / R);
+}
+
+__device__ __forceinline__ double2 kernel_smooth(double k, double R)
+{
+    const double u = 0.5 * k * R;
+    double sn, cs;
+    sincos(u, &sn, &cs);
+    const double sc = u < 1e-4 ? 1.0 - u * u / 6.0 : sn / u;
+    return make_double2(-k * sc * sn, k * sc * cs);
+}
+
+// psi0 and psi1 of source triangle s at r: seven-point rule on the kernel
+// (its smooth remainder when `extract`), plus the static part in closed form.
+__device__ SrcPot source_potential(const DevMesh &m, P3 r, int s, double k, bool extract)
+{
+    SrcPot P;
+    P.s = make_double2(0.0, 0.0);
+    for (int c = 0; c < 3; ++c) P.v[c] = make_double2(0.0, 0.0);
+    const double As = m.area[s];
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-        const P3 rq = mk(m.tq + 21 * s + 3 * q);
-        const double R = lenp(r - rq);
-        double gr, gi;
-        if (singular) {
-            const double x = k * R;
-            if (x < 1e-8) {
-                gr = -0.5 * k * k * R;
-                gi = k;
-            } else {
-                double sh, ch, sx, cx;
-                sincos(0.5 * x, &sh, &ch);
-                sincos(x, &sx, &cx);
-                gr = -2.0 * sh * sh / R;
-                gi = sx / R;
-            }
-        } else {
-            double sx, cx;
-            sincos(k * R, &sx, &cx);
-            gr = cx / R;
-            gi = sx / R;
+        const P3 d = mk(m.tq + 21 * s + 3 * q) - r;
+        const double R = lenp(d);
+        const double2 g = extract ? kernel_smooth(k, R) : kernel_full(k, R);
+        const double w = As * c_rule[q][3];
+        P.s.x += w * g.x;
+        P.s.y += w * g.y;
+        const double dc[3] = {d.x, d.y, d.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            P.v[c].x += w * dc[c] * g.x;
+            P.v[c].y += w * dc[c] * g.y;
         }
-        const double w = A * c_rule[q][3];
-        P0.re += w * gr;
-        P0.im += w * gi;
-        P1.re = P1.re + (w * gr) * rq;
-        P1.im = P1.im + (w * gi) * rq;
     }
-    if (singular) {
-        P3 v[3] = {mk(m.tv + 9 * s), mk(m.tv + 9 * s + 3), mk(m.tv + 9 * s + 6)};
-        double J0;
-        P3 J1, rho;
-        static_terms(r, v, J0, J1, rho);
-        P0.re += J0;
-        P1.re = P1.re + J1 + J0 * rho;
+    if (extract) {
+        const P3 p[3] = {mk(m.tv + 9 * s), mk(m.tv + 9 * s + 3), mk(m.tv + 9 * s + 6)};
+        double s0;
+        P3 s1;
+        flat_static(r, p, s0, s1);
+        P.s.x += s0;
+        P.v[0].x += s1.x;
+        P.v[1].x += s1.y;
+        P.v[2].x += s1.z;
     }
+    return P;
 }
 
-__device__ bool near_singular(const DevMesh &m, int t, int s)
+// Pairs whose inner integral takes the closed-form static part: the same
+// triangle, triangles with a common vertex, and triangles whose centroids
+// lie closer than twice the longer of their longest edges.
+__device__ bool extract_pair(const DevMesh &m, int t, int s)
 {
-    if (t == s) return true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-            if (m.tvi[3 * t + a] == m.tvi[3 * s + b]) return true;
-    const double d = lenp(mk(m.cen + 3 * t) - mk(m.cen + 3 * s));
-    return d < 2.0 * fmax(m.hmax[t], m.hmax[s]);
+    bool touch = t == s;
+    for (int x = 0; x < 9; ++x) touch = touch || m.tvi[3 * t + x / 3] == m.tvi[3 * s + x % 3];
+    if (touch) return true;
+    const P3 dc = mk(m.cen + 3 * t) - mk(m.cen + 3 * s);
+    const double lim = 2.0 * fmax(m.hmax[t], m.hmax[s]);
+    return dotp(dc, dc) < lim * lim;
 }
 
-// Outer triangle t of test function (sign si, length li, free vertex vi),
-// inner triangle s of source function (sj, lj, vj):
-// sum_p A_t w_p [ f_i(r_p) . int f_j g  -  div f_i div f_j int g / k^2 ]
-template <int DSIGN = -1>
-__device__ Z1 pair_integral(const DevMesh &m, int t, double si, double li, P3 vi, int s, double sj, double lj,
-                            P3 vj, double k, bool singular)
+// One RWG half on the outer triangle t (free vertex vo, coefficient co = sign
+// l / (2 A_t)) against one on the inner triangle s (vi, ci): the two parts of
+// Eq. (5) after integration by parts, without their constants,
+//   vec = sum_p A_t w_p f_o(r_p) . int_s f_i g,   sca = sum_p A_t w_p int_s g,
+// so that the pair adds i k eta (vec - 4 co ci sca / k^2) to Z.
+__device__ void half_pair(const DevMesh &m, int t, double co, P3 vo, int s, double ci, P3 vi, double k,
+                          bool extract, double2 &vec, double2 &sca)
 {
-    const double At = m.area[t], As = m.area[s];
-    const double ci = si * li / (2.0 * At), cj = sj * lj / (2.0 * As);
-    const double dd = (si * li / At) * (sj * lj / As) / (k * k);
-    Z1 acc = {0.0, 0.0};
+    vec = make_double2(0.0, 0.0);
+    sca = make_double2(0.0, 0.0);
+    const double At = m.area[t];
 #pragma unroll 1
     for (int p = 0; p < 7; ++p) {
         const P3 r = mk(m.tq + 21 * t + 3 * p);
-        Z1 P0;
-        Z3 P1;
-        inner_potentials(m, r, s, k, singular, P0, P1);
-        const P3 fi = ci * (r - vi);
-        // int f_j g = cj (P1 - vj P0)
-        const double vre = cj * (dotp(fi, P1.re) - P0.re * dotp(fi, vj));
-        const double vim = cj * (dotp(fi, P1.im) - P0.im * dotp(fi, vj));
+        const SrcPot P = source_potential(m, r, s, k, extract);
+        const P3 fo = co * (r - vo);
+        const P3 rv = r - vi;
+        // f_o . (psi1 + (r - vi) psi0) ci
+        const double a0 = fo.x * ci, a1 = fo.y * ci, a2 = fo.z * ci;
+        const double fr = dotp(fo, rv) * ci;
         const double w = At * c_rule[p][3];
-        if (DSIGN < 0) {
-            acc.re += w * (vre - dd * P0.re);
-            acc.im += w * (vim - dd * P0.im);
-        } else {
-            acc.re += w * (vre + dd * P0.re);
-            acc.im += w * (vim + dd * P0.im);
-        }
+        vec.x += w * (a0 * P.v[0].x + a1 * P.v[1].x + a2 * P.v[2].x + fr * P.s.x);
+        vec.y += w * (a0 * P.v[0].y + a1 * P.v[1].y + a2 * P.v[2].y + fr * P.s.y);
+        sca.x += w * P.s.x;
+        sca.y += w * P.s.y;
     }
-    return acc;
 }
 
-// sum_p sum_q A_t w_p A_s w_q [f_i(r_p) . f_j(r_q) - div f_i div f_j / k^2] i exp(ik|r_p - r_q|)
-__device__ Z1 pair_integral_dk(const DevMesh &m, int t, double si, double li, P3 vi, int s, double sj, double lj,
-                               P3 vj, double k)
+// The same two parts with the kernel's wavenumber derivative dg/dk =
+// i exp(ikR) (bounded: seven-point rule on both triangles).
+__device__ void half_pair_dk(const DevMesh &m, int t, double co, P3 vo, int s, double ci, P3 vi, double k,
+                             double2 &vec, double2 &sca)
 {
+    vec = make_double2(0.0, 0.0);
+    sca = make_double2(0.0, 0.0);
     const double At = m.area[t], As = m.area[s];
-    const double ci = si * li / (2.0 * At), cj = sj * lj / (2.0 * As);
-    const double dd = (si * li / At) * (sj * lj / As) / (k * k);
-    Z1 acc = {0.0, 0.0};
 #pragma unroll 1
     for (int p = 0; p < 7; ++p) {
         const P3 r = mk(m.tq + 21 * t + 3 * p);
-        const P3 fi = ci * (r - vi);
-        double are = 0.0, aim = 0.0;
+        const P3 fo = co * (r - vo);
+        double2 pv = make_double2(0.0, 0.0), ps = make_double2(0.0, 0.0);
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
             const P3 rq = mk(m.tq + 21 * s + 3 * q);
-            const double ff = dotp(fi, cj * (rq - vj)) - dd;
-            double sx, cx;
-            sincos(k * lenp(r - rq), &sx, &cx);
-            const double w = As * c_rule[q][3] * ff;
-            are -= w * sx;   // i exp(ikR) = -sin + i cos
-            aim += w * cx;
+            double sn, cs;
+            sincos(k * lenp(r - rq), &sn, &cs);
+            const double w = As * c_rule[q][3];
+            const double ff = dotp(fo, ci * (rq - vi));
+            // i exp(ikR) = -sin + i cos
+            pv.x -= w * ff * sn;
+            pv.y += w * ff * cs;
+            ps.x -= w * sn;
+            ps.y += w * cs;
         }
         const double w = At * c_rule[p][3];
-        acc.re += w * are;
-        acc.im += w * aim;
+        vec.x += w * pv.x;
+        vec.y += w * pv.y;
+        sca.x += w * ps.x;
+        sca.y += w * ps.y;
     }
-    return acc;
 }
 
+// Entry (i, j) of the near field as its vector and scalar parts summed over
+// the 2 x 2 triangle pairs; pairs with the static part in closed form are
+// the mean of both orders (outer/inner exchanged), so the blocks are
+// symmetric.  DK also returns the parts with dg/dk.
+template <bool DK>
+__device__ void rwg_entry(const DevMesh &m, int64_t i, int64_t j, double k, double2 &vec, double2 &sca,
+                          double2 &vec_dk, double2 &sca_dk)
+{
+    vec = sca = vec_dk = sca_dk = make_double2(0.0, 0.0);
+    for (int a = 0; a < 4; ++a) {
+        const int hi = a >> 1, hj = a & 1;
+        const int t = m.rtri[2 * i + hi], s = m.rtri[2 * j + hj];
+        const double co = (hi ? -1.0 : 1.0) * m.rlen[i] / (2.0 * m.area[t]);
+        const double ci = (hj ? -1.0 : 1.0) * m.rlen[j] / (2.0 * m.area[s]);
+        const P3 vo = mk(m.rvf + 6 * i + 3 * hi), vi = mk(m.rvf + 6 * j + 3 * hj);
+        const bool ex = extract_pair(m, t, s);
+        double2 v1, s1;
+        half_pair(m, t, co, vo, s, ci, vi, k, ex, v1, s1);
+        double f = 4.0 * co * ci;
+        if (ex) {
+            double2 v2, s2;
+            half_pair(m, s, ci, vi, t, co, vo, k, true, v2, s2);
+            v1 = make_double2(0.5 * (v1.x + v2.x), 0.5 * (v1.y + v2.y));
+            s1 = make_double2(0.5 * (s1.x + s2.x), 0.5 * (s1.y + s2.y));
+        }
+        vec.x += v1.x;
+        vec.y += v1.y;
+        sca.x += f * s1.x;
+        sca.y += f * s1.y;
+        if (DK) {
+            half_pair_dk(m, t, co, vo, s, ci, vi, k, v1, s1);
+            vec_dk.x += v1.x;
+            vec_dk.y += v1.y;
+            sca_dk.x += f * s1.x;
+            sca_dk.y += f * s1.y;
+        }
+    }
+}
+
+// One CTA per leaf strip; threads over its (row, column) entries in the
+// strip's column-major order.
+//   Z      = i k eta (vec - sca / k^2)
+//   dZ/dk  = i eta (vec + sca / k^2) + i k eta (vec' - sca' / k^2)
+template <bool DK>
 __global__ void k_near_fill(DevMesh m, DevNear nr, double k, double eta, double2 *val)
 {
     const int b = blockIdx.x;
-    const int r0 = nr.box_ptr[b];
-    const int nrow = nr.box_ptr[b + 1] - r0;
-    const int c0 = nr.col_ptr[b];
-    const int ncol = nr.col_ptr[b + 1] - c0;
+    const int r0 = nr.box_ptr[b], nrow = nr.box_ptr[b + 1] - r0;
+    const int c0 = nr.col_ptr[b], ncol = nr.col_ptr[b + 1] - c0;
     const int64_t off = nr.strip_off[b];
     const int64_t count = (int64_t)nrow * ncol;
+    const double ik2 = 1.0 / (k * k);
     for (int64_t e = threadIdx.x; e < count; e += blockDim.x) {
-        const int c = (int)(e / nrow), rr = (int)(e % nrow);
-        const int i = r0 + rr, j = nr.strip_col[c0 + c];
-        Z1 tot = {0.0, 0.0};
-        for (int a = 0; a < 2; ++a) {
-            const int t = m.rtri[2 * i + a];
-            const double si = a == 0 ? 1.0 : -1.0;
-            const P3 vi = mk(m.rvf + 6 * i + 3 * a);
-            for (int bb = 0; bb < 2; ++bb) {
-                const int s = m.rtri[2 * j + bb];
-                const double sj = bb == 0 ? 1.0 : -1.0;
-                const P3 vj = mk(m.rvf + 6 * j + 3 * bb);
-                const bool sing = near_singular(m, t, s);
-                Z1 z = pair_integral(m, t, si, m.rlen[i], vi, s, sj, m.rlen[j], vj, k, sing);
-                if (sing) {
-                    Z1 zr = pair_integral(m, s, sj, m.rlen[j], vj, t, si, m.rlen[i], vi, k, sing);
-                    z.re = 0.5 * (z.re + zr.re);
-                    z.im = 0.5 * (z.im + zr.im);
-                }
-                tot.re += z.re;
-                tot.im += z.im;
-            }
+        const int64_t i = r0 + e % nrow, j = nr.strip_col[c0 + e / nrow];
+        double2 vec, sca, vd, sd;
+        rwg_entry<DK>(m, i, j, k, vec, sca, vd, sd);
+        double2 z;
+        if (!DK) {
+            // i k eta (x + i y) = k eta (-y + i x)
+            const double x = vec.x - ik2 * sca.x, y = vec.y - ik2 * sca.y;
+            z = make_double2(-k * eta * y, k * eta * x);
+        } else {
+            const double x0 = vec.x + ik2 * sca.x, y0 = vec.y + ik2 * sca.y;
+            const double x1 = vd.x - ik2 * sd.x, y1 = vd.y - ik2 * sd.y;
+            z = make_double2(-eta * y0 - k * eta * y1, eta * x0 + k * eta * x1);
         }
-        // multiply by i k eta
-        val[off + e] = make_double2(-k * eta * tot.im, k * eta * tot.re);
-    }
-}
-
-__global__ void k_near_fill_dk(DevMesh m, DevNear nr, double k, double eta, double2 *val)
-{
-    const int b = blockIdx.x;
-    const int r0 = nr.box_ptr[b];
-    const int nrow = nr.box_ptr[b + 1] - r0;
-    const int c0 = nr.col_ptr[b];
-    const int ncol = nr.col_ptr[b + 1] - c0;
-    const int64_t off = nr.strip_off[b];
-    const int64_t count = (int64_t)nrow * ncol;
-    for (int64_t e = threadIdx.x; e < count; e += blockDim.x) {
-        const int c = (int)(e / nrow), rr = (int)(e % nrow);
-        const int i = r0 + rr, j = nr.strip_col[c0 + c];
-        Z1 tv = {0.0, 0.0}, td = {0.0, 0.0};
-        for (int a = 0; a < 2; ++a) {
-            const int t = m.rtri[2 * i + a];
-            const double si = a == 0 ? 1.0 : -1.0;
-            const P3 vi = mk(m.rvf + 6 * i + 3 * a);
-            for (int bb = 0; bb < 2; ++bb) {
-                const int s = m.rtri[2 * j + bb];
-                const double sj = bb == 0 ? 1.0 : -1.0;
-                const P3 vj = mk(m.rvf + 6 * j + 3 * bb);
-                const bool sing = near_singular(m, t, s);
-                Z1 z = pair_integral<1>(m, t, si, m.rlen[i], vi, s, sj, m.rlen[j], vj, k, sing);
-                if (sing) {
-                    Z1 zr = pair_integral<1>(m, s, sj, m.rlen[j], vj, t, si, m.rlen[i], vi, k, sing);
-                    z.re = 0.5 * (z.re + zr.re);
-                    z.im = 0.5 * (z.im + zr.im);
-                }
-                tv.re += z.re;
-                tv.im += z.im;
-                const Z1 d = pair_integral_dk(m, t, si, m.rlen[i], vi, s, sj, m.rlen[j], vj, k);
-                td.re += d.re;
-                td.im += d.im;
-            }
-        }
-        // i eta (A + Phi / k^2) + i k eta (A' - Phi' / k^2)
-        val[off + e] = make_double2(-eta * tv.im - k * eta * td.im, eta * tv.re + k * eta * td.re);
+        val[off + e] = z;
     }
 }
 
@@ -401,7 +434,7 @@ cudaError_t launch_near_fill(const DevMesh &m, const DevNear &nr, double k, doub
     cudaError_t e = upload_rule();
     if (e != cudaSuccess) return e;
     if (nr.nleaf == 0) return cudaSuccess;
-    k_near_fill<<<nr.nleaf, 128, 0, s>>>(m, nr, k, eta, val);
+    k_near_fill<false><<<nr.nleaf, 128, 0, s>>>(m, nr, k, eta, val);
     return cudaGetLastError();
 }
 
@@ -411,7 +444,7 @@ cudaError_t launch_near_fill_dk(const DevMesh &m, const DevNear &nr, double k, d
     cudaError_t e = upload_rule();
     if (e != cudaSuccess) return e;
     if (nr.nleaf == 0) return cudaSuccess;
-    k_near_fill_dk<<<nr.nleaf, 128, 0, s>>>(m, nr, k, eta, val);
+    k_near_fill<true><<<nr.nleaf, 128, 0, s>>>(m, nr, k, eta, val);
     return cudaGetLastError();
 }
 

@@ -3,10 +3,13 @@
 solves, every product through the GPU MLFMA, against the dense FP64 oracle's
 characteristic values on the same 1,920-unknown sphere mesh.
 
-The MLFMA product itself differs from the dense matrix by ~9e-4 (relative
-2-norm, 3-digit expansion); the characteristic values inherit a difference
-of that order relative to their size, which bounds what the comparison can
-show: |lambda_gpu - lambda_oracle| <= 2e-3 * max(|lambda|, 0.1)."""
+The eigenvalue target is |lambda_gpu - lambda_oracle| <= 1e-4 on the 10
+values nearest zero.  The characteristic values inherit the MLFMA product's
+own error relative to their size; with the 3-digit expansion of the product
+parity tests (9e-4 against the dense matrix) that is 1.9e-4, so these solves
+use a 5-digit plan (d0 = 5 in Eq. (9); on this three-level tree there is no
+interpolation, so the expansion is the only approximation), whose product
+error is ~1e-5."""
 import numpy as np
 import pytest
 
@@ -27,11 +30,11 @@ def setup_module():
     Z = efie.Problem(v, t, W.k).dense()
     _c["Z"] = Z
     _c["ref"] = cm.cm_values_arnoldi(Z, 10)
-    _c["plan"] = M.MlfmaPlan(v, t, W.k, W.levels, W.digits)
+    _c["plan"] = M.MlfmaPlan(v, t, W.k, W.levels, 5.0)
 
 
 def _close(lam, ref):
-    return np.all(np.abs(np.sort(lam) - np.sort(ref)) <= 2e-3 * np.maximum(np.abs(np.sort(ref)), 0.1))
+    return np.abs(np.sort(lam) - np.sort(ref)).max() <= 1e-4
 
 
 @pytest.mark.parametrize("prec", [M.FP64, M.FP32])

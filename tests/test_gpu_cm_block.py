@@ -2,9 +2,10 @@
 invert subspace iteration with Rayleigh-Ritz on X^-1 R, the inner solves of
 the whole block advancing together through batched MLFMA products, against
 the dense FP64 oracle's characteristic values on the 1,920-unknown sphere
-(same bound as the single-vector solver: the MLFMA product's own ~1e-3
-error carried into the values, |dlambda| <= 2e-3 max(|lambda|, 0.1)), and
-against cm_ira_solve on the same MLFMA pencil (no such error between them)."""
+(|dlambda| <= 1e-4 on the 10 values nearest zero, with the 5-digit plan of
+the single-vector tests, whose product error ~1e-5 keeps the values inside
+that bound), and against cm_ira_solve on the same MLFMA pencil (no such
+error between them)."""
 import numpy as np
 import pytest
 
@@ -25,11 +26,11 @@ def setup_module():
     Z = efie.Problem(v, t, W.k).dense()
     _c["Z"] = Z
     _c["ref"] = cm.cm_values(Z, 10)
-    _c["plan"] = M.MlfmaPlan(v, t, W.k, W.levels, W.digits)
+    _c["plan"] = M.MlfmaPlan(v, t, W.k, W.levels, 5.0)
 
 
 def _close(lam, ref):
-    return np.all(np.abs(np.sort(lam) - np.sort(ref)) <= 2e-3 * np.maximum(np.abs(np.sort(ref)), 0.1))
+    return np.abs(np.sort(lam) - np.sort(ref)).max() <= 1e-4
 
 
 @pytest.mark.parametrize("prec", [M.FP32, M.FP64])
@@ -104,7 +105,7 @@ def test_block_sphere_30720_te10_cluster():
     ref = np.loadtxt(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
                                   "sphere_30720_cm_values.txt"))
     ref20 = np.sort(ref[np.argsort(np.abs(ref))[:20]])
-    assert np.all(np.abs(np.sort(lam) - ref20) <= 2e-3 * np.maximum(np.abs(ref20), 0.1)), (lam, ref20)
+    assert np.abs(np.sort(lam) - ref20).max() <= 1e-4, (lam, ref20)
     assert abs(lam.mean() - ref20.mean()) < 1e-3 * abs(ref20.mean())
     ka = W.k * 2.0
     te10 = -spherical_yn(10, ka) / spherical_jn(10, ka)

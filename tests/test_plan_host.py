@@ -246,3 +246,25 @@ def test_header_is_plain_c(tmp_path):
                 [gcc, "-x", "c++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)]):
         r = subprocess.run(cmd, capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+
+def test_overlapping_x_and_y_rejected():
+    """x and y may not share a byte: a y equal to x, starting inside x or
+    ending inside x is MLFMA_EINVAL before anything else is looked at; a y
+    that only touches x passes that check (and then fails for the host-only
+    plan with another message)."""
+    import ctypes
+    W, v, t, P = host_plan("sphere-r0.5m-ico2")
+    lib = M.load()
+    n, B = P.n, 2
+    xbytes, ybytes = n * B * 8, n * B * 16      # FP64 real x, complex128 y
+    buf = np.zeros((xbytes + 2 * ybytes) // 8, np.float64)
+    x = buf.ctypes.data + ybytes
+    for fn in (lib.mlfma_matvec_host, lib.mlfma_matvec_noalloc):
+        for y in (x, x + 8, x + xbytes - 8, x - ybytes + 8):
+            st = fn(P._h, ctypes.c_void_p(x), 0, ctypes.c_void_p(y), B, M.FP64, None)
+            assert st == 1 and b"overlap" in lib.mlfma_last_error(), (fn, y - x)
+        for y in (x + xbytes, x - ybytes):
+            st = fn(P._h, ctypes.c_void_p(x), 0, ctypes.c_void_p(y), B, M.FP64, None)
+            assert st == 1 and b"overlap" not in lib.mlfma_last_error(), (fn, y - x)

@@ -1,6 +1,6 @@
 """mlfma_matvec_noalloc: the product for callers that cannot allocate device
-memory when they need it (an open stream capture, memory held entirely by
-another allocator, a real-time loop).  Called through the C ABI and checked
+memory when they need it (memory held entirely by another allocator, a
+real-time loop that must not allocate).  Called through the C ABI and checked
 against mlfma_matvec on the same plan and inputs, twice in a row, since every
 call reuses one static scratch array that keeps the previous call's
 contents.  Collected last so that a run stopping at the first failure has
