@@ -308,7 +308,10 @@ def main():
         dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
         dist = dist_mod
 
-    from paper_1412_1756_gb300 import FP32, FP64, MlfmaPlan
+    from paper_1412_1756_gb300 import FP32, FP64, MIXED_3XTF32, MIXED_TF32, MlfmaPlan
+    # batched precisions: FP32 throughout (CUDA-core interpolation), and FP32
+    # with the interpolation on the tensor cores as 3xTF32 or one TF32 product
+    modes = [("fp32", FP32), ("3xtf32", MIXED_3XTF32), ("tf32", MIXED_TF32)]
 
     wl = workloads.get(a.workload)
     v, t = wl.mesh()
@@ -360,51 +363,71 @@ def main():
         tuned = {"fp32_b%d_stage_sum_ms" % B: [r4(d32), r4(t32)],
                  "fp64_b1_stage_sum_ms": [r4(d64), r4(t64)]}
 
-    # --- mixed precision, batched (the headline)
+    # --- the FP64 oracle on sampled rows of the timed inputs
+    idx = np.random.default_rng(11).choice(n, 16, replace=False)
+    ref = None
+    if rank == 0:
+        from oracle import efie
+        ref = efie.Problem(v, t, wl.k).matvec_rows(x_np, idx)
+
+    def oracle_err(y):
+        if ref is None:
+            return None
+        yn = y.cpu().numpy()
+        return float(np.linalg.norm(yn[idx] - ref) / np.linalg.norm(ref))
+
+    # --- mixed precision, batched: every mode timed on the same inputs; the
+    # headline is the fastest one within the 1e-3 bound on those inputs
+    runs = {}
     with ClockSampler(local) as clk:
         torch.cuda.nvtx.range_push("timed")   # profilers can select the timed products (ncu --nvtx-include timed/)
-        ms = timed(lambda: plan.matvec(x32, y32), a.steps, a.warmup)
+        for name, pr in modes:
+            ms_m = timed(lambda: plan.matvec(x32, y32, prec=pr), a.steps, a.warmup)
+            runs[name] = {"ms_per_step": ms_m / a.steps, "value": replica_rate(B, a.steps, ms_m / 1e3, world),
+                          "err_vs_oracle": oracle_err(y32)}
         torch.cuda.nvtx.range_pop()
     clocks = clk.summary()
-    value = replica_rate(B, a.steps, ms / 1e3, world)
+    ok_modes = [m for m, _ in modes if runs[m]["err_vs_oracle"] is None or runs[m]["err_vs_oracle"] <= 1e-3]
+    head = min(ok_modes or ["fp32"], key=lambda m: runs[m]["ms_per_step"])
+    head_prec = dict(modes)[head]
+    ms = runs[head]["ms_per_step"] * a.steps
+    value = runs[head]["value"]
+    err = runs[head]["err_vs_oracle"]
+    plan.matvec(x32, y32, prec=head_prec)
     # --- plain FP64 single vector on the same GPU and input column
     steps64 = max(3, a.steps)
     ms64 = timed(lambda: plan.matvec(x64_1, y64), steps64, a.warmup)
     fp64_rate = replica_rate(1, steps64, ms64 / 1e3, 1)
-
-    # --- FP32 against FP64 stage by stage on the timed inputs: the outgoing
-    # field of every far level (aggregation and upward pass), the incoming
-    # field (translation and downward pass) and the product
-    stage_err = {}
+    err64 = None
     if rank == 0:
-        y64b = plan.matvec(x32.to(torch.float64)).cpu().numpy()
-        fields = {}
-        for prec in (FP32, FP64):
-            plan.matvec(x32 if prec == FP32 else x32.to(torch.float64))
-            for l in range(2, info["leaf_level"] + 1):
-                for w, nm in ((0, "S"), (1, "G")):
-                    fields[(prec, nm, l)] = plan.export_field(prec, w, l, B)
-        for (prec, nm, l), f64 in list(fields.items()):
-            if prec != FP64:
-                continue
-            f32 = fields[(FP32, nm, l)].astype(np.complex128)
-            stage_err["%s%d" % (nm, l)] = float(np.linalg.norm(f32 - f64) / np.linalg.norm(f64))
-        y32b = plan.matvec(x32).cpu().numpy()
-        stage_err["y"] = float(np.linalg.norm(y32b - y64b) / np.linalg.norm(y64b))
-
-    # --- error against the FP64 oracle on the timed inputs (sampled rows)
-    y32_np = y32.cpu().numpy()
-    y64_np = y64.cpu().numpy()
-    err = None
-    if rank == 0:
-        from oracle import efie
-        idx = np.random.default_rng(11).choice(n, 16, replace=False)
-        ref = efie.Problem(v, t, wl.k).matvec_rows(x_np, idx)
-        err = float(np.linalg.norm(y32_np[idx] - ref) / np.linalg.norm(ref))
+        y64_np = y64.cpu().numpy()
         err64 = float(np.linalg.norm(y64_np[idx, 0] - ref[:, 0]) / np.linalg.norm(ref[:, 0]))
 
+    # --- each batched precision against FP64 stage by stage on the timed
+    # inputs: the outgoing field of every far level (aggregation and upward
+    # pass), the incoming field (translation and downward pass) and the product
+    stage_err = {}
+    if rank == 0:
+        x64 = x32.to(torch.float64)
+        y64b = plan.matvec(x64).cpu().numpy()
+        f64 = {}
+        for l in range(2, info["leaf_level"] + 1):
+            for w, nm in ((0, "S"), (1, "G")):
+                f64[(nm, l)] = plan.export_field(FP64, w, l, B)
+        for name, pr in modes:
+            yb = plan.matvec(x32, prec=pr).cpu().numpy()
+            e = {}
+            for (nm, l), ref64 in f64.items():
+                w = 0 if nm == "S" else 1
+                f = plan.export_field(FP32, w, l, B).astype(np.complex128)
+                e["%s%d" % (nm, l)] = float(np.linalg.norm(f - ref64) / np.linalg.norm(ref64))
+            e["y"] = float(np.linalg.norm(yb - y64b) / np.linalg.norm(y64b))
+            stage_err[name] = e
+        del f64
+        plan.matvec(x32, y32, prec=head_prec)
+
     # --- per-stage device times (serial pass) and roofline of the dominant kernel
-    stage_runs = [plan.profile_stages(x32, y32) for _ in range(3)]
+    stage_runs = [plan.profile_stages(x32, y32, prec=head_prec) for _ in range(3)]
     stages = {k: float(np.median([r[k] for r in stage_runs])) for k in stage_runs[0]}
     dom = max((k for k in stages if k not in ("prepare", "finalize")), key=lambda k: stages[k])
     hbm_peak, peak_src = peaks()
@@ -438,16 +461,17 @@ def main():
     xh = torch.from_numpy(x_np.astype(np.float32)).pin_memory().numpy()
     yh = torch.empty((n, B), dtype=torch.complex64).pin_memory().numpy()
     for _ in range(a.warmup):
-        plan.matvec_host(xh, FP32, yh)
+        plan.matvec_host(xh, head_prec, yh)
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        plan.matvec_host(xh, FP32, yh)
+        plan.matvec_host(xh, head_prec, yh)
     e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": replica_rate(B, a.steps, e2e_s, world), "unit": UNIT, "h2d_bytes_per_step": int(xh.nbytes),
            "d2h_bytes_per_step": int(yh.nbytes),
-           "how": "mlfma_matvec_host: pinned host x -> device, product, device -> pinned host y, stream sync"}
+           "how": "mlfma_matvec_host (headline precision): pinned host x -> device, product, device -> pinned host y, "
+                  "stream sync"}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -466,6 +490,12 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64", "data": "synthetic",
+            "precision": {"headline": head,
+                          "interpolation": {"fp32": "fp32 CUDA cores", "3xtf32": "tcgen05 3xTF32, fp32 accumulate",
+                                            "tf32": "tcgen05 TF32, fp32 accumulate"}[head],
+                          "rule": "fastest batched precision whose error against the oracle rows of the timed "
+                                  "inputs is <= 1e-3"},
+            "batched_precisions": runs,
             "config": {"workload": wl.name, "N": n, "levels": wl.levels, "digits": wl.digits, "batch": B,
                        "interp_order": 10, "k": wl.k, "l2": "flushed between timed steps (256 MB write)",
                        "mesh": wl.note,
@@ -473,16 +503,16 @@ def main():
                                          % json.dumps(tuned)) if tuned else "built-in"},
             "fp64_single_vector": {"value": fp64_rate * world, "unit": UNIT, "ms_per_matvec": ms64 / steps64,
                                    "speedup_of_mixed_batched": value / (fp64_rate * world)},
-            "err_vs_oracle": {"fp32_batched": err, "fp64_single": err64 if rank == 0 else None,
+            "err_vs_oracle": {"batched": err, "fp64_single": err64 if rank == 0 else None,
                               "rows": 16, "bound": 1e-3},
-            "err_fp32_vs_fp64_by_stage": stage_err,
+            "err_vs_fp64_by_stage": stage_err,
             "roofline": roof,
             "hbm_frac_by_stage": hbm_stages,
             "fp32_alu_frac_by_stage": alu_stages,
             "stage_ms": {k: round(vv, 4) for k, vv in stages.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches_per_step * a.steps,
+            "gpu_launches": launches_per_step * a.steps * len(modes),
             "clocks": clocks,
             "setup_s": info["setup_seconds"],
         }

@@ -60,8 +60,19 @@ typedef enum {
  * radiation patterns, translations, interpolation, accumulation).
  * MLFMA_FP32: complex FP32 near field, patterns, translation tables and
  * fields, FP32 interpolation coefficients, FP32 accumulation; the tables are
- * built in FP64 and rounded once. */
-typedef enum { MLFMA_FP64 = 0, MLFMA_FP32 = 1 } mlfma_prec;
+ * built in FP64 and rounded once.
+ * MLFMA_MIXED_TF32 / MLFMA_MIXED_3XTF32: MLFMA_FP32, except that the local
+ * interpolation and anterpolation between levels (Section III-C) run as dense
+ * products on the tensor cores (tcgen05.mma kind::tf32, FP32 accumulation in
+ * tensor memory): one TF32 product (operands truncated to 10 mantissa bits),
+ * or three (hi/lo split of both operands, accurate to FP32 rounding).  They
+ * use the FP32 tables of the plan and apply to Z products (mlfma_matvec,
+ * mlfma_matvec_adjoint, mlfma_matvec_host, mlfma_profile_stages); other
+ * entry points return MLFMA_ENOTSUP.  Levels whose grids exceed the
+ * tensor-core kernels' limits use the FP32 CUDA-core kernels.  A tensor-core
+ * kernel whose bounded wait ran out is reported as MLFMA_ETIMEOUT by the
+ * next mlfma_sync (or by mlfma_matvec_host, which waits). */
+typedef enum { MLFMA_FP64 = 0, MLFMA_FP32 = 1, MLFMA_MIXED_TF32 = 2, MLFMA_MIXED_3XTF32 = 3 } mlfma_prec;
 
 typedef struct {
     int interp_order;   /* points per dimension of the local Lagrange
@@ -436,6 +447,27 @@ mlfma_status cm_rayleigh_ritz(int64_t n, int p, const double *Y, const double *R
  */
 mlfma_status cm_eig_derivatives(mlfma_plan_t plan, int nev, const double *lambda, const double *J,
                                 int prec, double *dlambda);
+
+/*
+ * Following characteristic modes over frequency (Section V tracks the values
+ * over a frequency sweep; the paper does not say how modes are paired):
+ * pairs the nb modes (lambda_b, Jb) found at one wavenumber with the na modes
+ * (lambda_a, Ja) of the previous one by their currents.  Clusters of values
+ * (sorted values whose neighbours differ by at most cluster_tol times their
+ * magnitude) are paired first, by the share of the smaller cluster's span
+ * that lies in the other's (||Ja_A^T Jb_B||_F^2 / min(|A|, |B|) with unit
+ * columns; pairs of score >= 0.5, greedily by score, each cluster once); the
+ * modes of paired clusters are then matched greedily by |Ja_i . Jb_j|.  Inside
+ * a degenerate cluster the single pairings are as arbitrary as the basis the
+ * eigensolver returned; compare cluster sums or means there.  Host only.
+ *  Ja [n][na], Jb [n][nb] host, real (the layout cm_ira_solve writes)
+ *  match   [nb] out: index into set a of each mode of set b, -1 if none
+ *  overlap [nb] out: score of the cluster pair the mode belongs to (0 if none)
+ * Errors: EINVAL for NULL pointers, empty sets or cluster_tol < 0.
+ */
+mlfma_status cm_track_modes(int64_t n, int na, const double *lambda_a, const double *Ja, int nb,
+                            const double *lambda_b, const double *Jb, double cluster_tol, int *match,
+                            double *overlap);
 
 /* Summary of a plan (host copy; all fields filled). */
 #define MLFMA_MAX_LEVELS 22

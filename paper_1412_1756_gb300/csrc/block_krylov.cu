@@ -28,9 +28,15 @@ constexpr int kRowBlocks = 96;   // row blocks of the column-dot kernel
 
 inline int grid_of(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
 
-// part[(j p + c) nrb + blk] = sum over the CTA's rows i of V_j[i][c] w[i][c]
-// (FP64).  A warp reads 32 adjacent columns of one row; 8 warps per CTA take
-// interleaved rows; grid (nrb, nv, ceil(p / 32)).
+// part[(j p + c) nrb + blk] = sum over the CTA's rows i of V_j[i][c] w[i][c].
+// A warp reads 32 adjacent columns of one row; 8 warps per CTA take
+// interleaved rows; grid (nrb, nv, ceil(p / 32)).  Each thread accumulates
+// in FP32 with compensation: a product a b is split exactly into its rounded
+// value pr and error fma(a, b, -pr), the running sum takes pr by TwoSum
+// (Knuth: the rounding error of s + pr is recovered exactly) and a second
+// FP32 accumulator collects both errors, so the thread's sum carries about
+// twice the FP32 precision at FP32 ALU cost; the two accumulators are
+// widened to FP64 only for the reduction across threads.
 __global__ void __launch_bounds__(256) k_col_dots(const float *V, int64_t ld, const float *w, int64_t n, int p,
                                                   double *part)
 {
@@ -38,11 +44,18 @@ __global__ void __launch_bounds__(256) k_col_dots(const float *V, int64_t ld, co
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int c = blockIdx.z * 32 + tx;
     const float *v = V + (int64_t)blockIdx.y * ld;
-    double s = 0;
+    float s = 0.f, err = 0.f;
     if (c < p)
-        for (int64_t i = (int64_t)blockIdx.x * 8 + ty; i < n; i += (int64_t)gridDim.x * 8)
-            s += (double)v[i * p + c] * (double)w[i * p + c];
-    red[ty][tx] = s;
+        for (int64_t i = (int64_t)blockIdx.x * 8 + ty; i < n; i += (int64_t)gridDim.x * 8) {
+            const float a = v[i * p + c], b = w[i * p + c];
+            const float pr = a * b;
+            const float pe = fmaf(a, b, -pr);
+            const float t = s + pr;
+            const float z = t - s;
+            err += ((s - (t - z)) + (pr - z)) + pe;
+            s = t;
+        }
+    red[ty][tx] = (double)s + (double)err;
     __syncthreads();
     if (ty == 0 && c < p) {
         double t = 0;
@@ -62,17 +75,24 @@ __global__ void k_col_dots_reduce(const double *part, int nrb, int64_t m, double
     }
 }
 
-// out[i][c] = (acc ? out[i][c] : 0) + sign * sum_{j < nv} coef[j p + c] V_j[i][c]
-__global__ void k_col_lincomb(float *out, const float *V, int64_t ld, int nv, const double *coef, int64_t n, int p,
+// out[i][c] = (acc ? out[i][c] : 0) + sign * sum_{j < nv} coef[j p + c] V_j[i][c],
+// with the coefficients narrowed to FP32 once (k_narrow) rather than per
+// element.
+__global__ void k_col_lincomb(float *out, const float *V, int64_t ld, int nv, const float *coef, int64_t n, int p,
                               float sign, int acc)
 {
     BLOCK_LOOP(e, n * p)
     {
         const int c = (int)(e % p);
         float s = 0.f;
-        for (int j = 0; j < nv; ++j) s = fmaf((float)coef[(int64_t)j * p + c], V[(int64_t)j * ld + e], s);
+        for (int j = 0; j < nv; ++j) s = fmaf(coef[(int64_t)j * p + c], V[(int64_t)j * ld + e], s);
         out[e] = (acc ? out[e] : 0.f) + sign * s;
     }
+}
+
+__global__ void k_narrow(float *dst, const double *src, int64_t n)
+{
+    BLOCK_LOOP(e, n) dst[e] = (float)src[e];
 }
 
 // dst[i][c] = f[c] src[i][c]
@@ -119,6 +139,7 @@ class BlockGmres {
     float *w = nullptr, *t = nullptr, *d = nullptr, *r = nullptr, *rr = nullptr;
     float2 *sai = nullptr;
     double *part = nullptr, *hd = nullptr, *cf = nullptr;
+    float *cf32 = nullptr;   // coefficients narrowed for k_col_lincomb
     std::vector<int64_t> perm;
     std::vector<float> stage;
     std::vector<double> hh;
@@ -126,7 +147,7 @@ class BlockGmres {
     ~BlockGmres()
     {
         for (void *q : {(void *)V, (void *)w, (void *)t, (void *)d, (void *)r, (void *)rr, (void *)sai, (void *)part,
-                        (void *)hd, (void *)cf})
+                        (void *)hd, (void *)cf, (void *)cf32})
             if (q) cudaFree(q);
         if (s) cudaStreamDestroy(s);
     }
@@ -224,6 +245,7 @@ BlockGmres *block_gmres_create(mlfma_plan_t p, const std::complex<double> *sai, 
     alloc((void **)&g->part, (size_t)(restart + 1) * cols * kRowBlocks * sizeof(double));
     alloc((void **)&g->hd, (size_t)(restart + 1) * cols * sizeof(double));
     alloc((void **)&g->cf, (size_t)(restart + 1) * cols * sizeof(double));
+    alloc((void **)&g->cf32, (size_t)(restart + 1) * cols * sizeof(float));
     g->aZ = a32;
     g->aZ.B = cols;
     g->aP = g->aZ;
@@ -321,7 +343,8 @@ int block_gmres_run(BlockGmres *g, const double *bh, double *dh, int guess, doub
                 for (int c = 0; c < p; ++c)
                     if (active[c])
                         for (int j = 0; j <= k; ++j) h(c, j, k) += g->hh[(size_t)j * p + c];
-                k_col_lincomb<<<grid_of(np), 256, 0, g->s>>>(vk1, g->V, np, k + 1, g->hd, n, p, -1.f, 1);
+                k_narrow<<<grid_of((int64_t)(k + 1) * p), 256, 0, g->s>>>(g->cf32, g->hd, (int64_t)(k + 1) * p);
+                k_col_lincomb<<<grid_of(np), 256, 0, g->s>>>(vk1, g->V, np, k + 1, g->cf32, n, p, -1.f, 1);
             }
             BTRY(g->norms(vk1, hn));
             for (int c = 0; c < p; ++c) f[c] = active[c] && hn[c] > 0 ? 1.0 / hn[c] : 0.0;
@@ -364,7 +387,8 @@ int block_gmres_run(BlockGmres *g, const double *bh, double *dh, int guess, doub
         }
         if (steps > 0) {
             BTRY(g->upload(f, (size_t)steps * p));
-            k_col_lincomb<<<grid_of(np), 256, 0, g->s>>>(g->t, g->V, np, steps, g->cf, n, p, 1.f, 0);
+            k_narrow<<<grid_of((int64_t)steps * p), 256, 0, g->s>>>(g->cf32, g->cf, (int64_t)steps * p);
+            k_col_lincomb<<<grid_of(np), 256, 0, g->s>>>(g->t, g->V, np, steps, g->cf32, n, p, 1.f, 0);
             BTRY(g->precondition(g->t, g->w));
             k_accumulate<<<grid_of(np), 256, 0, g->s>>>(g->d, g->w, np);
         }

@@ -8,6 +8,7 @@
 #include <complex>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 #include <memory>
 #include <new>
@@ -140,68 +141,139 @@ cudaError_t upload_pairs(DevMem &M, const std::vector<cd> &v, const R **out)
 // Tables of a parent level l (to and from level l + 1): phase shifts, the
 // packed interpolation stencils and the anterpolation stencils zero-padded
 // to dn_taps taps per row.
-// Round an FP32 value to TF32 (10 explicit mantissa bits), to nearest with
-// ties away from zero, on its bit pattern (finite values).
-static float tf32_round(float x)
+// Tables of the tensor-core interpolation kernels (umma_interp.cu) of a
+// parent level: each one-dimensional step as the dense B operand of
+// tcgen05.mma kind::tf32, N rows of K values, K-major with the 128-byte
+// swizzle (per 32-value K-atom: 8-row groups of 1024 bytes, row r of a group
+// at r * 128, its 16-byte chunk c at position c ^ r), TF32 hi part (the FP32
+// value rounded to the nearest TF32, 10 mantissa bits, ties away from zero)
+// then the lo part (the FP32 rest).
+static float tf32_rn(float x)
 {
     uint32_t u;
     std::memcpy(&u, &x, 4);
-    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    u = (u + 0x1000u) & 0xffffe000u;
     float r;
     std::memcpy(&r, &u, 4);
     return r;
 }
 
-// Dense row-major A [m][k] (zero beyond its extent) in mma.m16n8k8 TF32
-// A-fragment order, hi and lo parts: lane (g = lane / 4, q = lane % 4) holds
-// A[g][q], A[g+8][q], A[g][q+4], A[g+8][q+4] of each 16 x 8 tile.
-static std::vector<float> tc_fragments(const std::vector<double> &A, int m, int k, int &mt, int &kt)
+// dense [rows][K] (rows <= N), appended to img at a 1024-byte boundary
+static void umma_step_image(const std::vector<double> &A, int rows, UmmaStep &st, std::vector<unsigned char> &img)
 {
-    mt = (m + 15) / 16;
-    kt = (k + 7) / 8;
-    std::vector<float> f((size_t)mt * kt * 32 * 8, 0.0f);
-    auto at = [&](int r, int c) { return (r < m && c < k) ? A[(size_t)r * k + c] : 0.0; };
-    for (int a = 0; a < mt; ++a)
-        for (int b = 0; b < kt; ++b)
-            for (int lane = 0; lane < 32; ++lane) {
-                const int g = lane >> 2, q = lane & 3;
-                const double v[4] = {at(a * 16 + g, b * 8 + q), at(a * 16 + g + 8, b * 8 + q), at(a * 16 + g, b * 8 + q + 4),
-                                     at(a * 16 + g + 8, b * 8 + q + 4)};
-                float *dst = &f[(((size_t)a * kt + b) * 32 + lane) * 8];
-                for (int r = 0; r < 4; ++r) {
-                    const float x = (float)v[r];
-                    const float hi = tf32_round(x);
-                    dst[r] = hi;
-                    dst[4 + r] = tf32_round(x - hi);
-                }
-            }
-    return f;
+    const int atoms = (st.K + 31) / 32;
+    st.bytes = atoms * st.N * 128;
+    st.off = (int)((img.size() + 1023) / 1024 * 1024);
+    img.resize((size_t)st.off + 2 * (size_t)st.bytes, 0);
+    st.kmask = 0;
+    for (int n = 0; n < rows; ++n)
+        for (int k = 0; k < st.K; ++k) {
+            const double v = A[(size_t)n * st.K + k];
+            if (v == 0.0) continue;
+            st.kmask |= 1u << (k / 8);
+            const size_t o = (size_t)(k / 32) * st.N * 128 + (n / 8) * 1024 + (n % 8) * 128 +
+                             ((((k % 32) / 4) ^ (n % 8)) << 4) + (k % 4) * 4;
+            const float f = (float)v, hi = tf32_rn(f), lo = f - hi;
+            std::memcpy(&img[st.off + o], &hi, 4);
+            std::memcpy(&img[st.off + st.bytes + o], &lo, 4);
+        }
 }
 
-template <class R>
-cudaError_t upload_tc_tables(DevMem &M, const PlanHost &H, const Level &Lv, DevLevel<R> &D)
+static int up8(int v) { return (v + 7) / 8 * 8; }
+static int up4(int v) { return (v + 3) / 4 * 4; }
+static int up16(int v) { return (v + 15) / 16 * 16; }
+
+// Up: phi (B1: rows = parent phi, extended by 16 rows that repeat the first
+// ones so that reflected columns never wrap; K = child phi), then theta (B2:
+// rows = parent theta; K = child theta, then from kr0 on the child theta rows
+// taken at phi + pi).  Down: theta (B1: rows = child theta; K = parent theta,
+// then the block taken at phi + pi), then phi (B2: rows = child phi; K =
+// parent phi).  A level whose steps exceed the kernels' limits (K <= 256,
+// N <= 256, tensor memory <= 512 columns) gets no tables.
+static cudaError_t upload_umma_tables(DevMem &M, const PlanHost &H, const Level &Lv, DevLevel<float> &D, int *err)
 {
-    if (sizeof(R) != 4) return cudaSuccess;
     const Level &C = H.lv[Lv.l + 1];
-    const int nthc = C.nth, nphc = C.nph;
-    std::vector<double> th((size_t)Lv.nth * 2 * nthc, 0.0), ph((size_t)Lv.nph * nphc, 0.0);
-    for (int t = 0; t < Lv.nth; ++t)
-        for (int e = Lv.th_up.ptr[t]; e < Lv.th_up.ptr[t + 1]; ++e)
-            th[(size_t)t * 2 * nthc + (Lv.th_up.refl[e] ? nthc : 0) + Lv.th_up.idx[e]] += Lv.th_up.coef[e];
-    for (int u = 0; u < Lv.nph; ++u)
-        for (int e = Lv.ph_up.ptr[u]; e < Lv.ph_up.ptr[u + 1]; ++e)
-            ph[(size_t)u * nphc + Lv.ph_up.idx[e]] += Lv.ph_up.coef[e];
+    const int nthp = Lv.nth, nphp = Lv.nph, nthc = C.nth, nphc = C.nph;
+    auto fits = [](const UmmaStep &st) { return st.K <= 256 && st.N <= 256 && st.K > 0 && st.N > 0; };
     cudaError_t e;
-    const float *p;
-    if ((e = M.upload(tc_fragments(th, Lv.nth, 2 * nthc, D.tc_mt_th, D.tc_kt_th), &p)) != cudaSuccess) return e;
-    D.tc_th = p;
-    if ((e = M.upload(tc_fragments(ph, Lv.nph, nphc, D.tc_mt_ph, D.tc_kt_ph), &p)) != cudaSuccess) return e;
-    D.tc_ph = p;
+    {   // up
+        UmmaStep s1, s2;
+        s1.K = up8(nphc);
+        s1.N = up16(nphp + 16);
+        s1.kr0 = s1.K;
+        s2.kr0 = up4(nthc);
+        s2.K = up8(s2.kr0 + nthc);
+        s2.N = up16(nthp);
+        const int tiles1 = (nthc + 15) / 16, tiles2 = (nphp + 15) / 16;
+        const int cols = tiles1 * s1.N + s2.N + tiles2 * s2.N;
+        if (fits(s1) && fits(s2) && cols <= 512) {
+            std::vector<double> b1((size_t)s1.N * s1.K, 0.0), b2((size_t)s2.N * s2.K, 0.0);
+            for (int n = 0; n < nphp + 16; ++n) {
+                const int u = n % nphp;
+                for (int f = Lv.ph_up.ptr[u]; f < Lv.ph_up.ptr[u + 1]; ++f) b1[(size_t)n * s1.K + Lv.ph_up.idx[f]] += Lv.ph_up.coef[f];
+            }
+            for (int t = 0; t < nthp; ++t)
+                for (int f = Lv.th_up.ptr[t]; f < Lv.th_up.ptr[t + 1]; ++f)
+                    b2[(size_t)t * s2.K + (Lv.th_up.refl[f] ? s2.kr0 : 0) + Lv.th_up.idx[f]] += Lv.th_up.coef[f];
+            std::vector<unsigned char> img;
+            umma_step_image(b1, s1.N, s1, img);
+            umma_step_image(b2, s2.N, s2, img);
+            const unsigned char *d;
+            if ((e = M.upload(img, &d)) != cudaSuccess) return e;
+            D.um_up = d;
+            D.um_up_bytes = (int)img.size();
+            D.um_up1 = s1;
+            D.um_up2 = s2;
+        }
+    }
+    {   // down
+        UmmaStep s1, s2;
+        s1.kr0 = up4(nthp);
+        s1.K = up8(s1.kr0 + nthp);
+        s1.N = up16(nthc);
+        s2.K = up8(nphp);
+        s2.N = up16(nphc);
+        s2.kr0 = s2.K;
+        const int tiles1 = (nphp + 15) / 16;
+        const int cols = tiles1 * s1.N + s2.N;
+        if (fits(s1) && fits(s2) && cols <= 512) {
+            std::vector<double> b1((size_t)s1.N * s1.K, 0.0), b2((size_t)s2.N * s2.K, 0.0);
+            for (int t = 0; t < nthc; ++t)
+                for (int f = Lv.th_dn.ptr[t]; f < Lv.th_dn.ptr[t + 1]; ++f)
+                    b1[(size_t)t * s1.K + (Lv.th_dn.refl[f] ? s1.kr0 : 0) + Lv.th_dn.idx[f]] += Lv.th_dn.coef[f];
+            for (int v = 0; v < nphc; ++v)
+                for (int f = Lv.ph_dn.ptr[v]; f < Lv.ph_dn.ptr[v + 1]; ++f) b2[(size_t)v * s2.K + Lv.ph_dn.idx[f]] += Lv.ph_dn.coef[f];
+            std::vector<unsigned char> img;
+            umma_step_image(b1, s1.N, s1, img);
+            umma_step_image(b2, s2.N, s2, img);
+            const unsigned char *d;
+            if ((e = M.upload(img, &d)) != cudaSuccess) return e;
+            D.um_dn = d;
+            D.um_dn_bytes = (int)img.size();
+            D.um_dn1 = s1;
+            D.um_dn2 = s2;
+        }
+    }
+    D.um_err = err;
+    const char *hook = std::getenv("MLFMA_TEST_WITHHOLD_ARRIVAL");
+    D.um_test = (hook && hook[0] == '1') ? 1 : 0;
     return cudaSuccess;
 }
 
 template <class R>
-cudaError_t upload_parent_tables(DevMem &M, const PlanHost &H, const Level &Lv, DevLevel<R> &D)
+cudaError_t upload_tc_tables(DevMem &, const PlanHost &, const Level &, DevLevel<R> &, int *)
+{
+    return cudaSuccess;
+}
+
+template <>
+cudaError_t upload_tc_tables<float>(DevMem &M, const PlanHost &H, const Level &Lv, DevLevel<float> &D, int *err)
+{
+    return upload_umma_tables(M, H, Lv, D, err);
+}
+
+template <class R>
+cudaError_t upload_parent_tables(DevMem &M, const PlanHost &H, const Level &Lv, DevLevel<R> &D, int *err)
 {
     cudaError_t e;
     if ((e = upload_pairs<R>(M, Lv.shift, &D.shift)) != cudaSuccess) return e;
@@ -238,7 +310,7 @@ cudaError_t upload_parent_tables(DevMem &M, const PlanHost &H, const Level &Lv, 
     };
     if ((e = M.upload(pad(Lv.th_dn), &D.thd_pad)) != cudaSuccess) return e;
     if ((e = M.upload(pad(Lv.ph_dn), &D.phd_pad)) != cudaSuccess) return e;
-    return upload_tc_tables<R>(M, H, Lv, D);
+    return upload_tc_tables<R>(M, H, Lv, D, err);
 }
 
 template <class R>
@@ -274,6 +346,10 @@ cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *ne
         }
     }
     void *d;
+    // status word of the tensor-core kernels' bounded waits (0 = fine)
+    if ((e = M.alloc(&d, 16)) != cudaSuccess) return e;
+    if ((e = cudaMemset(d, 0, 16)) != cudaSuccess) return e;
+    a.um_err = static_cast<int *>(d);
     if ((e = M.alloc(&d, (size_t)H.N * Bmax * sizeof(R))) != cudaSuccess) return e;
     a.xp = static_cast<R *>(d);
     if ((e = M.alloc(&d, (size_t)H.N * Bmax * 2 * sizeof(R))) != cudaSuccess) return e;
@@ -298,7 +374,7 @@ cudaError_t setup_precision(mlfma_plan_t p, ProductArgs<R> &a, const double2 *ne
         D.phd_ptr = ip[14]; D.phd_idx = ip[15];
         if ((e = upload_pairs<R>(M, Lv.alpha, &D.alpha)) != cudaSuccess) return e;
         if (l < H.leaf) {
-            if ((e = upload_parent_tables<R>(M, H, Lv, D)) != cudaSuccess) return e;
+            if ((e = upload_parent_tables<R>(M, H, Lv, D, a.um_err)) != cudaSuccess) return e;
         }
         std::vector<R> w(Lv.K);
         for (int q = 0; q < Lv.K; ++q)
@@ -587,7 +663,7 @@ cudaError_t setup_r(mlfma_plan_t p, const ProductArgs<R> &a, ProductArgs<R> &ar)
             if ((e = M.upload(Lv.octant, &D.octant)) != cudaSuccess) return e;
             if ((e = M.upload(Lv.child_ptr, &D.child_ptr)) != cudaSuccess) return e;
             if ((e = M.upload(H.lv[0].child_ptr, &D.pchild_ptr)) != cudaSuccess) return e;
-            if ((e = upload_parent_tables<R>(M, H, Lv, D)) != cudaSuccess) return e;
+            if ((e = upload_parent_tables<R>(M, H, Lv, D, nullptr)) != cudaSuccess) return e;
             std::vector<R> w(Lv.K);
             for (int q = 0; q < Lv.K; ++q) w[q] = (R)(Lv.wt[q / Lv.nph] * 2.0 * M_PI / Lv.nph);
             if ((e = M.upload(w, &D.wq)) != cudaSuccess) return e;
@@ -718,7 +794,7 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
         for (int l = a.coarsest; l <= a.leaf; ++l) {
             pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6, 7, 8}, best.tr[l]);
             if (l < a.leaf) {
-                pick(STAGE_UP + l, {1, 2, 4, 8, 16, 100}, best.up_nb[l]);
+                pick(STAGE_UP + l, {1, 2, 4, 8, 16}, best.up_nb[l]);
                 pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108}, best.down_nb[l]);
             }
         }
@@ -758,7 +834,7 @@ template <class R>
 mlfma_status core_graph(mlfma_plan_t p, const ProductArgs<R> &a, int prec, int kind, cudaGraphExec_t *out)
 {
     const int dk = kind == KIND_DK;
-    auto key = std::make_pair(prec + 2 * kind, a.B);
+    auto key = std::make_pair(prec + 4 * kind, a.B);
     auto it = p->graphs.find(key);
     if (it != p->graphs.end()) {
         *out = it->second;
@@ -789,7 +865,8 @@ mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int
 {
     const int dk = kind == KIND_DK;
     if (kind == KIND_Z) {
-        auto t = p->tunes.find(std::make_pair(prec, a.B));
+        const int tprec = prec == MLFMA_FP64 ? MLFMA_FP64 : MLFMA_FP32;   // mixed precisions: FP32 shapes
+        auto t = p->tunes.find(std::make_pair(tprec, a.B));
         if (t != p->tunes.end()) a.tune = t->second;
     }
     cudaError_t e;
@@ -827,6 +904,19 @@ mlfma_status run(mlfma_plan_t p, ProductArgs<R> a, int prec, const void *xd, int
     return MLFMA_OK;
 }
 
+// Status word of the tensor-core kernels (after the work that may have set
+// it has finished): a bounded wait that ran out is MLFMA_ETIMEOUT, once.
+mlfma_status check_umma_status(mlfma_plan_t p)
+{
+    if (!p->has32 || !p->a32.um_err) return MLFMA_OK;
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, p->a32.um_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core status");
+    if (!h) return MLFMA_OK;
+    if ((e = cudaMemset(p->a32.um_err, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "tensor-core status");
+    return fail(MLFMA_ETIMEOUT, "a tensor-core interpolation kernel gave up waiting for its MMAs; its output is invalid");
+}
+
 mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, int prec, void *stream, int adjoint,
                      bool host, double *stage_ms = nullptr, int kind = KIND_Z)
 {
@@ -834,6 +924,15 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
     if (check_plan(p)) return MLFMA_EINVAL;
     if (!x || !y) return fail(MLFMA_EINVAL, "x or y is NULL");
     if (B < 1) return fail(MLFMA_EINVAL, "B must be >= 1");
+    // the mixed precisions are FP32 products with tensor-core interpolation
+    const int key_prec = prec;
+    int umma = 0;
+    if (prec == MLFMA_MIXED_TF32 || prec == MLFMA_MIXED_3XTF32) {
+        if (kind != KIND_Z)
+            return fail(MLFMA_ENOTSUP, "the TF32 precisions apply to Z products (mlfma_matvec, _adjoint, _host)");
+        umma = prec == MLFMA_MIXED_TF32 ? 1 : 3;
+        prec = MLFMA_FP32;
+    }
     const int64_t Bi = B * (xc ? 2 : 1);
     if (Bi > p->opts.max_batch) return fail(MLFMA_EINVAL, "B exceeds the plan's max_batch");
     {
@@ -887,13 +986,15 @@ mlfma_status product(mlfma_plan_t p, const void *x, int xc, void *y, int64_t B, 
     } else {
         ProductArgs<float> a = kind == KIND_X ? p->ax32 : kind == KIND_R ? p->ar32 : p->a32;
         a.B = (int)Bi;
-        st = run<float>(p, a, prec, xd, xc, yd, (int)B, adjoint, kind, s, stage_ms);
+        a.umma = umma;
+        st = run<float>(p, a, key_prec, xd, xc, yd, (int)B, adjoint, kind, s, stage_ms);
     }
     if (st != MLFMA_OK) return st;
     if (host) {
         if ((e = cudaMemcpyAsync(y, p->stage_y, ybytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return cuda_fail(e, "copy y to host");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "product");
+        if (umma) return check_umma_status(p);
     }
     return MLFMA_OK;
 }
@@ -1205,7 +1306,7 @@ mlfma_status mlfma_tune_set(mlfma_plan_t p, int64_t B, int xc, int prec, const i
                   choices[2] >= 0 && choices[2] <= 3;
         for (int l = 0; l < MLFMA_MAX_LEVELS && ok; ++l) {
             const int u = choices[3 + l], d = choices[3 + MLFMA_MAX_LEVELS + l], r = choices[3 + 2 * MLFMA_MAX_LEVELS + l];
-            ok = (u == 0 || pow2(u) || u == 100) && (d == 0 || pow2(d) || d == 104 || d == 108) && r >= 0 && r <= 8;
+            ok = (u == 0 || pow2(u)) && (d == 0 || pow2(d) || d == 104 || d == 108) && r >= 0 && r <= 8;
         }
         if (!ok) return fail(MLFMA_EINVAL, "a launch-shape choice is outside its documented set");
     }
@@ -1277,7 +1378,7 @@ mlfma_status mlfma_sync(mlfma_plan_t p, void *stream)
     DeviceGuard g(p->device);
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "mlfma_sync");
-    return MLFMA_OK;
+    return check_umma_status(p);
 }
 
 mlfma_status mlfma_plan_info(mlfma_plan_t p, mlfma_info *info)

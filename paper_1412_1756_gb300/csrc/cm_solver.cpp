@@ -1171,3 +1171,100 @@ extern "C" mlfma_status cm_eig_derivatives(mlfma_plan_t plan, int nev, const dou
     if (prev != dev) cudaSetDevice(prev);
     return st;
 }
+
+// ------------------------------------------------- modes over frequency ---
+
+// Matching the modes of one wavenumber to those of the previous one, by
+// their currents (the paper follows characteristic values over frequency in
+// Section V without saying how modes are paired).  The currents of a
+// degenerate cluster span a subspace whose basis the eigensolver picks
+// freely, so clusters are paired first, by how much of one cluster's span
+// lies in the other's, and single modes inside paired clusters afterwards.
+//   1. columns scaled to unit 2-norm; clusters: runs of values (sorted)
+//      whose neighbours differ by at most cluster_tol * max(|lambda|, 1e-12);
+//   2. cluster score s(A, B) = ||Ja_A^T Jb_B||_F^2 / min(|A|, |B|) (1 when
+//      the smaller span lies in the larger), pairs taken greedily by
+//      decreasing score while s >= 0.5, each cluster once;
+//   3. inside a pair, modes matched greedily by |Ja_i . Jb_j|.
+extern "C" mlfma_status cm_track_modes(int64_t n, int na, const double *lambda_a, const double *Ja, int nb,
+                                       const double *lambda_b, const double *Jb, double cluster_tol, int *match,
+                                       double *overlap)
+{
+    if (n < 1 || na < 1 || nb < 1 || !lambda_a || !Ja || !lambda_b || !Jb || !match || !overlap || !(cluster_tol >= 0))
+        return fail(MLFMA_EINVAL, "cm_track_modes: NULL argument, empty set or negative cluster_tol");
+    auto norms = [&](const double *J, int m) {
+        std::vector<double> s(m, 0.0);
+        for (int64_t r = 0; r < n; ++r)
+            for (int c = 0; c < m; ++c) s[c] += J[r * m + c] * J[r * m + c];
+        for (double &v : s) v = v > 0 ? 1.0 / std::sqrt(v) : 0.0;
+        return s;
+    };
+    const std::vector<double> sa = norms(Ja, na), sb = norms(Jb, nb);
+    // O[i][j] = Ja_i . Jb_j (unit columns)
+    std::vector<double> O((size_t)na * nb, 0.0);
+    for (int64_t r = 0; r < n; ++r)
+        for (int i = 0; i < na; ++i) {
+            const double a = Ja[r * na + i] * sa[i];
+            if (a == 0.0) continue;
+            for (int j = 0; j < nb; ++j) O[(size_t)i * nb + j] += a * Jb[r * nb + j];
+        }
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nb; ++j) O[(size_t)i * nb + j] *= sb[j];
+    auto clusters = [&](const double *lam, int m) {
+        std::vector<int> ord(m);
+        for (int i = 0; i < m; ++i) ord[i] = i;
+        std::sort(ord.begin(), ord.end(), [&](int x, int y) { return lam[x] < lam[y]; });
+        std::vector<std::vector<int>> cl;
+        for (int t = 0; t < m; ++t) {
+            const int i = ord[t];
+            if (t > 0) {
+                const double p = lam[ord[t - 1]];
+                if (std::fabs(lam[i] - p) <= cluster_tol * std::max({std::fabs(lam[i]), std::fabs(p), 1e-12})) {
+                    cl.back().push_back(i);
+                    continue;
+                }
+            }
+            cl.push_back({i});
+        }
+        return cl;
+    };
+    const auto ca = clusters(lambda_a, na), cb = clusters(lambda_b, nb);
+    struct Pair {
+        double s;
+        int a, b;
+    };
+    std::vector<Pair> pairs;
+    for (int x = 0; x < (int)ca.size(); ++x)
+        for (int y = 0; y < (int)cb.size(); ++y) {
+            double f = 0;
+            for (int i : ca[x])
+                for (int j : cb[y]) f += O[(size_t)i * nb + j] * O[(size_t)i * nb + j];
+            pairs.push_back({f / (double)std::min(ca[x].size(), cb[y].size()), x, y});
+        }
+    std::sort(pairs.begin(), pairs.end(), [](const Pair &u, const Pair &v) { return u.s > v.s; });
+    std::vector<char> used_a(ca.size(), 0), used_b(cb.size(), 0);
+    for (int j = 0; j < nb; ++j) {
+        match[j] = -1;
+        overlap[j] = 0.0;
+    }
+    for (const Pair &pr : pairs) {
+        if (pr.s < 0.5) break;
+        if (used_a[pr.a] || used_b[pr.b]) continue;
+        used_a[pr.a] = used_b[pr.b] = 1;
+        std::vector<int> ia = ca[pr.a], ib = cb[pr.b];
+        while (!ia.empty() && !ib.empty()) {
+            size_t bi = 0, bj = 0;
+            double best = -1;
+            for (size_t u = 0; u < ia.size(); ++u)
+                for (size_t v = 0; v < ib.size(); ++v) {
+                    const double o = std::fabs(O[(size_t)ia[u] * nb + ib[v]]);
+                    if (o > best) { best = o; bi = u; bj = v; }
+                }
+            match[ib[bj]] = ia[bi];
+            ia.erase(ia.begin() + bi);
+            ib.erase(ib.begin() + bj);
+        }
+        for (int j : cb[pr.b]) overlap[j] = std::min(1.0, pr.s);
+    }
+    return MLFMA_OK;
+}

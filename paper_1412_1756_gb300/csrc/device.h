@@ -38,6 +38,18 @@ struct DevNear {
     int max_rows = 0;                    // largest leaf box
 };
 
+// One dense step of the tensor-core interpolation: the image of the step's
+// matrix as the B operand of tcgen05.mma kind::tf32 (N rows of K values,
+// K-major, 128-byte swizzle; TF32 hi part, then the lo part).
+struct UmmaStep {
+    int K = 0;            // contraction length (multiple of 8)
+    int N = 0;            // output columns (multiple of 16)
+    int kr0 = 0;          // theta steps: first K column of the block taken at phi + pi
+    uint32_t kmask = 0;   // bit s set: K-step s (columns 8s .. 8s+7) holds a nonzero coefficient
+    int off = 0;          // byte offset of the hi image in the level's image buffer (lo follows)
+    int bytes = 0;        // bytes of one image: ceil(K / 32) * N * 128
+};
+
 // One stencil tap: source index (theta stencils: bit 30 set = take the
 // sample at phi + pi) and its coefficient.
 template <class R>
@@ -80,12 +92,14 @@ struct DevLevel {
     // anterpolation stencils zero-padded to dn_taps taps per row (16, 20, 24 or 32)
     const Tap<R> *thd_pad = nullptr, *phd_pad = nullptr;
     int dn_taps = 0;
-    // FP32 parents: the interpolation steps as dense matrices for the tensor
-    // cores, in mma.m16n8k8 A-fragment order with a TF32 hi/lo split:
-    // [mtile][ktile][lane][hi a0..a3, lo a0..a3].  theta: [nth][2 child nth]
-    // (second half: samples taken at phi + pi); phi: [nph][child nph].
-    const float *tc_th = nullptr, *tc_ph = nullptr;
-    int tc_mt_th = 0, tc_kt_th = 0, tc_mt_ph = 0, tc_kt_ph = 0;
+    // FP32 parents: the interpolation (up: phi then theta) and anterpolation
+    // (down: theta then phi) steps as dense matrices for the tcgen05 tensor
+    // cores (null where a level's dimensions do not fit the kernels)
+    const unsigned char *um_up = nullptr, *um_dn = nullptr;   // step 1 hi, lo, step 2 hi, lo
+    int um_up_bytes = 0, um_dn_bytes = 0;
+    UmmaStep um_up1, um_up2, um_dn1, um_dn2;
+    int *um_err = nullptr;   // set to 1 by a tensor-core kernel whose bounded wait ran out
+    int um_test = 0;         // test hook: the first CTA of a launch withholds its first arrival
     int up_order = 0;           // taps per forward stencil row (the interpolation order)
     const R *wq = nullptr;               // [K] quadrature weight (leaf: times -k^2 eta / 4 pi)
     R *S = nullptr;                      // outgoing field [nbox][2][K][B]
@@ -139,6 +153,8 @@ struct ProductArgs {
     const int64_t *perm = nullptr;  // [N]
     R *xp = nullptr;                // [N][B] real
     R *yp = nullptr;                // [N][B] complex
+    int *um_err = nullptr;          // set by a tensor-core kernel whose bounded wait ran out
+    int umma = 0;                   // FP32 fields: 0 CUDA-core interpolation; 1 TF32, 3 3xTF32 tensor cores
     DevLevel<R> lv[22];
 };
 
@@ -193,5 +209,13 @@ cudaError_t launch_core_dk(const ProductArgs<R> &a, cudaStream_t s, StageClock *
 // error for a choice that does not apply (the tuner skips it).
 template <class R>
 cudaError_t launch_stage(const ProductArgs<R> &a, int stage, int choice, cudaStream_t s);
+
+// Tensor-core (tcgen05) interpolation and anterpolation of FP32 fields
+// (umma_interp.cu).  cudaErrorInvalidConfiguration, with nothing launched,
+// when the level has no tensor-core tables or does not fit the kernels.
+cudaError_t launch_up_umma(const DevLevel<float> &P, const DevLevel<float> &Ch, int B, int Bs, int acc, bool split,
+                           cudaStream_t s);
+cudaError_t launch_down_umma(const DevLevel<float> &P, const DevLevel<float> &Ch, int B, int Bs, bool split,
+                             cudaStream_t s);
 
 }  // namespace mlfma

@@ -746,189 +746,6 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
     }
 }
 
-// ------------------------------------------------ upward, tensor cores ---
-// A candidate of the autotuner (measured slower than k_up on GB300: the
-// warp-level mma.sync TF32 path runs about one m16n8k8 per 17 cycles per SM
-// here, 2.5-4.6x the CUDA-core kernel's time at B = 64).
-// FP32 only.  Per child, both interpolation steps are dense products on the
-// tensor cores (mma.sync m16n8k8 TF32 with a 3xTF32 hi/lo split, accurate to
-// FP32 rounding): theta  T[t][(v,b)] = sum_k Th[t][k] A[k][(v,b)] with k over
-// the child's theta rows taken at phi and at phi + pi; phi  D[u][(t,b)] =
-// sum_v Ph[u][v] T[t][(v,b)], each (v, b) or (t, b) pair giving two real
-// columns (re, im).  A warp owns a fixed set of phi output tiles and keeps
-// them, times the phase shift, in registers across the children.  One CTA
-// per (parent box, component, 8 columns).  Shared-memory pitches are padded
-// so that the four k rows of a fragment fall on different banks.
-__device__ __forceinline__ uint32_t tf32_rn(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
-{
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};\n"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-// d += A * B with A = ah + al, B = bh + bl (the al * bl term dropped)
-__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const float4 &ah4, const float4 &al4, const float (&bv)[2])
-{
-    uint32_t bh[2], bl[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        bh[i] = tf32_rn(bv[i]);
-        bl[i] = tf32_rn(bv[i] - __uint_as_float(bh[i]));
-    }
-    const uint32_t ah[4] = {__float_as_uint(ah4.x), __float_as_uint(ah4.y), __float_as_uint(ah4.z), __float_as_uint(ah4.w)};
-    const uint32_t al[4] = {__float_as_uint(al4.x), __float_as_uint(al4.y), __float_as_uint(al4.z), __float_as_uint(al4.w)};
-    mma_tf32(d, al, bh);
-    mma_tf32(d, ah, bl);
-    mma_tf32(d, ah, bh);
-}
-
-constexpr int kTcNB = 8;                 // columns per CTA
-constexpr int kTcTV = kTcNB + 4;         // T pitch per (t, v) row, complex
-
-template <int TPW>
-__global__ void __launch_bounds__(256, TPW <= 8 ? 2 : 1) k_up_tc(DevLevel<float> P, DevLevel<float> Ch, int B, int Bs, int accumulate)
-{
-    constexpr int NB = kTcNB, TV = kTcTV;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nthc = Ch.nth, nphc = Ch.nph, hc = nphc / 2, Kc = Ch.K, ntp = P.nth, nphp = P.nph;
-    const int AJ = nphc * NB + 4;                                // child field pitch per theta row, complex
-    float2 *As = reinterpret_cast<float2 *>(smem_raw);           // [nthc][AJ]
-    float2 *Ts = As + (size_t)nthc * AJ;                         // [ntp][nphc][TV]
-    const int p = blockIdx.x, comp = blockIdx.y, b0 = blockIdx.z * NB;
-    const int nb = min(NB, B - b0);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-    const int MTt = P.tc_mt_th, KTt = P.tc_kt_th, MTp = P.tc_mt_ph, KTp = P.tc_kt_ph;
-    const int NTt = nphc * NB / 4;                               // theta n-tiles: 4 (v, b) pairs each
-    const int NTp = ntp * NB / 4;                                // phi n-tiles: 4 (t, b) pairs each
-    const float4 *fth = reinterpret_cast<const float4 *>(P.tc_th);
-    const float4 *fph = reinterpret_cast<const float4 *>(P.tc_ph);
-    float O[TPW][4];
-#pragma unroll
-    for (int i = 0; i < TPW; ++i) O[i][0] = O[i][1] = O[i][2] = O[i][3] = 0.f;
-    const float2 *S = reinterpret_cast<const float2 *>(Ch.S);
-    const float2 *shift = reinterpret_cast<const float2 *>(P.shift);
-    const int bb = threadIdx.x % NB, slot = threadIdx.x / NB, nslot = blockDim.x / NB;
-    const int c0 = P.child_ptr[p], c1 = P.child_ptr[p + 1];
-    for (int c = c0; c < c1; ++c) {
-        // child field -> As (padded theta-row pitch)
-        const float2 *src = S + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + bb;
-#pragma unroll 4
-        for (int qq = slot; qq < Kc; qq += nslot) {
-            const int j = qq / nphc, v = qq - j * nphc;
-            As[j * AJ + v * NB + bb] = bb < nb ? src[(int64_t)qq * Bs] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        // theta step: T = Th * A
-        for (int nt = warp; nt < NTt; nt += 8) {
-            float d[4][4];
-#pragma unroll
-            for (int m = 0; m < 4; ++m) d[m][0] = d[m][1] = d[m][2] = d[m][3] = 0.f;
-            const int pr = nt * 4 + (g >> 1), part = g & 1;     // this lane's B column: pair and re/im
-            const int v = pr / NB, b = pr % NB;
-            const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
-            for (int kt = 0; kt < KTt; ++kt) {
-                float bv[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int k = kt * 8 + q + 4 * h;
-                    float x = 0.f;
-                    if (k < 2 * nthc) {
-                        const int refl = k >= nthc, j = k - refl * nthc;
-                        const float2 a = As[j * AJ + (refl ? vs : v) * NB + b];
-                        x = part ? a.y : a.x;
-                    }
-                    bv[h] = x;
-                }
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    if (m >= MTt) break;
-                    const float4 *fr = fth + (((size_t)m * KTt + kt) * 32 + lane) * 2;
-                    mma_3xtf32(d[m], fr[0], fr[1], bv);
-                }
-            }
-            // D rows t = m*16 + g (+8); columns (2q, 2q+1) = (re, im) of pair nt*4 + q
-            const int pr2 = nt * 4 + q, v2 = pr2 / NB, b2 = pr2 % NB;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                if (m >= MTt) break;
-                const int t = m * 16 + g;
-                if (t < ntp) Ts[(t * nphc + v2) * TV + b2] = make_float2(d[m][0], d[m][1]);
-                if (t + 8 < ntp) Ts[((t + 8) * nphc + v2) * TV + b2] = make_float2(d[m][2], d[m][3]);
-            }
-        }
-        __syncthreads();
-        // phi step and shift, accumulated in registers
-        const float2 *sh = shift + (int64_t)Ch.octant[c] * P.K;
-#pragma unroll
-        for (int i = 0; i < TPW; ++i) {
-            const int it = warp + 8 * i;
-            if (it >= MTp * NTp) break;
-            const int mp = it / NTp, np = it - mp * NTp;
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-            const int pr = np * 4 + (g >> 1), part = g & 1;
-            const int t = pr / NB, b = pr % NB;
-            for (int kt = 0; kt < KTp; ++kt) {
-                float bv[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int v = kt * 8 + q + 4 * h;
-                    float x = 0.f;
-                    if (v < nphc && t < ntp) {
-                        const float2 a = Ts[(t * nphc + v) * TV + b];
-                        x = part ? a.y : a.x;
-                    }
-                    bv[h] = x;
-                }
-                const float4 *fr = fph + (((size_t)mp * KTp + kt) * 32 + lane) * 2;
-                mma_3xtf32(d, fr[0], fr[1], bv);
-            }
-            const int pr2 = np * 4 + q, t2 = pr2 / NB;
-            const int u = mp * 16 + g;
-            if (t2 < ntp) {
-                if (u < nphp) {
-                    const float2 z = sh[t2 * nphp + u];
-                    O[i][0] += z.x * d[0] - z.y * d[1];
-                    O[i][1] += z.x * d[1] + z.y * d[0];
-                }
-                if (u + 8 < nphp) {
-                    const float2 z = sh[t2 * nphp + u + 8];
-                    O[i][2] += z.x * d[2] - z.y * d[3];
-                    O[i][3] += z.x * d[3] + z.y * d[2];
-                }
-            }
-        }
-        __syncthreads();
-    }
-    float2 *dst = reinterpret_cast<float2 *>(P.S) + ((int64_t)p * 2 + comp) * P.K * Bs + b0;
-#pragma unroll
-    for (int i = 0; i < TPW; ++i) {
-        const int it = warp + 8 * i;
-        if (it >= MTp * NTp) break;
-        const int mp = it / NTp, np = it - mp * NTp;
-        const int pr2 = np * 4 + q, t2 = pr2 / NB, b2 = pr2 % NB;
-        const int u = mp * 16 + g;
-        if (t2 >= ntp || b2 >= nb) continue;
-        for (int h = 0; h < 2; ++h) {
-            const int uu = u + 8 * h;
-            if (uu >= nphp) continue;
-            float2 *o = dst + (int64_t)(t2 * nphp + uu) * Bs + b2;
-            float2 val = make_float2(O[i][2 * h], O[i][2 * h + 1]);
-            if (accumulate) {
-                const float2 y = *o;
-                val.x += y.x;
-                val.y += y.y;
-            }
-            *o = val;
-        }
-    }
-}
-
 // --------------------------------------------------------- downward ---
 // One CTA per (child box, component, chunk of NB columns).  At entry both the
 // parent's incoming field and the child's own are requested with
@@ -1660,34 +1477,12 @@ int column_chunk(int B, size_t per_col_bytes)
 }
 
 // B columns of fields with row stride Bs; acc: add into the parent field
-// Tensor-core up pass (FP32): tiles per warp, shared memory
-template <class R>
-cudaError_t launch_up_tc(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, int acc, cudaStream_t s)
-{
-    if constexpr (sizeof(R) != 4) {
-        return cudaErrorInvalidConfiguration;
-    } else {
-        if (!P.tc_th || !P.tc_ph || P.tc_mt_th > 4) return cudaErrorInvalidConfiguration;
-        const int tiles = P.tc_mt_ph * (P.nth * kTcNB / 4);
-        const int tpw = (tiles + 7) / 8;
-        const size_t smem = ((size_t)Ch.nth * (Ch.nph * kTcNB + 4) + (size_t)P.nth * Ch.nph * kTcTV) * sizeof(float2);
-        if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
-        dim3 grid(P.nbox, 2, (B + kTcNB - 1) / kTcNB);
-        if (tpw <= 8) k_up_tc<8><<<grid, 256, smem, s>>>(P, Ch, B, Bs, acc);
-        else if (tpw <= 16) k_up_tc<16><<<grid, 256, smem, s>>>(P, Ch, B, Bs, acc);
-        else if (tpw <= 24) k_up_tc<24><<<grid, 256, smem, s>>>(P, Ch, B, Bs, acc);
-        else return cudaErrorInvalidConfiguration;
-        return cudaGetLastError();
-    }
-}
-
 template <class R>
 cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, int acc, cudaStream_t s,
                       int nb_choice = 0)
 {
     using C = typename Cx<R>::T;
     const int order = P.up_order;
-    if (nb_choice == 100) return launch_up_tc<R>(P, Ch, B, Bs, acc, s);   // a tuner candidate, not the default
     int nb = column_chunk<R>(B, ((size_t)Ch.K + (size_t)P.nth * (Ch.nph + P.nph)) * sizeof(C));
     if (nb_choice) {
         if (nb_choice > 16 || (nb_choice & (nb_choice - 1)) || nb_choice > std::max(1, B)) return cudaErrorInvalidConfiguration;
@@ -1833,7 +1628,6 @@ cudaError_t prime_kernels()
     ALLOW((k_near<R, 1, true>)); ALLOW((k_near<R, 2, true>)); ALLOW((k_near<R, 4, true>));
     ALLOW((k_near<R, 8, true>)); ALLOW((k_near<R, 16, true>));
     ALLOW((k_near_wide<R, 8>)); ALLOW((k_near_wide<R, 16>));
-    if (sizeof(R) == 4) { ALLOW((k_up_tc<8>)); ALLOW((k_up_tc<16>)); ALLOW((k_up_tc<24>)); }
     ALLOW((k_down_pp<R, 4, 16>)); ALLOW((k_down_pp<R, 4, 20>)); ALLOW((k_down_pp<R, 8, 16>)); ALLOW((k_down_pp<R, 8, 20>));
     ALLOW(k_radiate<R>);
     ALLOW(k_radiate_wide<R>);
@@ -1875,6 +1669,32 @@ inline cudaError_t tick(StageClock *clk, int stage, cudaStream_t s)
 }
 }  // namespace
 
+// One level of the up / down pass: the tensor-core kernels when the product
+// asks for them and the level fits, else the CUDA-core kernels.
+template <class R>
+cudaError_t up_level(const ProductArgs<R> &a, int l, int B, cudaStream_t s, int choice)
+{
+    if constexpr (sizeof(R) == 4) {
+        if (a.umma) {
+            cudaError_t e = launch_up_umma(a.lv[l], a.lv[l + 1], B, B, 0, a.umma == 3, s);
+            if (e != cudaErrorInvalidConfiguration) return e;
+        }
+    }
+    return launch_up<R>(a.lv[l], a.lv[l + 1], B, B, 0, s, choice);
+}
+
+template <class R>
+cudaError_t down_level(const ProductArgs<R> &a, int l, int B, cudaStream_t s, int choice)
+{
+    if constexpr (sizeof(R) == 4) {
+        if (a.umma) {
+            cudaError_t e = launch_down_umma(a.lv[l], a.lv[l + 1], B, B, a.umma == 3, s);
+            if (e != cudaErrorInvalidConfiguration) return e;
+        }
+    }
+    return launch_down<R>(a.lv[l], a.lv[l + 1], B, B, s, choice);
+}
+
 template <class R>
 cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClock *clk)
 {
@@ -1903,7 +1723,7 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
         TRY(launch_translate<R>(a.lv[leaf], B, B, 0, st, tu.tr[leaf]));
         TRY(tick(clk, STAGE_TRANSLATE + leaf, st));
         for (int l = leaf - 1; l >= top; --l) {
-            TRY(launch_up<R>(a.lv[l], a.lv[l + 1], B, B, 0, sf, tu.up_nb[l]));
+            TRY(up_level<R>(a, l, B, sf, tu.up_nb[l]));
             TRY(tick(clk, STAGE_UP + l, sf));
             if (l == top) {
                 TRY(launch_translate<R>(a.lv[l], B, B, 0, sf, tu.tr[l]));
@@ -1922,7 +1742,7 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
             TRY(cudaStreamWaitEvent(sf, cs.ev[2], 0));
         }
         for (int l = top; l < leaf; ++l) {
-            TRY(launch_down<R>(a.lv[l], a.lv[l + 1], B, B, sf, tu.down_nb[l]));
+            TRY(down_level<R>(a, l, B, sf, tu.down_nb[l]));
             TRY(tick(clk, STAGE_DOWN + l, sf));
         }
         if (!serial) {

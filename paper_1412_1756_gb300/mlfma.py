@@ -15,6 +15,8 @@ from . import _build
 
 FP64 = 0
 FP32 = 1
+MIXED_TF32 = 2      # FP32 product, tensor-core (TF32) interpolation
+MIXED_3XTF32 = 3    # FP32 product, tensor-core (3xTF32 split) interpolation
 MAX_LEVELS = 22
 
 (X_PERM, X_LEAF_BOX, X_GRID, X_ALPHA, X_ALPHA_OFFS, X_INTERP, X_BOX_CENTERS, X_NEAR_COUNT, X_ANTERP, X_ALPHA_J,
@@ -26,7 +28,7 @@ EXPORTED = ["mlfma_default_opts", "mlfma_plan", "mlfma_num_unknowns", "mlfma_rwg
             "mlfma_matvec_adjoint", "mlfma_matvec_dk", "mlfma_matvec_dk_adjoint", "mlfma_matvec_x",
             "mlfma_matvec_r", "mlfma_matvec_host", "mlfma_sync", "mlfma_plan_info", "mlfma_export",
             "mlfma_profile_stages", "mlfma_export_field", "mlfma_tune", "mlfma_tune_get", "mlfma_tune_set", "mlfma_matvec_noalloc", "mlfma_cm_default_opts", "cm_ira_solve", "cm_block_solve", "cm_rayleigh_ritz",
-            "cm_eig_derivatives",
+            "cm_eig_derivatives", "cm_track_modes",
             "mlfma_set_create", "mlfma_set_matvec", "mlfma_set_info", "mlfma_set_plan", "mlfma_set_destroy",
             "mlfma_destroy", "mlfma_last_error"]
 CM_ZINV_R, CM_XINV_R = 0, 1
@@ -105,6 +107,7 @@ def load(build_if_missing: bool = False):
     L.cm_block_solve.argtypes = [P, ctypes.POINTER(CmOpts), P, P, ctypes.POINTER(CmStats)]
     L.cm_rayleigh_ritz.argtypes = [I64, I, P, P, P, P, P, ctypes.POINTER(I)]
     L.cm_eig_derivatives.argtypes = [P, I, P, P, I, P]
+    L.cm_track_modes.argtypes = [I64, I, P, P, I, P, P, ctypes.c_double, P, P]
     L.mlfma_plan_info.argtypes = [P, ctypes.POINTER(Info)]
     L.mlfma_export.argtypes = [P, I, I, P, I64, ctypes.POINTER(I64)]
     L.mlfma_destroy.argtypes = [P]
@@ -228,7 +231,7 @@ class MlfmaPlan:
             return FP64
         raise TypeError("x must be float32/float64/complex64/complex128, got %s" % dtype)
 
-    def _product(self, fn, x, y, stream):
+    def _product(self, fn, x, y, stream, prec=None):
         import torch
         if not x.is_cuda:
             raise ValueError("x must be a CUDA tensor (use matvec_host for host arrays)")
@@ -237,9 +240,14 @@ class MlfmaPlan:
         if x2.dim() != 2 or x2.shape[0] != self.n:
             raise ValueError("x must be [N] or [N, B] with N = %d" % self.n)
         x2 = x2.contiguous()
-        prec = self._prec_of(x2.dtype)
+        dprec = self._prec_of(x2.dtype)
+        if prec in (MIXED_TF32, MIXED_3XTF32):
+            if dprec != FP32:
+                raise TypeError("the TF32 precisions take float32 / complex64 x")
+        else:
+            prec = dprec
         xc = 1 if x2.is_complex() else 0
-        cdt = torch.complex64 if prec == FP32 else torch.complex128
+        cdt = torch.complex128 if prec == FP64 else torch.complex64
         B = x2.shape[1]
         if y is None:
             y = torch.empty((self.n, B), dtype=cdt, device=x2.device)
@@ -250,13 +258,15 @@ class MlfmaPlan:
                   ctypes.c_void_p(s)))
         return y.reshape(self.n) if squeeze else y.reshape(self.n, B)
 
-    def matvec(self, x, y=None, stream=None):
-        """y = Z x for a CUDA tensor x [N] or [N, B] (real or complex)."""
-        return self._product(self._lib.mlfma_matvec, x, y, stream)
+    def matvec(self, x, y=None, stream=None, prec=None):
+        """y = Z x for a CUDA tensor x [N] or [N, B] (real or complex).  The
+        precision follows x's dtype; prec = MIXED_TF32 or MIXED_3XTF32 (with
+        float32 / complex64 x) selects tensor-core interpolation."""
+        return self._product(self._lib.mlfma_matvec, x, y, stream, prec)
 
-    def matvec_adjoint(self, x, y=None, stream=None):
+    def matvec_adjoint(self, x, y=None, stream=None, prec=None):
         """y = Z^H x."""
-        return self._product(self._lib.mlfma_matvec_adjoint, x, y, stream)
+        return self._product(self._lib.mlfma_matvec_adjoint, x, y, stream, prec)
 
     def _dk_product(self, fn, x, y, stream):
         # value and tangent fields share the plan's field buffers: at most
@@ -292,8 +302,8 @@ class MlfmaPlan:
 
     def matvec_host(self, x: np.ndarray, prec: int = FP32, y: np.ndarray = None, stream=None) -> np.ndarray:
         """y = Z x for HOST arrays (copies inside the call; waits for completion)."""
-        rdt = np.float32 if prec == FP32 else np.float64
-        cdt = np.complex64 if prec == FP32 else np.complex128
+        rdt = np.float64 if prec == FP64 else np.float32
+        cdt = np.complex128 if prec == FP64 else np.complex64
         squeeze = x.ndim == 1
         x2 = x.reshape(self.n, -1)
         xc = 1 if np.iscomplexobj(x2) else 0
@@ -356,12 +366,12 @@ class MlfmaPlan:
         c = np.ascontiguousarray(choices, dtype=np.int32).reshape(TUNE_FIELDS)
         _check(self._lib.mlfma_tune_set(self._h, int(B), 1 if complex_x else 0, int(prec), _np_ptr(c)))
 
-    def profile_stages(self, x, y=None, stream=None) -> dict:
+    def profile_stages(self, x, y=None, stream=None, prec=None) -> dict:
         """Serial per-stage device times (ms) of one product (measurement aid)."""
         import torch
         ms = np.zeros(STAGE_COUNT)
         fn = lambda h, xp, xc, yp, B, prec, s: self._lib.mlfma_profile_stages(h, xp, xc, yp, B, prec, s, _np_ptr(ms))
-        self._product(fn, x, y, stream)
+        self._product(fn, x, y, stream, prec)
         out = {"prepare": ms[0], "near": ms[1], "radiate": ms[2], "receive": ms[69], "finalize": ms[70]}
         for l in range(22):
             if ms[3 + l]:
@@ -456,6 +466,24 @@ def rayleigh_ritz(Y, RY, W):
     _check(L.cm_rayleigh_ritz(n, p, _np_ptr(Y), _np_ptr(RY), _np_ptr(W), _np_ptr(mu), _np_ptr(coef),
                               ctypes.byref(r)))
     return mu[:r.value], coef[:, :r.value]
+
+
+def track_modes(lam_a, Ja, lam_b, Jb, cluster_tol=1e-2):
+    """Pair the modes (lam_b, Jb) with the previous wavenumber's (lam_a, Ja)
+    (cm_track_modes): returns (match [nb] indices into set a or -1,
+    overlap [nb] cluster-pair scores)."""
+    L = load()
+    la = np.ascontiguousarray(lam_a, dtype=np.float64)
+    lb = np.ascontiguousarray(lam_b, dtype=np.float64)
+    A = np.ascontiguousarray(Ja, dtype=np.float64)
+    Bm = np.ascontiguousarray(Jb, dtype=np.float64)
+    if A.ndim != 2 or Bm.ndim != 2 or A.shape[0] != Bm.shape[0] or A.shape[1] != la.size or Bm.shape[1] != lb.size:
+        raise ValueError("Ja [n][na], Jb [n][nb] with matching value counts")
+    match = np.zeros(lb.size, np.int32)
+    ov = np.zeros(lb.size)
+    _check(L.cm_track_modes(A.shape[0], la.size, _np_ptr(la), _np_ptr(A), lb.size, _np_ptr(lb), _np_ptr(Bm),
+                            float(cluster_tol), _np_ptr(match), _np_ptr(ov)))
+    return match, ov
 
 
 def tune_cache_key(gpu_name, info, interp_order, B, prec, complex_x) -> str:
