@@ -78,3 +78,29 @@ def test_sphere_two_million_nine_levels():
     assert _rel(yd, prob.rows_dk(idx) @ x) < 3e-2
     P.close()
     torch.cuda.empty_cache()
+
+
+def test_sphere_two_million_eight_levels():
+    """The 1,966,080-unknown sphere at 8 levels (0.125 wavelength leaves, the
+    depth at which the 3-digit expansion still holds): forward, adjoint and
+    dZ/dk products of 16 columns (FP32) on 16 sampled exact oracle rows, each
+    within the 1e-3 bound of the product."""
+    W = workloads.get("sphere-r8m-ico8-8lv")
+    v, t = W.mesh()
+    P = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=32, precisions=(M.FP32,))
+    idx = np.random.default_rng(8).choice(P.n, 16, replace=False)
+    prob = efie.Problem(v, t, W.k)
+    x = workloads.rhs(P.n, 16, W.seed)
+    xd = torch.from_numpy(x).to("cuda", torch.float32)
+    rows = prob.rows(idx)
+    e = _rel(P.matvec(xd).cpu().numpy()[idx], rows @ x)
+    assert e < 1e-3, e
+    xc = workloads.rhs_complex(P.n, 8, W.seed)
+    ya = P.matvec_adjoint(torch.from_numpy(xc).to("cuda", torch.complex64)).cpu().numpy()[idx]
+    ea = _rel(ya, rows.conj() @ xc)
+    assert ea < 1e-3, ea
+    del rows
+    ed = _rel(P.matvec_dk(xd).cpu().numpy()[idx], prob.rows_dk(idx) @ x)
+    assert ed < 1e-3, ed
+    P.close()
+    torch.cuda.empty_cache()

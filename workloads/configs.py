@@ -56,6 +56,11 @@ WORKLOADS = {
     "sphere-r8m-ico8": Workload("sphere-r8m-ico8", lambda: meshes.icosphere(8, 8.0),
                                 TWO_PI, 9, 3.0, 16, 1412175605,
                                 "PEC sphere r=8 m, wavelength 1 m", 1966080),
+    # the same sphere with 8 levels (0.125 wavelength leaves): the depth at
+    # which Eq. (9) with d0 = 3 still delivers about 3 digits
+    "sphere-r8m-ico8-8lv": Workload("sphere-r8m-ico8-8lv", lambda: meshes.icosphere(8, 8.0),
+                                    TWO_PI, 8, 3.0, 16, 1412175605,
+                                    "PEC sphere r=8 m, 8 levels", 1966080),
     # small sphere for fast tests: 320 triangles / 480 RWG
     "sphere-r0.5m-ico2": Workload("sphere-r0.5m-ico2", lambda: meshes.icosphere(2, 0.5),
                                   TWO_PI, 3, 3.0, 4, 1412175606,
