@@ -60,6 +60,8 @@ def parse():
                     help="JSON file of tuned launch shapes: reuse an entry for this GPU and tree, else tune and store")
     ap.add_argument("--stages-only", action="store_true",
                     help="build the plan and run one serial per-stage pass (for profilers), print stage times")
+    ap.add_argument("--precision", choices=["fp32", "3xtf32", "tf32"], default="fp32",
+                    help="precision of the --stages-only pass")
     return ap.parse_args()
 
 
@@ -167,19 +169,11 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-# DRAM bytes (read + write) per launch measured by ncu at this workload and
-# B = 64: {(stage, kernel source digest): bytes}.  Summaries in profiles/.
+# DRAM bytes (read + write) per launch of the dominant stage measured by ncu
+# at B = 64: {(workload, stage, kernel source digest): bytes}.  Summaries in
+# profiles/ (k_down_cube8m-6lv_B64.md).
 NCU_TRAFFIC = {
-    ("near", "53cc9ae71ce75206"): 108_645_632 + 4_603_904,
-    ("radiate", "53cc9ae71ce75206"): 90_378_752 + 133_051_904,
-    ("translate4", "53cc9ae71ce75206"): 193_549_056 + 156_163_328,
-    ("up3", "53cc9ae71ce75206"): 232_115_712 + 82_766_848,
-    ("translate3", "53cc9ae71ce75206"): 110_322_944 + 71_647_744,
-    ("up2", "53cc9ae71ce75206"): 111_794_176 + 25_882_880,
-    ("translate2", "53cc9ae71ce75206"): 52_891_904 + 7_876_864,
-    ("down2", "53cc9ae71ce75206"): 162_190_080 + 60_851_200,
-    ("down3", "53cc9ae71ce75206"): 301_853_440 + 143_796_992,
-    ("receive", "53cc9ae71ce75206"): 367_722_752 + 12_132_096,
+    ("cube8m-6lv", "down4", "5aff218f72d724e6"): 4_822_725_000 + 1_676_389_000,
 }
 
 
@@ -322,8 +316,11 @@ def main():
         if not a.no_tune:
             plan.tune(B, FP32, cache=a.tune_cache)
         torch.cuda.synchronize()
+        pr = dict(modes)[a.precision]
+        plan.profile_stages(xs, prec=pr)           # first use: graph-free set-up of this precision
+        torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("profile")   # profilers can select this pass (ncu --nvtx-include profile/)
-        st = plan.profile_stages(xs)
+        st = plan.profile_stages(xs, prec=pr)
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"stage_ms": st}))
         return
@@ -382,7 +379,9 @@ def main():
     with ClockSampler(local) as clk:
         torch.cuda.nvtx.range_push("timed")   # profilers can select the timed products (ncu --nvtx-include timed/)
         for name, pr in modes:
+            torch.cuda.nvtx.range_push(name)  # one precision: ncu --nvtx-include timed/fp32/
             ms_m = timed(lambda: plan.matvec(x32, y32, prec=pr), a.steps, a.warmup)
+            torch.cuda.nvtx.range_pop()
             runs[name] = {"ms_per_step": ms_m / a.steps, "value": replica_rate(B, a.steps, ms_m / 1e3, world),
                           "err_vs_oracle": oracle_err(y32)}
         torch.cuda.nvtx.range_pop()
@@ -433,7 +432,7 @@ def main():
     hbm_peak, peak_src = peaks()
     abytes, aflops = algorithmic(info, B, dom)
     dom_ms = stages[dom]
-    traffic = NCU_TRAFFIC.get((dom, kernel_digest()))
+    traffic = NCU_TRAFFIC.get((wl.name, dom, kernel_digest()))
     if dom.startswith("translate"):
         # diagonal complex products over the interaction lists: FP32 ALU-bound
         clk = clocks.get("sm_mhz") or 2070.0
