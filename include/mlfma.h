@@ -243,10 +243,13 @@ mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec
  *       3 chunks of 16 columns
  *   [1] radiation: 1 one CTA per box, 2 / 3 / 4 tiles of 32 / 16 / 8 columns
  *   [2] reception: 1 / 2 / 3 tiles of 32 / 16 / 8 columns
- *   [3 + l]       up pass into level l: columns per CTA 1..16, or 100 for the
- *                 tensor-core (mma.sync 3xTF32, FP32 only) variant
+ *   [3 + l]       up pass into level l: columns per CTA 1..16, or 202 / 204 /
+ *                 208 / 216 with 2 / 4 / 8 / 16 columns and the interpolation
+ *                 rows taken in pairs (FP32 only)
  *   [3 + 22 + l]  down pass from level l: columns per CTA 1..16 (one CTA per
- *                 child), or 104 / 108 one CTA per parent with 4 / 8 columns
+ *                 child), 104 / 108 one CTA per parent with 4 / 8 columns, or
+ *                 204 / 208 / 216 one CTA per child with 4 / 8 / 16 columns and
+ *                 the anterpolation rows taken in pairs (FP32 only)
  *   [3 + 44 + l]  translation at level l: 1 two columns per thread; 2..6 one
  *                 column with 1, 2, 4, 8, 16 lanes per output; 7 / 8 one warp
  *                 per (child, sample) with 2 / 1 columns per lane

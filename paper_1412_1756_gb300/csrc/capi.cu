@@ -310,6 +310,59 @@ cudaError_t upload_parent_tables(DevMem &M, const PlanHost &H, const Level &Lv, 
     };
     if ((e = M.upload(pad(Lv.th_dn), &D.thd_pad)) != cudaSuccess) return e;
     if ((e = M.upload(pad(Lv.ph_dn), &D.phd_pad)) != cudaSuccess) return e;
+    // rows in pairs: per pair the union of both rows' taps (source index with
+    // the reflection bit), one coefficient per row, zero-padded to dn2_taps
+    auto pairs = [&](const Stencil &st, std::vector<std::map<int32_t, std::pair<double, double>>> &out) {
+        const int rows = (int)st.ptr.size() - 1;
+        out.assign((rows + 1) / 2, {});
+        for (int r = 0; r < rows; ++r)
+            for (int e2 = st.ptr[r]; e2 < st.ptr[r + 1]; ++e2) {
+                const int32_t key = st.idx[e2] | ((!st.refl.empty() && st.refl[e2]) ? kTapRefl : 0);
+                auto &cc = out[r / 2][key];
+                (r % 2 ? cc.second : cc.first) += st.coef[e2];
+            }
+    };
+    auto pack2 = [&](const std::vector<std::map<int32_t, std::pair<double, double>>> &v, int taps) {
+        std::vector<Tap2<R>> t(v.size() * (size_t)taps, Tap2<R>{0, {(R)0, (R)0}});
+        for (size_t b = 0; b < v.size(); ++b) {
+            int f = 0;
+            for (const auto &kv : v[b]) {
+                Tap2<R> &tp = t[b * taps + f++];
+                tp.i = kv.first;
+                tp.c[0] = (R)kv.second.first;
+                tp.c[1] = (R)kv.second.second;
+            }
+        }
+        return t;
+    };
+    auto widest = [](const std::vector<std::map<int32_t, std::pair<double, double>>> &a,
+                     const std::vector<std::map<int32_t, std::pair<double, double>>> &b) {
+        size_t w = 0;
+        for (const auto *v : {&a, &b})
+            for (const auto &m : *v) w = std::max(w, m.size());
+        return w;
+    };
+    std::vector<std::map<int32_t, std::pair<double, double>>> pth, pph, puth, puph;
+    pairs(Lv.th_dn, pth);
+    pairs(Lv.ph_dn, pph);
+    const size_t wd = widest(pth, pph);
+    D.dn2_taps = 0;
+    for (int tm : {16, 20, 24})
+        if (!D.dn2_taps && wd <= (size_t)tm) D.dn2_taps = tm;
+    if (D.dn2_taps) {
+        if ((e = M.upload(pack2(pth, D.dn2_taps), &D.thd2)) != cudaSuccess) return e;
+        if ((e = M.upload(pack2(pph, D.dn2_taps), &D.phd2)) != cudaSuccess) return e;
+    }
+    pairs(Lv.th_up, puth);
+    pairs(Lv.ph_up, puph);
+    const size_t wu = widest(puth, puph);
+    D.up2_taps = 0;
+    for (int tm : {12, 16})
+        if (!D.up2_taps && wu <= (size_t)tm) D.up2_taps = tm;
+    if (D.up2_taps) {
+        if ((e = M.upload(pack2(puth, D.up2_taps), &D.thu2)) != cudaSuccess) return e;
+        if ((e = M.upload(pack2(puph, D.up2_taps), &D.phu2)) != cudaSuccess) return e;
+    }
     return upload_tc_tables<R>(M, H, Lv, D, err);
 }
 
@@ -794,8 +847,8 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
         for (int l = a.coarsest; l <= a.leaf; ++l) {
             pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6, 7, 8}, best.tr[l]);
             if (l < a.leaf) {
-                pick(STAGE_UP + l, {1, 2, 4, 8, 16}, best.up_nb[l]);
-                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108}, best.down_nb[l]);
+                pick(STAGE_UP + l, {1, 2, 4, 8, 16, 202, 204, 208, 216}, best.up_nb[l]);
+                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108, 204, 208, 216}, best.down_nb[l]);
             }
         }
     }
@@ -1306,7 +1359,7 @@ mlfma_status mlfma_tune_set(mlfma_plan_t p, int64_t B, int xc, int prec, const i
                   choices[2] >= 0 && choices[2] <= 3;
         for (int l = 0; l < MLFMA_MAX_LEVELS && ok; ++l) {
             const int u = choices[3 + l], d = choices[3 + MLFMA_MAX_LEVELS + l], r = choices[3 + 2 * MLFMA_MAX_LEVELS + l];
-            ok = (u == 0 || pow2(u)) && (d == 0 || pow2(d) || d == 104 || d == 108) && r >= 0 && r <= 8;
+            ok = (u == 0 || pow2(u) || u == 202 || u == 204 || u == 208 || u == 216) && (d == 0 || pow2(d) || d == 104 || d == 108 || d == 204 || d == 208 || d == 216) && r >= 0 && r <= 8;
         }
         if (!ok) return fail(MLFMA_EINVAL, "a launch-shape choice is outside its documented set");
     }

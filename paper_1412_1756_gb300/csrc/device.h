@@ -50,6 +50,14 @@ struct UmmaStep {
     int bytes = 0;        // bytes of one image: ceil(K / 32) * N * 128
 };
 
+// One tap shared by a pair of stencil rows: source index (as in Tap) and the
+// coefficient of each row (zero where the tap is not one of that row's).
+template <class R>
+struct Tap2 {
+    int32_t i;
+    R c[2];
+};
+
 // One stencil tap: source index (theta stencils: bit 30 set = take the
 // sample at phi + pi) and its coefficient.
 template <class R>
@@ -89,9 +97,18 @@ struct DevLevel {
     const int32_t *phd_ptr = nullptr, *phd_idx = nullptr;
     const R *phd_c = nullptr;
     const Tap<R> *thu = nullptr, *phu = nullptr, *thd = nullptr, *phd = nullptr;   // packed taps
+    // the interpolation stencils with the rows in pairs: per pair the union of
+    // both rows' taps, one coefficient per row, zero-padded to up2_taps entries
+    // (0: not built)
+    const Tap2<R> *thu2 = nullptr, *phu2 = nullptr;
+    int up2_taps = 0;
     // anterpolation stencils zero-padded to dn_taps taps per row (16, 20, 24 or 32)
     const Tap<R> *thd_pad = nullptr, *phd_pad = nullptr;
     int dn_taps = 0;
+    // the same with the rows in pairs: per pair the union of both rows' taps
+    // with one coefficient per row, zero-padded to dn2_taps entries (0: not built)
+    const Tap2<R> *thd2 = nullptr, *phd2 = nullptr;
+    int dn2_taps = 0;
     // FP32 parents: the interpolation (up: phi then theta) and anterpolation
     // (down: theta then phi) steps as dense matrices for the tcgen05 tensor
     // cores (null where a level's dimensions do not fit the kernels)

@@ -617,7 +617,17 @@ struct SplitIL {
 // accumulated into the band's outputs in shared memory; one store of the
 // parent field at the end.  In each stencil step a thread holds the PO taps
 // of one stencil row in registers and applies them to a chunk of rows.
-template <class R, int NB, int PO>
+// Parent theta rows per band of a CTA (even when the rows go in pairs).
+__host__ __device__ inline int up_band_rows(int ntp, int RS, int RB)
+{
+    const int rows = (ntp + RS - 1) / RS;
+    return RB == 2 ? rows + (rows & 1) : rows;
+}
+
+// RB = 2: the interpolation rows go in pairs (tables thu2 / phu2: the union of
+// both rows' taps, PO entries, one coefficient per row), so each value a
+// thread loads from shared memory feeds both rows of the pair.
+template <class R, int NB, int PO, int RB = 1>
 __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B, int RS, int Bs, int accumulate)
 {
     using C = typename Cx<R>::T;
@@ -628,7 +638,7 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
     const int p = blockIdx.x, comp = blockIdx.y;
     const int nbc = (B + NB - 1) / NB;
     const int b0 = (blockIdx.z % nbc) * NB, rs = blockIdx.z / nbc;
-    const int rows = (ntp + RS - 1) / RS, t0 = rs * rows, t1 = min(ntp, t0 + rows);
+    const int rows = up_band_rows(ntp, RS, RB), t0 = rs * rows, t1 = min(ntp, t0 + rows);
     if (t0 >= t1) return;
     const int nr = t1 - t0;
     const int nb = min(NB, B - b0);
@@ -641,8 +651,8 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
     const C *S = reinterpret_cast<const C *>(Ch.S);
     const C *shift = reinterpret_cast<const C *>(P.shift) + (int64_t)t0 * nphp;
     for (int e = threadIdx.x; e < nO * PW; e += blockDim.x) O[e] = C{0, 0};
-    const SplitIL st(nr, NL);          // theta step: key = band theta row, rows = child phi index
-    const Split sp(nphp, nr, NL);      // phi step: key = parent phi index, span = band theta rows
+    const SplitIL st((nr + RB - 1) / RB, NL);   // theta step: key = band theta row (pair), rows = child phi index
+    const Split sp(nphp / RB, nr, NL);          // phi step: key = parent phi index (pair), span = band theta rows
     const int c0 = P.child_ptr[p], c1 = P.child_ptr[p + 1];
     C pre[PF];
     auto fetch = [&](int c) {
@@ -672,27 +682,42 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
             st.item(it, CP, key, cg, ch);
             int tb[PO];
             bool rf[PO];
-            R tc[PO];
+            R tc[RB][PO];
 #pragma unroll
             for (int f = 0; f < PO; ++f) {
-                const Tap<R> tap = P.thu[(size_t)(t0 + key) * PO + f];
-                tb[f] = (tap.i & (kTapRefl - 1)) * nphc;
-                rf[f] = (tap.i & kTapRefl) != 0;
-                tc[f] = tap.c;
+                int ti;
+                if constexpr (RB == 1) {
+                    const Tap<R> tap = P.thu[(size_t)(t0 + key) * PO + f];
+                    ti = tap.i;
+                    tc[0][f] = tap.c;
+                } else {
+                    const Tap2<R> tap = P.thu2[(size_t)(t0 / 2 + key) * PO + f];
+                    ti = tap.i;
+                    tc[0][f] = tap.c[0];
+                    tc[1][f] = tap.c[1];
+                }
+                tb[f] = (ti & (kTapRefl - 1)) * nphc;
+                rf[f] = (ti & kTapRefl) != 0;
             }
             for (int v = ch; v < nphc; v += st.chunks) {
                 const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
-                C s[CP];
+                C s[RB][CP];
 #pragma unroll
-                for (int k = 0; k < CP; ++k) s[k] = C{0, 0};
+                for (int r = 0; r < RB; ++r)
+#pragma unroll
+                    for (int k = 0; k < CP; ++k) s[r][k] = C{0, 0};
 #pragma unroll
                 for (int f = 0; f < PO; ++f) {
                     C a[CP];
                     lds_cols<C, CP>(A + (tb[f] + (rf[f] ? vs : v)) * PW + cg, a);
 #pragma unroll
-                    for (int k = 0; k < CP; ++k) rfma(s[k], tc[f], a[k]);
+                    for (int r = 0; r < RB; ++r)
+#pragma unroll
+                        for (int k = 0; k < CP; ++k) rfma(s[r][k], tc[r][f], a[k]);
                 }
-                sts_cols<C, CP>(T + (key * nphc + v) * PW + cg, s);
+#pragma unroll
+                for (int r = 0; r < RB; ++r)
+                    if (key * RB + r < nr) sts_cols<C, CP>(T + ((key * RB + r) * nphc + v) * PW + cg, s[r]);
             }
         }
         __syncthreads();
@@ -701,32 +726,46 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
             int key, cg, lo, hi;
             sp.item(it, NL, CP, nr, key, cg, lo, hi);
             int pb[PO];
-            R pc[PO];
+            R pc[RB][PO];
 #pragma unroll
             for (int f = 0; f < PO; ++f) {
-                const Tap<R> tap = P.phu[(size_t)key * PO + f];
-                pb[f] = tap.i;
-                pc[f] = tap.c;
+                if constexpr (RB == 1) {
+                    const Tap<R> tap = P.phu[(size_t)key * PO + f];
+                    pb[f] = tap.i;
+                    pc[0][f] = tap.c;
+                } else {
+                    const Tap2<R> tap = P.phu2[(size_t)key * PO + f];
+                    pb[f] = tap.i;
+                    pc[0][f] = tap.c[0];
+                    pc[1][f] = tap.c[1];
+                }
             }
             for (int tr = lo; tr < hi; ++tr) {
                 const C *trow = T + tr * nphc * PW + cg;
-                C s[CP];
+                C s[RB][CP];
 #pragma unroll
-                for (int k = 0; k < CP; ++k) s[k] = C{0, 0};
+                for (int r = 0; r < RB; ++r)
+#pragma unroll
+                    for (int k = 0; k < CP; ++k) s[r][k] = C{0, 0};
 #pragma unroll
                 for (int f = 0; f < PO; ++f) {
                     C a[CP];
                     lds_cols<C, CP>(trow + pb[f] * PW, a);
 #pragma unroll
-                    for (int k = 0; k < CP; ++k) rfma(s[k], pc[f], a[k]);
-                }
-                const int o = tr * nphp + key;
-                const C z = sh[o];
-                C acc[CP];
-                lds_cols<C, CP>(O + o * PW + cg, acc);
+                    for (int r = 0; r < RB; ++r)
 #pragma unroll
-                for (int k = 0; k < CP; ++k) cfma(acc[k], z, s[k]);
-                sts_cols<C, CP>(O + o * PW + cg, acc);
+                        for (int k = 0; k < CP; ++k) rfma(s[r][k], pc[r][f], a[k]);
+                }
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const int o = tr * nphp + key * RB + r;
+                    const C z = sh[o];
+                    C acc[CP];
+                    lds_cols<C, CP>(O + o * PW + cg, acc);
+#pragma unroll
+                    for (int k = 0; k < CP; ++k) cfma(acc[k], z, s[r][k]);
+                    sts_cols<C, CP>(O + o * PW + cg, acc);
+                }
             }
         }
         __syncthreads();
@@ -757,8 +796,12 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
 // stencils) are zero-padded to TM taps per row so that a thread holds one
 // row's taps in registers and sweeps them over a chunk of rows, CP adjacent
 // columns per 16-byte shared-memory access (the layout of the upward pass).
-template <class R, int NB, int TM>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4 && TM <= 20) ? 4 : 1) k_down(DevLevel<R> P, DevLevel<R> Ch, int B, int Bs)
+// RB = 2: the anterpolation rows go in pairs (tables thd2 / phd2: the union of
+// both rows' taps, one coefficient per row), so each value a thread loads
+// from shared memory feeds both rows of the pair.
+template <class R, int NB, int TM, int RB = 1>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && TM <= 20) ? (RB == 1 ? 4 : (TM <= 16 ? 3 : 2)) : 1)
+    k_down(DevLevel<R> P, DevLevel<R> Ch, int B, int Bs)
 {
     using C = typename Cx<R>::T;
     constexpr int CP = ColPair<R, NB>::CP, NL = NB / CP, PW = NB;
@@ -797,64 +840,94 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 && TM <= 20) ? 4 : 1) k_d
         }
     }
     __syncthreads();
-    // phi: U(tp, v) = sum_f c_f H(tp, u_f(v)); key = child phi index v, rows = parent theta rows
-    const SplitIL sp(nphc, NL);
+    // phi: U(tp, v) = sum_f c_f H(tp, u_f(v)); key = child phi index v (a pair
+    // of them for RB = 2), rows = parent theta rows
+    const SplitIL sp((nphc + RB - 1) / RB, NL);
     for (int it = threadIdx.x; it < sp.items; it += blockDim.x) {
         int key, cg, ch;
         sp.item(it, CP, key, cg, ch);
         int pb[TM];
-        R pc[TM];
+        R pc[RB][TM];
 #pragma unroll
         for (int f = 0; f < TM; ++f) {
-            const Tap<R> tap = P.phd_pad[(size_t)key * TM + f];
-            pb[f] = tap.i * PW;
-            pc[f] = tap.c;
+            if constexpr (RB == 1) {
+                const Tap<R> tap = P.phd_pad[(size_t)key * TM + f];
+                pb[f] = tap.i * PW;
+                pc[0][f] = tap.c;
+            } else {
+                const Tap2<R> tap = P.phd2[(size_t)key * TM + f];
+                pb[f] = tap.i * PW;
+                pc[0][f] = tap.c[0];
+                pc[1][f] = tap.c[1];
+            }
         }
         for (int tp = ch; tp < ntp; tp += sp.chunks) {
             const C *hrow = H + tp * hp * PW + cg;
-            C s[CP];
+            C s[RB][CP];
 #pragma unroll
-            for (int k = 0; k < CP; ++k) s[k] = C{0, 0};
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+                for (int k = 0; k < CP; ++k) s[r][k] = C{0, 0};
 #pragma unroll
             for (int f = 0; f < TM; ++f) {
                 C a[CP];
                 lds_cols<C, CP>(hrow + pb[f], a);
 #pragma unroll
-                for (int k = 0; k < CP; ++k) rfma(s[k], pc[f], a[k]);
+                for (int r = 0; r < RB; ++r)
+#pragma unroll
+                    for (int k = 0; k < CP; ++k) rfma(s[r][k], pc[r][f], a[k]);
             }
-            sts_cols<C, CP>(U + (tp * nphc + key) * PW + cg, s);
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+                if (key * RB + r < nphc) sts_cols<C, CP>(U + (tp * nphc + key * RB + r) * PW + cg, s[r]);
         }
     }
     __syncthreads();
-    // theta: W(j, v) = sum_f c_f U(t_f, v or v + pi); key = child theta row j, span = child phi index
-    const SplitIL st(nthc, NL);
+    // theta: W(j, v) = sum_f c_f U(t_f, v or v + pi); key = child theta row j
+    // (a pair of them for RB = 2), span = child phi index
+    const SplitIL st((nthc + RB - 1) / RB, NL);
     C *W = H;
     for (int it = threadIdx.x; it < st.items; it += blockDim.x) {
         int key, cg, ch;
         st.item(it, CP, key, cg, ch);
         int tb[TM];
         bool rf[TM];
-        R tc[TM];
+        R tc[RB][TM];
 #pragma unroll
         for (int f = 0; f < TM; ++f) {
-            const Tap<R> tap = P.thd_pad[(size_t)key * TM + f];
-            tb[f] = (tap.i & (kTapRefl - 1)) * nphc;
-            rf[f] = (tap.i & kTapRefl) != 0;
-            tc[f] = tap.c;
+            int ti;
+            if constexpr (RB == 1) {
+                const Tap<R> tap = P.thd_pad[(size_t)key * TM + f];
+                ti = tap.i;
+                tc[0][f] = tap.c;
+            } else {
+                const Tap2<R> tap = P.thd2[(size_t)key * TM + f];
+                ti = tap.i;
+                tc[0][f] = tap.c[0];
+                tc[1][f] = tap.c[1];
+            }
+            tb[f] = (ti & (kTapRefl - 1)) * nphc;
+            rf[f] = (ti & kTapRefl) != 0;
         }
         for (int v = ch; v < nphc; v += st.chunks) {
             const int vs = v + hc < nphc ? v + hc : v + hc - nphc;
-            C s[CP];
+            C s[RB][CP];
 #pragma unroll
-            for (int k = 0; k < CP; ++k) s[k] = C{0, 0};
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+                for (int k = 0; k < CP; ++k) s[r][k] = C{0, 0};
 #pragma unroll
             for (int f = 0; f < TM; ++f) {
                 C a[CP];
                 lds_cols<C, CP>(U + (tb[f] + (rf[f] ? vs : v)) * PW + cg, a);
 #pragma unroll
-                for (int k = 0; k < CP; ++k) rfma(s[k], tc[f], a[k]);
+                for (int r = 0; r < RB; ++r)
+#pragma unroll
+                    for (int k = 0; k < CP; ++k) rfma(s[r][k], tc[r][f], a[k]);
             }
-            sts_cols<C, CP>(W + (key * nphc + v) * PW + cg, s);
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+                if (key * RB + r < nthc) sts_cols<C, CP>(W + ((key * RB + r) * nphc + v) * PW + cg, s[r]);
         }
     }
     cp_async_wait<0>();
@@ -1436,12 +1509,12 @@ cudaError_t launch_receive(const ProductArgs<R> &a, int Bs, cudaStream_t s, int 
 }
 
 // ---- upward: columns per CTA NB, parent theta rows split RS ways
-template <class R, int NB, int PO>
+template <class R, int NB, int PO, int RB = 1>
 cudaError_t launch_up_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, int acc, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     auto smem_of = [&](int rs) {
-        const int rows = (P.nth + rs - 1) / rs;
+        const int rows = up_band_rows(P.nth, rs, RB);
         return ((size_t)Ch.K + (size_t)rows * (Ch.nph + P.nph)) * NB * sizeof(C);
     };
     int RS = 1;
@@ -1450,13 +1523,28 @@ cudaError_t launch_up_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int
     const int64_t ctas = (int64_t)P.nbox * 2 * ((B + NB - 1) / NB);
     while (ctas * RS < 8 * 152 && 2 * RS <= P.nth / 2) RS *= 2;
     dim3 grid(P.nbox, 2, ((B + NB - 1) / NB) * RS);
-    k_up<R, NB, PO><<<grid, 256, smem_of(RS), s>>>(P, Ch, B, RS, Bs, acc);
+    k_up<R, NB, PO, RB><<<grid, 256, smem_of(RS), s>>>(P, Ch, B, RS, Bs, acc);
     return cudaGetLastError();
 }
 
+// rb = 1: rows one at a time (the interpolation order's taps); rb = 2: rows
+// in pairs (up2_taps, FP32)
 template <class R, int NB>
-cudaError_t launch_up_po(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, int acc, int order, cudaStream_t s)
+cudaError_t launch_up_po(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, int acc, int order, cudaStream_t s,
+                         int rb = 1)
 {
+    if (rb == 2) {
+        if constexpr (sizeof(R) == 4) {
+            if (!P.thu2 || !P.phu2) return cudaErrorInvalidConfiguration;
+            switch (P.up2_taps) {
+            case 12: return launch_up_nb<R, NB, 12, 2>(P, Ch, B, Bs, acc, s);
+            case 16: return launch_up_nb<R, NB, 16, 2>(P, Ch, B, Bs, acc, s);
+            default: return cudaErrorInvalidConfiguration;
+            }
+        } else {
+            return cudaErrorInvalidConfiguration;
+        }
+    }
     switch (order) {
     case 4: return launch_up_nb<R, NB, 4>(P, Ch, B, Bs, acc, s);
     case 6: return launch_up_nb<R, NB, 6>(P, Ch, B, Bs, acc, s);
@@ -1484,16 +1572,21 @@ cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs
     using C = typename Cx<R>::T;
     const int order = P.up_order;
     int nb = column_chunk<R>(B, ((size_t)Ch.K + (size_t)P.nth * (Ch.nph + P.nph)) * sizeof(C));
+    int rb = 1;
+    if (nb_choice > 200) {   // 202 .. 216: rows in pairs, 2 .. 16 columns per CTA
+        rb = 2;
+        nb_choice -= 200;
+    }
     if (nb_choice) {
         if (nb_choice > 16 || (nb_choice & (nb_choice - 1)) || nb_choice > std::max(1, B)) return cudaErrorInvalidConfiguration;
         nb = nb_choice;
     }
     switch (nb) {
-    case 1: return launch_up_po<R, 1>(P, Ch, B, Bs, acc, order, s);
-    case 2: return launch_up_po<R, 2>(P, Ch, B, Bs, acc, order, s);
-    case 4: return launch_up_po<R, 4>(P, Ch, B, Bs, acc, order, s);
-    case 8: return launch_up_po<R, 8>(P, Ch, B, Bs, acc, order, s);
-    default: return launch_up_po<R, 16>(P, Ch, B, Bs, acc, order, s);
+    case 1: return launch_up_po<R, 1>(P, Ch, B, Bs, acc, order, s, rb);
+    case 2: return launch_up_po<R, 2>(P, Ch, B, Bs, acc, order, s, rb);
+    case 4: return launch_up_po<R, 4>(P, Ch, B, Bs, acc, order, s, rb);
+    case 8: return launch_up_po<R, 8>(P, Ch, B, Bs, acc, order, s, rb);
+    default: return launch_up_po<R, 16>(P, Ch, B, Bs, acc, order, s, rb);
     }
 }
 
@@ -1553,22 +1646,37 @@ cudaError_t launch_translate(const DevLevel<R> &Lv, int B, int Bs, int acc, cuda
 }
 
 // ---- downward: columns per CTA NB, anterpolation taps per row TM
-template <class R, int NB, int TM>
+template <class R, int NB, int TM, int RB>
 cudaError_t launch_down_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, size_t smem, cudaStream_t s)
 {
     dim3 grid(Ch.nbox, 2, (B + NB - 1) / NB);
-    k_down<R, NB, TM><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
+    k_down<R, NB, TM, RB><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
     return cudaGetLastError();
 }
 
+// RB = 1: rows one at a time (dn_taps); RB = 2: rows in pairs (dn2_taps, FP32)
 template <class R, int NB>
-cudaError_t launch_down_tm(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, size_t smem, cudaStream_t s)
+cudaError_t launch_down_tm(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, size_t smem, cudaStream_t s,
+                           int rb = 1)
 {
+    if (rb == 2) {
+        if constexpr (sizeof(R) == 4) {
+            if (!P.thd2 || !P.phd2) return cudaErrorInvalidConfiguration;
+            switch (P.dn2_taps) {
+            case 16: return launch_down_nb<R, NB, 16, 2>(P, Ch, B, Bs, smem, s);
+            case 20: return launch_down_nb<R, NB, 20, 2>(P, Ch, B, Bs, smem, s);
+            case 24: return launch_down_nb<R, NB, 24, 2>(P, Ch, B, Bs, smem, s);
+            default: return cudaErrorInvalidConfiguration;
+            }
+        } else {
+            return cudaErrorInvalidConfiguration;
+        }
+    }
     switch (P.dn_taps) {
-    case 16: return launch_down_nb<R, NB, 16>(P, Ch, B, Bs, smem, s);
-    case 20: return launch_down_nb<R, NB, 20>(P, Ch, B, Bs, smem, s);
-    case 24: return launch_down_nb<R, NB, 24>(P, Ch, B, Bs, smem, s);
-    case 32: return launch_down_nb<R, NB, 32>(P, Ch, B, Bs, smem, s);
+    case 16: return launch_down_nb<R, NB, 16, 1>(P, Ch, B, Bs, smem, s);
+    case 20: return launch_down_nb<R, NB, 20, 1>(P, Ch, B, Bs, smem, s);
+    case 24: return launch_down_nb<R, NB, 24, 1>(P, Ch, B, Bs, smem, s);
+    case 32: return launch_down_nb<R, NB, 32, 1>(P, Ch, B, Bs, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1598,6 +1706,11 @@ cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int 
     using C = typename Cx<R>::T;
     const size_t per_col = ((size_t)P.K + (size_t)P.nth + (size_t)P.nth * Ch.nph + (size_t)Ch.K) * sizeof(C);
     int nb = column_chunk<R>(B, per_col);
+    int rb = 1;
+    if (nb_choice > 200) {   // 204, 208, 216: rows in pairs, 4 / 8 / 16 columns per CTA
+        rb = 2;
+        nb_choice -= 200;
+    }
     if (nb_choice) {
         if (nb_choice > 16 || (nb_choice & (nb_choice - 1)) || nb_choice > std::max(1, B)) return cudaErrorInvalidConfiguration;
         nb = nb_choice;
@@ -1605,11 +1718,11 @@ cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int 
     const size_t smem = per_col * nb;
     if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
     switch (nb) {
-    case 1: return launch_down_tm<R, 1>(P, Ch, B, Bs, smem, s);
-    case 2: return launch_down_tm<R, 2>(P, Ch, B, Bs, smem, s);
-    case 4: return launch_down_tm<R, 4>(P, Ch, B, Bs, smem, s);
-    case 8: return launch_down_tm<R, 8>(P, Ch, B, Bs, smem, s);
-    default: return launch_down_tm<R, 16>(P, Ch, B, Bs, smem, s);
+    case 1: return launch_down_tm<R, 1>(P, Ch, B, Bs, smem, s, rb);
+    case 2: return launch_down_tm<R, 2>(P, Ch, B, Bs, smem, s, rb);
+    case 4: return launch_down_tm<R, 4>(P, Ch, B, Bs, smem, s, rb);
+    case 8: return launch_down_tm<R, 8>(P, Ch, B, Bs, smem, s, rb);
+    default: return launch_down_tm<R, 16>(P, Ch, B, Bs, smem, s, rb);
     }
 }
 
@@ -1623,8 +1736,10 @@ cudaError_t prime_kernels()
     cudaError_t e;
 #define ALLOW(k) do { if ((e = allow_smem(k)) != cudaSuccess) return e; } while (0)
 #define ALLOW_UP(NB) ALLOW((k_up<R, NB, 4>)); ALLOW((k_up<R, NB, 6>)); ALLOW((k_up<R, NB, 8>)); \
-    ALLOW((k_up<R, NB, 10>)); ALLOW((k_up<R, NB, 12>)); ALLOW((k_down<R, NB, 16>)); ALLOW((k_down<R, NB, 20>)); \
-    ALLOW((k_down<R, NB, 24>)); ALLOW((k_down<R, NB, 32>))
+    ALLOW((k_up<R, NB, 10>)); ALLOW((k_up<R, NB, 12>)); ALLOW((k_down<R, NB, 16, 1>)); ALLOW((k_down<R, NB, 20, 1>)); \
+    ALLOW((k_down<R, NB, 24, 1>)); ALLOW((k_down<R, NB, 32, 1>)); \
+    if (sizeof(R) == 4) { ALLOW((k_down<R, NB, 16, 2>)); ALLOW((k_down<R, NB, 20, 2>)); ALLOW((k_down<R, NB, 24, 2>)); \
+                          ALLOW((k_up<R, NB, 12, 2>)); ALLOW((k_up<R, NB, 16, 2>)); }
     ALLOW((k_near<R, 1, true>)); ALLOW((k_near<R, 2, true>)); ALLOW((k_near<R, 4, true>));
     ALLOW((k_near<R, 8, true>)); ALLOW((k_near<R, 16, true>));
     ALLOW((k_near_wide<R, 8>)); ALLOW((k_near_wide<R, 16>));

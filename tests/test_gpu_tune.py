@@ -76,8 +76,8 @@ def test_every_candidate_shape_computes_the_same_product(dt, prec, tol):
         cands += [(3 + 2 * L + l, c) for c in range(1, 9)]
         if l < 4:
             cands += [(3 + l, c) for c in (1, 2, 4, 8, 16)] + [(3 + L + l, c) for c in (1, 2, 4, 8, 16, 104, 108)]
-            if prec == M.FP32:
-                cands.append((3 + l, 100))
+            if prec == M.FP32:   # interpolation / anterpolation rows in pairs
+                cands += [(3 + l, c) for c in (202, 204, 208, 216)] + [(3 + L + l, c) for c in (204, 208, 216)]
     for field, c in cands:
         ch = np.zeros(M.TUNE_FIELDS, np.int32)
         ch[field] = c
@@ -124,3 +124,33 @@ def test_tune_set_rejects_undocumented_shapes():
         P.tune_set(9, good, M.FP32)
     P.tune_set(4, good, M.FP32)
     assert np.array_equal(P.tune_get(4, M.FP32), good)
+
+
+@pytest.mark.parametrize("name,B", [("sphere-r2m-ico5", 64), ("plate6m-strips", 16), ("sphere-r2m-ico5", 7)])
+def test_paired_rows_variants_match_builtin(name, B):
+    """The up and down passes with their interpolation / anterpolation rows
+    taken in pairs (tune values 202..216: one shared-memory load feeds both
+    rows of a pair) compute the same product as the one-row kernels, every
+    level pinned to them, for each columns-per-CTA choice: FP32 rounding
+    (1e-5), and the oracle's bound on sampled exact rows."""
+    W = workloads.get(name)
+    v, t = W.mesh()
+    P = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=64, precisions=(M.FP32,))
+    x = workloads.rhs(P.n, B, W.seed)
+    xd = torch.from_numpy(x).to("cuda", torch.float32)
+    y0 = P.matvec(xd).cpu().numpy()
+    info = P.info()
+    idx = np.random.default_rng(9).choice(P.n, 8, replace=False)
+    ref = efie.Problem(v, t, W.k).matvec_rows(x, idx)
+    for nb in (2, 4, 8, 16):
+        if nb > B:
+            continue
+        c = np.zeros(M.TUNE_FIELDS, np.int32)
+        for l in range(2, info["leaf_level"]):
+            c[3 + l] = 200 + nb
+            if nb >= 4:
+                c[3 + M.MAX_LEVELS + l] = 200 + nb
+        P.tune_set(B, c, M.FP32)
+        y = P.matvec(xd).cpu().numpy()
+        assert rel(y, y0) < 1e-5, (nb, rel(y, y0))
+        assert rel(y[idx], ref) < 1e-3
