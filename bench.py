@@ -173,7 +173,7 @@ def kernel_digest():
 # at B = 64: {(workload, stage, kernel source digest): bytes}.  Summaries in
 # profiles/ (k_down_cube8m-6lv_B64.md).
 NCU_TRAFFIC = {
-    ("cube8m-6lv", "down4", "5aff218f72d724e6"): 4_822_725_000 + 1_676_389_000,
+    ("cube8m-6lv", "down4", "c6a6225a1d97581e"): 4_820_682_000 + 1_676_295_000,
 }
 
 
