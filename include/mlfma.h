@@ -245,14 +245,21 @@ mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec
  *   [2] reception: 1 / 2 / 3 tiles of 32 / 16 / 8 columns
  *   [3 + l]       up pass into level l: columns per CTA 1..16, or 202 / 204 /
  *                 208 / 216 with 2 / 4 / 8 / 16 columns and the interpolation
- *                 rows taken in pairs (FP32 only)
+ *                 rows taken in pairs (FP32 only), or 304 / 308 / 316 the
+ *                 windowed kernel (rows in groups of four on windows of
+ *                 consecutive source samples, MLFMA_X_WIN_SHAPE) with
+ *                 4 / 8 / 16 columns (FP32 only)
  *   [3 + 22 + l]  down pass from level l: columns per CTA 1..16 (one CTA per
- *                 child), 104 / 108 one CTA per parent with 4 / 8 columns, or
+ *                 child), 104 / 108 one CTA per parent with 4 / 8 columns,
  *                 204 / 208 / 216 one CTA per child with 4 / 8 / 16 columns and
- *                 the anterpolation rows taken in pairs (FP32 only)
+ *                 the anterpolation rows taken in pairs (FP32 only), or
+ *                 304 / 308 / 316 the windowed kernel with 4 / 8 / 16 columns
+ *                 (FP32 only)
  *   [3 + 44 + l]  translation at level l: 1 two columns per thread; 2..6 one
  *                 column with 1, 2, 4, 8, 16 lanes per output; 7 / 8 one warp
- *                 per (child, sample) with 2 / 1 columns per lane
+ *                 per (child, sample) with 2 / 1 columns per lane; 9 / 10 / 11
+ *                 four columns per thread and the children four at a time,
+ *                 64 / 32 / 16 columns per CTA (FP32 only)
  * Columns per CTA are powers of two (1, 2, 4, 8, 16).  mlfma_tune_set
  * returns MLFMA_EINVAL, and pins nothing, for B outside 1..max_batch, an
  * unknown prec or a value outside the sets above; a listed shape that does
@@ -519,6 +526,17 @@ mlfma_status mlfma_plan_info(mlfma_plan_t plan, mlfma_info *info);
  *   MLFMA_X_SIB_ALPHA  float64 [T][K][2] sin-kernel table of the sibling
  *                                      translations of Eq. (RI) at `level` (1..leaf)
  *   MLFMA_X_SIB_OFFS   int32 [T][3]    their offsets (in boxes)
+ *   MLFMA_X_WIN_INTERP float64 [K_parent][K_child]  MLFMA_X_INTERP as the FP32
+ *                                      windowed kernels apply it: rebuilt from the
+ *                                      stencil rows in groups of four, each group's
+ *                                      taps on one window of consecutive positions
+ *                                      (theta: pole reflections at -i-1 / 2n-i-1;
+ *                                      phi: modulo the grid); EINVAL where a window
+ *                                      would exceed 32 taps (those levels keep the
+ *                                      other kernels)
+ *   MLFMA_X_WIN_ANTERP float64 [K_child][K_parent]  the same for MLFMA_X_ANTERP
+ *   MLFMA_X_WIN_SHAPE  int32 [8]       (groups, window width) of the four windowed
+ *                                      stencils: up theta, up phi, down phi, down theta
  * The grid of level 1 exists for plans with at least 3 levels (it serves the
  * sibling scheme only).
  */
@@ -526,7 +544,7 @@ enum {
     MLFMA_X_PERM = 1, MLFMA_X_LEAF_BOX = 2, MLFMA_X_GRID = 3, MLFMA_X_ALPHA = 4,
     MLFMA_X_ALPHA_OFFS = 5, MLFMA_X_INTERP = 6, MLFMA_X_BOX_CENTERS = 7, MLFMA_X_NEAR_COUNT = 8,
     MLFMA_X_ANTERP = 9, MLFMA_X_ALPHA_J = 10, MLFMA_X_ALPHA_Y = 11, MLFMA_X_SIB_ALPHA = 12,
-    MLFMA_X_SIB_OFFS = 13
+    MLFMA_X_SIB_OFFS = 13, MLFMA_X_WIN_INTERP = 14, MLFMA_X_WIN_ANTERP = 15, MLFMA_X_WIN_SHAPE = 16
 };
 mlfma_status mlfma_export(mlfma_plan_t plan, int what, int level, void *dst, int64_t cap,
                           int64_t *needed);

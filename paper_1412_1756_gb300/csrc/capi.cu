@@ -363,6 +363,28 @@ cudaError_t upload_parent_tables(DevMem &M, const PlanHost &H, const Level &Lv, 
         if ((e = M.upload(pack2(puth, D.up2_taps), &D.thu2)) != cudaSuccess) return e;
         if ((e = M.upload(pack2(puph, D.up2_taps), &D.phu2)) != cudaSuccess) return e;
     }
+    if constexpr (sizeof(R) == 4) {
+        // the four stencils on windows (FP32 windowed kernels)
+        auto upload_win = [&](const WinStencil &w, WinDev &d) -> cudaError_t {
+            d = WinDev();
+            if (!w.groups) return cudaSuccess;
+            std::vector<float4> cf((size_t)w.groups * w.tw);
+            for (size_t i = 0; i < cf.size(); ++i)
+                cf[i] = make_float4((float)w.coef[4 * i], (float)w.coef[4 * i + 1], (float)w.coef[4 * i + 2],
+                                    (float)w.coef[4 * i + 3]);
+            cudaError_t e2;
+            if ((e2 = M.upload(cf, &d.coef)) != cudaSuccess) return e2;
+            if ((e2 = M.upload(w.start, &d.start)) != cudaSuccess) return e2;
+            d.groups = w.groups;
+            d.tw = w.tw;
+            return cudaSuccess;
+        };
+        static_assert(kWinRows == 4, "the windowed kernels take rows in groups of four");
+        if ((e = upload_win(Lv.wu_th, D.wu_th)) != cudaSuccess) return e;
+        if ((e = upload_win(Lv.wu_ph, D.wu_ph)) != cudaSuccess) return e;
+        if ((e = upload_win(Lv.wd_ph, D.wd_ph)) != cudaSuccess) return e;
+        if ((e = upload_win(Lv.wd_th, D.wd_th)) != cudaSuccess) return e;
+    }
     return upload_tc_tables<R>(M, H, Lv, D, err);
 }
 
@@ -845,10 +867,10 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
         pick(STAGE_RADIATE, {1, 2, 3, 4}, best.radiate);
         pick(STAGE_RECEIVE, {1, 2, 3}, best.receive);
         for (int l = a.coarsest; l <= a.leaf; ++l) {
-            pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6, 7, 8}, best.tr[l]);
+            pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11}, best.tr[l]);
             if (l < a.leaf) {
-                pick(STAGE_UP + l, {1, 2, 4, 8, 16, 202, 204, 208, 216}, best.up_nb[l]);
-                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108, 204, 208, 216}, best.down_nb[l]);
+                pick(STAGE_UP + l, {1, 2, 4, 8, 16, 202, 204, 208, 216, 304, 308, 316}, best.up_nb[l]);
+                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108, 204, 208, 216, 304, 308, 316}, best.down_nb[l]);
             }
         }
     }
@@ -898,11 +920,13 @@ mlfma_status core_graph(mlfma_plan_t p, const ProductArgs<R> &a, int prec, int k
     cudaError_t el = dk ? launch_core_dk<R>(a, p->cs.main, nullptr) : launch_core<R>(a, p->cs, nullptr);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(p->cs.main, &g);
-    if (el != cudaSuccess) {
+    if (el != cudaSuccess || e != cudaSuccess) {
+        // a failed capture leaves its error as the thread's last CUDA error:
+        // clear it, so that the next launch does not report it as its own
         if (g) cudaGraphDestroy(g);
-        return cuda_fail(el, "core pass launch");
+        cudaGetLastError();
+        return el != cudaSuccess ? cuda_fail(el, "core pass launch") : cuda_fail(e, "graph capture");
     }
-    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
@@ -1359,7 +1383,9 @@ mlfma_status mlfma_tune_set(mlfma_plan_t p, int64_t B, int xc, int prec, const i
                   choices[2] >= 0 && choices[2] <= 3;
         for (int l = 0; l < MLFMA_MAX_LEVELS && ok; ++l) {
             const int u = choices[3 + l], d = choices[3 + MLFMA_MAX_LEVELS + l], r = choices[3 + 2 * MLFMA_MAX_LEVELS + l];
-            ok = (u == 0 || pow2(u) || u == 202 || u == 204 || u == 208 || u == 216) && (d == 0 || pow2(d) || d == 104 || d == 108 || d == 204 || d == 208 || d == 216) && r >= 0 && r <= 8;
+            auto win = [](int x) { return x == 304 || x == 308 || x == 316; };
+            ok = (u == 0 || pow2(u) || u == 202 || u == 204 || u == 208 || u == 216 || win(u)) &&
+                 (d == 0 || pow2(d) || d == 104 || d == 108 || d == 204 || d == 208 || d == 216 || win(d)) && r >= 0 && r <= 11;
         }
         if (!ok) return fail(MLFMA_EINVAL, "a launch-shape choice is outside its documented set");
     }
@@ -1548,6 +1574,80 @@ mlfma_status mlfma_export(mlfma_plan_t p, int what, int level, void *dst, int64_
                             Pa.th_dn.coef[f] * Pa.ph_dn.coef[e];
                 }
         put(Ax.data(), Ax.size() * sizeof(double));
+        break;
+    }
+    case MLFMA_X_WIN_INTERP:
+    case MLFMA_X_WIN_ANTERP: {
+        if (!(level >= 2 && level < H.leaf)) return fail(MLFMA_EINVAL, "no interpolation at this level");
+        const Level &Pa = H.lv[level], &C = H.lv[level + 1];
+        const bool up = what == MLFMA_X_WIN_INTERP;
+        const WinStencil &wt = up ? Pa.wu_th : Pa.wd_th, &wp = up ? Pa.wu_ph : Pa.wd_ph;
+        if (!wt.groups || !wp.groups) return fail(MLFMA_EINVAL, "no windowed tables at this level");
+        // the tables as the windowed kernels read them: theta rows r (source
+        // rows n_t, columns nph_t), phi rows (source samples n_p)
+        const int n_t = up ? C.nth : Pa.nth, n_p = up ? C.nph : Pa.nph;
+        const int rows_t = up ? Pa.nth : C.nth, rows_p = up ? Pa.nph : C.nph;
+        const int nph_t = C.nph;   // both theta steps run over the child's phi grid
+        auto theta_tap = [&](int r, int f, int &src, int &refl, double &c) {
+            const int g = r / kWinRows, e = wt.start[g] + f;
+            c = wt.coef[((size_t)g * wt.tw + f) * kWinRows + r % kWinRows];
+            refl = e < 0 || e >= n_t;
+            src = e < 0 ? -e - 1 : (e >= n_t ? 2 * n_t - e - 1 : e);
+        };
+        auto phi_tap = [&](int r, int f, int &src, double &c) {
+            const int g = r / kWinRows;
+            c = wp.coef[((size_t)g * wp.tw + f) * kWinRows + r % kWinRows];
+            src = (wp.start[g] + f) % n_p;
+        };
+        std::vector<double> M((size_t)Pa.K * C.K, 0.0);
+        if (up) {
+            // parent (t, u) <- phi rows u of T(t, v) <- theta rows t of the child (j, v or v + pi)
+            for (int t = 0; t < rows_t; ++t)
+                for (int u = 0; u < rows_p; ++u)
+                    for (int e = 0; e < wp.tw; ++e) {
+                        int v0;
+                        double cp;
+                        phi_tap(u, e, v0, cp);
+                        if (cp == 0) continue;
+                        for (int f = 0; f < wt.tw; ++f) {
+                            int j, refl;
+                            double ct;
+                            theta_tap(t, f, j, refl, ct);
+                            if (ct == 0) continue;
+                            const int v = refl ? (v0 + nph_t / 2) % nph_t : v0;
+                            M[(size_t)(t * Pa.nph + u) * C.K + j * C.nph + v] += cp * ct;
+                        }
+                    }
+        } else {
+            // child (j, v') <- theta rows j of U(t, v' or v' + pi) <- phi rows v of the parent (t, u)
+            for (int j = 0; j < rows_t; ++j)
+                for (int vp = 0; vp < C.nph; ++vp)
+                    for (int f = 0; f < wt.tw; ++f) {
+                        int t, refl;
+                        double ct;
+                        theta_tap(j, f, t, refl, ct);
+                        if (ct == 0) continue;
+                        const int v = refl ? (vp + nph_t / 2) % nph_t : vp;
+                        for (int e = 0; e < wp.tw; ++e) {
+                            int u;
+                            double cp;
+                            phi_tap(v, e, u, cp);
+                            if (cp == 0) continue;
+                            M[(size_t)(j * C.nph + vp) * Pa.K + t * Pa.nph + u] += ct * cp;
+                        }
+                    }
+        }
+        (void)rows_p;
+        put(M.data(), M.size() * sizeof(double));
+        break;
+    }
+    case MLFMA_X_WIN_SHAPE: {
+        if (!(level >= 2 && level < H.leaf)) return fail(MLFMA_EINVAL, "no interpolation at this level");
+        const Level &Pa = H.lv[level];
+        int32_t sh[8];
+        const WinStencil *w[4] = {&Pa.wu_th, &Pa.wu_ph, &Pa.wd_ph, &Pa.wd_th};
+        for (int i = 0; i < 4; ++i) { sh[2 * i] = w[i]->groups; sh[2 * i + 1] = w[i]->tw; }
+        put(sh, sizeof(sh));
         break;
     }
     default:

@@ -67,6 +67,19 @@ struct Tap {
 };
 constexpr int32_t kTapRefl = 1 << 30;
 
+// A stencil's rows in groups of four on windows of consecutive source
+// positions, for the FP32 windowed kernels: tap f of group g is position
+// start[g] + f with coefficients coef[g * tw + f] (one per row of the
+// group).  Periodic (phi) stencils: position e is sample e mod n.  Theta
+// stencils: e in [0, n) is row e; e < 0 is row -e-1 and e >= n is row
+// 2n-e-1, both at phi + pi (pole reflection; its sign is in the
+// coefficients).
+struct WinDev {
+    int groups = 0, tw = 0;   // groups = 0: not available at this level
+    const int32_t *start = nullptr;
+    const float4 *coef = nullptr;
+};
+
 // One far level's tables in arithmetic type R (complex values as R pairs).
 template <class R>
 struct DevLevel {
@@ -109,6 +122,8 @@ struct DevLevel {
     // with one coefficient per row, zero-padded to dn2_taps entries (0: not built)
     const Tap2<R> *thd2 = nullptr, *phd2 = nullptr;
     int dn2_taps = 0;
+    // the four stencils on windows (up theta, up phi, down phi, down theta)
+    WinDev wu_th, wu_ph, wd_ph, wd_th;
     // FP32 parents: the interpolation (up: phi then theta) and anterpolation
     // (down: theta then phi) steps as dense matrices for the tcgen05 tensor
     // cores (null where a level's dimensions do not fit the kernels)
@@ -234,5 +249,22 @@ cudaError_t launch_up_umma(const DevLevel<float> &P, const DevLevel<float> &Ch, 
                            cudaStream_t s);
 cudaError_t launch_down_umma(const DevLevel<float> &P, const DevLevel<float> &Ch, int B, int Bs, bool split,
                              cudaStream_t s);
+
+// Windowed CUDA-core interpolation and anterpolation of FP32 fields
+// (window_interp.cu), NB = 4, 8 or 16 columns per CTA.
+// cudaErrorInvalidConfiguration, with nothing launched, when the level has
+// no windowed tables or does not fit the kernels.
+cudaError_t launch_up_win(const DevLevel<float> &P, const DevLevel<float> &Ch, int B, int Bs, int acc, int nb,
+                          cudaStream_t s);
+cudaError_t launch_down_win(const DevLevel<float> &P, const DevLevel<float> &Ch, int B, int Bs, int nb,
+                            cudaStream_t s);
+cudaError_t prime_win_kernels();
+
+// Translation of FP32 fields grouped by parent, four columns per thread and
+// the children four at a time (translate_quad.cu), NB = 16, 32 or 64
+// columns per CTA.  cudaErrorInvalidConfiguration, with nothing launched,
+// when the level's tables or shared memory do not fit the kernel.
+cudaError_t launch_translate_quad(const DevLevel<float> &lv, int B, int Bs, int acc, int nb, cudaStream_t s);
+cudaError_t prime_translate_quad();
 
 }  // namespace mlfma

@@ -9,6 +9,7 @@
 namespace mlfma {
 
 static const double kPi = 3.14159265358979323846;
+static const int kWinMax = 32;   // widest window of the windowed stencil tables
 
 // ------------------------------------------------------------ specfun ---
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
@@ -201,6 +202,73 @@ static void transpose_stencil(const Stencil &F, int nrows_out, Scale scale, Sten
         }
         Tr.ptr.push_back((int32_t)Tr.idx.size());
     }
+}
+
+// ------------------------------------------------------ windowed rows ---
+bool win_stencil(const Stencil &S, int n, bool theta, int tw_max, WinStencil &W)
+{
+    const int rows = (int)S.ptr.size() - 1;
+    W = WinStencil();
+    if (rows <= 0 || n <= 0) return false;
+    const int groups = (rows + kWinRows - 1) / kWinRows;
+    struct Ent { int row, pos; double c; };
+    std::vector<std::vector<Ent>> ent(groups);
+    std::vector<int> lo(groups), hi(groups);
+    int tw = 0;
+    for (int g = 0; g < groups; ++g) {
+        const int r0 = g * kWinRows, r1 = std::min(rows, r0 + kWinRows);
+        if (theta) {
+            for (int r = r0; r < r1; ++r) {
+                // a reflected sample goes to the pole nearer the row's direct taps
+                double sum = 0;
+                int cnt = 0;
+                for (int e = S.ptr[r]; e < S.ptr[r + 1]; ++e)
+                    if (!S.refl[e]) { sum += S.idx[e]; ++cnt; }
+                const double mid = cnt ? sum / cnt : (r < rows / 2 ? 0.0 : n - 1.0);
+                for (int e = S.ptr[r]; e < S.ptr[r + 1]; ++e) {
+                    int pos = S.idx[e];
+                    if (S.refl[e]) {
+                        const int north = -pos - 1, south = 2 * n - pos - 1;
+                        pos = std::abs(north - mid) <= std::abs(south - mid) ? north : south;
+                    }
+                    ent[g].push_back({r - r0, pos, S.coef[e]});
+                }
+            }
+        } else {
+            // the shortest arc of the periodic grid holding every tap of the group
+            std::vector<int> u;
+            for (int r = r0; r < r1; ++r)
+                for (int e = S.ptr[r]; e < S.ptr[r + 1]; ++e) u.push_back(S.idx[e]);
+            std::sort(u.begin(), u.end());
+            u.erase(std::unique(u.begin(), u.end()), u.end());
+            int best = -1, gap = -1;
+            for (size_t i = 0; i < u.size(); ++i) {
+                const int nx = i + 1 < u.size() ? u[i + 1] : u[0] + n;
+                if (nx - u[i] > gap) { gap = nx - u[i]; best = (int)i; }
+            }
+            const int st = u[(best + 1) % u.size()];
+            for (int r = r0; r < r1; ++r)
+                for (int e = S.ptr[r]; e < S.ptr[r + 1]; ++e)
+                    ent[g].push_back({r - r0, st + ((S.idx[e] - st) % n + n) % n, S.coef[e]});
+        }
+        lo[g] = hi[g] = ent[g].front().pos;
+        for (const Ent &x : ent[g]) { lo[g] = std::min(lo[g], x.pos); hi[g] = std::max(hi[g], x.pos); }
+        tw = std::max(tw, hi[g] - lo[g] + 1);
+        if (theta && (lo[g] < -n || hi[g] >= 2 * n)) return false;
+    }
+    if (tw > tw_max || (!theta && tw > n) || (theta && tw > 3 * n)) return false;
+    W.groups = groups;
+    W.tw = tw;
+    W.start.resize(groups);
+    W.coef.assign((size_t)groups * tw * kWinRows, 0.0);
+    for (int g = 0; g < groups; ++g) {
+        // theta: keep the window inside [-n, 2n); phi: start in [0, n)
+        int st = lo[g];
+        if (theta) st = std::max(-n, std::min(st, 2 * n - tw));
+        for (const Ent &x : ent[g]) W.coef[((size_t)g * tw + (x.pos - st)) * kWinRows + x.row] += x.c;
+        W.start[g] = theta ? st : ((st % n) + n) % n;
+    }
+    return true;
 }
 
 // ------------------------------------------------------------- grids ---
@@ -673,6 +741,10 @@ std::string build_plan_host(PlanHost &P, const double *verts, int64_t nv, const 
         const double phr = (double)C.nph / (double)Pa.nph;
         transpose_stencil(Pa.ph_up, C.nph, [&](int, int) { return phr; }, Pa.ph_dn);
         transpose_stencil(Pa.th_up, C.nth, [&](int t, int j) { return Pa.wt[t] / C.wt[j]; }, Pa.th_dn);
+        win_stencil(Pa.th_up, C.nth, true, kWinMax, Pa.wu_th);
+        win_stencil(Pa.ph_up, C.nph, false, kWinMax, Pa.wu_ph);
+        win_stencil(Pa.ph_dn, Pa.nph, false, kWinMax, Pa.wd_ph);
+        win_stencil(Pa.th_dn, Pa.nth, true, kWinMax, Pa.wd_th);
         Pa.shift.resize((size_t)8 * Pa.K);
         Pa.shift_dk.resize((size_t)8 * Pa.K);
         for (int o = 0; o < 8; ++o) {

@@ -28,6 +28,26 @@ struct Stencil {
     std::vector<double> coef;     // pole reflection sign folded in
 };
 
+// A stencil's rows in groups of kWinRows, each group's taps placed on one
+// window of consecutive source positions (tw wide, tap f at position
+// start + f), with one coefficient per row of the group (zero where a row
+// has no tap at that position).  Periodic (phi) stencils over n source
+// samples: position e is sample e mod n, start in [0, n).  Theta stencils:
+// position e in [0, n) is sample e; e < 0 is sample -e-1 and e >= n is
+// sample 2n-e-1, both taken at phi + pi (the pole reflection, whose sign
+// is already in the coefficient); start >= -n and start + tw <= 2n.
+constexpr int kWinRows = 4;
+struct WinStencil {
+    int groups = 0;                 // ceil(rows / kWinRows); 0: not built (a window wider than allowed)
+    int tw = 0;                     // window width
+    std::vector<int32_t> start;     // [groups]
+    std::vector<double> coef;       // [groups][tw][kWinRows]
+};
+
+// Builds W from S (n source samples).  False, with W.groups = 0, when a
+// group's window would be wider than tw_max (or than n for phi).
+bool win_stencil(const Stencil &S, int n, bool theta, int tw_max, WinStencil &W);
+
 struct Level {
     int l = 0;
     double a = 0.0;                 // box side
@@ -66,6 +86,7 @@ struct Level {
     std::vector<cd> shift_dk;       // [8][K]: d shift / dk = i khat.(r_parent - r_child) shift
     Stencil th_up, ph_up;           // child grid -> this grid (rows: nth / nph of this level)
     Stencil ph_dn, th_dn;           // weighted transposes (rows: child nph / child nth)
+    WinStencil wu_th, wu_ph, wd_ph, wd_th;   // the four stencils above on windows (kernels that take taps at fixed offsets)
     int nbox() const { return (int)code.size(); }
 };
 

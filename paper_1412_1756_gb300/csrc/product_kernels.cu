@@ -1570,6 +1570,10 @@ cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs
                       int nb_choice = 0)
 {
     using C = typename Cx<R>::T;
+    if (nb_choice > 300) {   // 304, 308, 316: windowed FP32 kernel, 4 / 8 / 16 columns per CTA
+        if constexpr (sizeof(R) == 4) return launch_up_win(P, Ch, B, Bs, acc, nb_choice - 300, s);
+        else return cudaErrorInvalidConfiguration;
+    }
     const int order = P.up_order;
     int nb = column_chunk<R>(B, ((size_t)Ch.K + (size_t)P.nth * (Ch.nph + P.nph)) * sizeof(C));
     int rb = 1;
@@ -1611,6 +1615,10 @@ cudaError_t launch_translate_es(const DevLevel<R> &Lv, int B, int Bs, int acc, c
 template <class R>
 cudaError_t launch_translate(const DevLevel<R> &Lv, int B, int Bs, int acc, cudaStream_t s, int choice = 0)
 {
+    if (choice >= 9 && choice <= 11) {   // four columns per thread, 64 / 32 / 16 columns per CTA
+        if constexpr (sizeof(R) == 4) return launch_translate_quad(Lv, B, Bs, acc, 64 >> (choice - 9), s);
+        else return cudaErrorInvalidConfiguration;
+    }
     if (choice == 7 || choice == 8) {
         using C = typename Cx<R>::T;
         if (!Lv.il_ptr) return cudaErrorInvalidConfiguration;
@@ -1701,6 +1709,10 @@ cudaError_t launch_down_pp(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, i
 template <class R>
 cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, cudaStream_t s, int nb_choice = 0)
 {
+    if (nb_choice > 300) {   // 304, 308, 316: windowed FP32 kernel, 4 / 8 / 16 columns per CTA
+        if constexpr (sizeof(R) == 4) return launch_down_win(P, Ch, B, Bs, nb_choice - 300, s);
+        else return cudaErrorInvalidConfiguration;
+    }
     if (nb_choice == 104) return launch_down_pp<R, 4>(P, Ch, B, Bs, s);
     if (nb_choice == 108) return launch_down_pp<R, 8>(P, Ch, B, Bs, s);
     using C = typename Cx<R>::T;
@@ -1752,6 +1764,10 @@ cudaError_t prime_kernels()
     ALLOW_UP(1); ALLOW_UP(2); ALLOW_UP(4); ALLOW_UP(8); ALLOW_UP(16);
 #undef ALLOW_UP
 #undef ALLOW
+    if (sizeof(R) == 4) {
+        if ((e = prime_win_kernels()) != cudaSuccess) return e;
+        return prime_translate_quad();
+    }
     return cudaSuccess;
 }
 
@@ -1811,7 +1827,7 @@ cudaError_t down_level(const ProductArgs<R> &a, int l, int B, cudaStream_t s, in
 }
 
 template <class R>
-cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClock *clk)
+cudaError_t launch_core_streams(const ProductArgs<R> &a, const CoreStreams &cs, StageClock *clk)
 {
     const int B = a.B, leaf = a.leaf, top = a.coarsest;
     const bool serial = clk != nullptr || cs.far == nullptr;
@@ -1869,6 +1885,22 @@ cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClo
     }
 #undef TRY
     return cudaSuccess;
+}
+
+// The concurrent pass above; when a launch fails part way, the side streams
+// are joined back into the main one (so that a stream capture in progress
+// can end, and no stream is left forked) and the failure is returned.
+template <class R>
+cudaError_t launch_core(const ProductArgs<R> &a, const CoreStreams &cs, StageClock *clk)
+{
+    const cudaError_t e = launch_core_streams<R>(a, cs, clk);
+    if (e != cudaSuccess && clk == nullptr && cs.far != nullptr) {
+        const cudaStream_t side[2] = {cs.far, cs.tr};
+        for (int i = 0; i < 2; ++i)
+            if (side[i] && cudaEventRecord(cs.ev[62 + i], side[i]) == cudaSuccess)
+                cudaStreamWaitEvent(cs.main, cs.ev[62 + i], 0);
+    }
+    return e;
 }
 
 // The k-derivative of the far pass, differentiated stage by stage with the

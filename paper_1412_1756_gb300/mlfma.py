@@ -20,7 +20,7 @@ MIXED_3XTF32 = 3    # FP32 product, tensor-core (3xTF32 split) interpolation
 MAX_LEVELS = 22
 
 (X_PERM, X_LEAF_BOX, X_GRID, X_ALPHA, X_ALPHA_OFFS, X_INTERP, X_BOX_CENTERS, X_NEAR_COUNT, X_ANTERP, X_ALPHA_J,
- X_ALPHA_Y, X_SIB_ALPHA, X_SIB_OFFS) = range(1, 14)
+ X_ALPHA_Y, X_SIB_ALPHA, X_SIB_OFFS, X_WIN_INTERP, X_WIN_ANTERP, X_WIN_SHAPE) = range(1, 17)
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ENOTSUP"}
 
@@ -209,6 +209,8 @@ class MlfmaPlan:
             return buf.view(np.int64)
         if what in (X_LEAF_BOX,):
             return buf.view(np.int32)
+        if what == X_WIN_SHAPE:
+            return buf.view(np.int32).reshape(4, 2)
         if what == X_NEAR_COUNT:
             return buf.view(np.int64)
         if what in (X_ALPHA_OFFS, X_SIB_OFFS):

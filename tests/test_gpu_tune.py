@@ -73,11 +73,12 @@ def test_every_candidate_shape_computes_the_same_product(dt, prec, tol):
     L = 22
     cands = [(0, c) for c in (1, 2, 3)] + [(1, c) for c in (1, 2, 3, 4)] + [(2, c) for c in (1, 2, 3)]
     for l in (2, 3, 4):
-        cands += [(3 + 2 * L + l, c) for c in range(1, 9)]
+        cands += [(3 + 2 * L + l, c) for c in range(1, 12 if prec == M.FP32 else 9)]
         if l < 4:
             cands += [(3 + l, c) for c in (1, 2, 4, 8, 16)] + [(3 + L + l, c) for c in (1, 2, 4, 8, 16, 104, 108)]
-            if prec == M.FP32:   # interpolation / anterpolation rows in pairs
+            if prec == M.FP32:   # rows in pairs; rows in groups of four on windows
                 cands += [(3 + l, c) for c in (202, 204, 208, 216)] + [(3 + L + l, c) for c in (204, 208, 216)]
+                cands += [(3 + l, c) for c in (304, 308, 316)] + [(3 + L + l, c) for c in (304, 308, 316)]
     for field, c in cands:
         ch = np.zeros(M.TUNE_FIELDS, np.int32)
         ch[field] = c
@@ -115,7 +116,7 @@ def test_tune_set_rejects_undocumented_shapes():
     v, t = W.mesh()
     P = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=8)
     good = P.tune_get(4, M.FP32)
-    for field, value in ((0, 4), (1, 5), (2, -1), (3 + 2, 3), (3 + 22 + 2, 100), (3 + 44 + 2, 9)):
+    for field, value in ((0, 4), (1, 5), (2, -1), (3 + 2, 3), (3 + 22 + 2, 100), (3 + 44 + 2, 12)):
         bad = good.copy()
         bad[field] = value
         with pytest.raises(M.MlfmaError):

@@ -208,6 +208,28 @@ def test_interpolation_band_limited(order, tol):
                 assert np.abs(Mx @ fc - fp).max() < tol * np.abs(fp).max()
 
 
+@pytest.mark.parametrize("name", ["sphere-r2m-ico5", "cube8m-6lv", "plate6m-strips"])
+@pytest.mark.parametrize("order", [6, 10])
+def test_windowed_tables_rebuild_the_stencils(name, order):
+    """The FP32 windowed kernels' tables (stencil rows in groups of four on
+    one window of consecutive positions each; pole reflections placed at
+    -i-1 / 2n-i-1, phi positions modulo the grid), expanded the way the
+    kernels read them, give the same interpolation and anterpolation
+    matrices as the row stencils (Section III-C), entry for entry; each
+    window is no wider than the union of four rows of its stencil can be."""
+    W, v, t, P = host_plan(name, interp_order=order)
+    for l in range(2, P.info()["leaf_level"]):
+        sh = P.export(M.X_WIN_SHAPE, l)
+        assert (sh[:, 0] > 0).all(), sh
+        # up: order taps per row, rows at most ~1 source step apart; down: the
+        # transposes, at most ~2 source steps apart per row
+        assert sh[0, 1] <= order + 4 and sh[1, 1] <= order + 4, sh
+        assert sh[2, 1] <= 2 * order + 8 and sh[3, 1] <= 2 * order + 8, sh
+        for wi, plain in ((M.X_WIN_INTERP, M.X_INTERP), (M.X_WIN_ANTERP, M.X_ANTERP)):
+            a, b = P.export(wi, l), P.export(plain, l)
+            assert np.abs(a - b).max() <= 1e-15 * np.abs(b).max()
+
+
 def test_tune_cache_key_and_file(tmp_path):
     """The tuned-shape cache: keys separate GPUs, trees, columns and
     precisions; the file round-trips and a damaged file reads as empty."""
