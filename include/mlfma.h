@@ -248,13 +248,17 @@ mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec
  *                 rows taken in pairs (FP32 only), or 304 / 308 / 316 the
  *                 windowed kernel (rows in groups of four on windows of
  *                 consecutive source samples, MLFMA_X_WIN_SHAPE) with
- *                 4 / 8 / 16 columns (FP32 only)
+ *                 4 / 8 / 16 columns, 404 / 408 the same with 4 / 8 columns
+ *                 and a register budget for one more CTA per SM (FP32 only)
  *   [3 + 22 + l]  down pass from level l: columns per CTA 1..16 (one CTA per
  *                 child), 104 / 108 one CTA per parent with 4 / 8 columns,
  *                 204 / 208 / 216 one CTA per child with 4 / 8 / 16 columns and
  *                 the anterpolation rows taken in pairs (FP32 only), or
- *                 304 / 308 / 316 the windowed kernel with 4 / 8 / 16 columns
- *                 (FP32 only)
+ *                 304 / 308 / 316 the windowed kernel with 4 / 8 / 16 columns,
+ *                 404 / 408 with 4 / 8 columns and a register budget for one
+ *                 more CTA per SM, 504 / 508 the windowed kernel with one CTA
+ *                 per parent (its field loaded once for all its children),
+ *                 4 / 8 columns (FP32 only)
  *   [3 + 44 + l]  translation at level l: 1 two columns per thread; 2..6 one
  *                 column with 1, 2, 4, 8, 16 lanes per output; 7 / 8 one warp
  *                 per (child, sample) with 2 / 1 columns per lane; 9 / 10 / 11

@@ -869,8 +869,9 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
         for (int l = a.coarsest; l <= a.leaf; ++l) {
             pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11}, best.tr[l]);
             if (l < a.leaf) {
-                pick(STAGE_UP + l, {1, 2, 4, 8, 16, 202, 204, 208, 216, 304, 308, 316}, best.up_nb[l]);
-                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108, 204, 208, 216, 304, 308, 316}, best.down_nb[l]);
+                pick(STAGE_UP + l, {1, 2, 4, 8, 16, 202, 204, 208, 216, 304, 308, 316, 404, 408}, best.up_nb[l]);
+                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108, 204, 208, 216, 304, 308, 316, 404, 408, 504, 508},
+                     best.down_nb[l]);
             }
         }
     }
@@ -1383,9 +1384,11 @@ mlfma_status mlfma_tune_set(mlfma_plan_t p, int64_t B, int xc, int prec, const i
                   choices[2] >= 0 && choices[2] <= 3;
         for (int l = 0; l < MLFMA_MAX_LEVELS && ok; ++l) {
             const int u = choices[3 + l], d = choices[3 + MLFMA_MAX_LEVELS + l], r = choices[3 + 2 * MLFMA_MAX_LEVELS + l];
-            auto win = [](int x) { return x == 304 || x == 308 || x == 316; };
+            auto win = [](int x) { return x == 304 || x == 308 || x == 316 || x == 404 || x == 408; };
             ok = (u == 0 || pow2(u) || u == 202 || u == 204 || u == 208 || u == 216 || win(u)) &&
-                 (d == 0 || pow2(d) || d == 104 || d == 108 || d == 204 || d == 208 || d == 216 || win(d)) && r >= 0 && r <= 11;
+                 (d == 0 || pow2(d) || d == 104 || d == 108 || d == 204 || d == 208 || d == 216 || win(d) || d == 504 ||
+                  d == 508) &&
+                 r >= 0 && r <= 11;
         }
         if (!ok) return fail(MLFMA_EINVAL, "a launch-shape choice is outside its documented set");
     }

@@ -1570,7 +1570,8 @@ cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs
                       int nb_choice = 0)
 {
     using C = typename Cx<R>::T;
-    if (nb_choice > 300) {   // 304, 308, 316: windowed FP32 kernel, 4 / 8 / 16 columns per CTA
+    if (nb_choice > 300) {   // 304, 308, 316 windowed FP32 kernel with 4 / 8 / 16 columns per CTA; 404, 408 the
+                             // same with 4 / 8 columns and registers for one more CTA per SM
         if constexpr (sizeof(R) == 4) return launch_up_win(P, Ch, B, Bs, acc, nb_choice - 300, s);
         else return cudaErrorInvalidConfiguration;
     }
@@ -1709,7 +1710,9 @@ cudaError_t launch_down_pp(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, i
 template <class R>
 cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, cudaStream_t s, int nb_choice = 0)
 {
-    if (nb_choice > 300) {   // 304, 308, 316: windowed FP32 kernel, 4 / 8 / 16 columns per CTA
+    if (nb_choice > 300) {   // 304, 308, 316 windowed FP32 kernel with 4 / 8 / 16 columns per CTA; 404, 408 the
+                             // same with 4 / 8 columns and registers for one more CTA per SM; 504, 508 one
+                             // CTA per parent (its field loaded once for all children), 4 / 8 columns
         if constexpr (sizeof(R) == 4) return launch_down_win(P, Ch, B, Bs, nb_choice - 300, s);
         else return cudaErrorInvalidConfiguration;
     }

@@ -197,12 +197,106 @@ __device__ __forceinline__ void st_pair(float2 *dst, float4 v, int cols, bool a1
 // is stored back.
 constexpr int kPF = 4;   // column pairs of the child's own field prefetched per thread
 
+// The phi anterpolation step of one child (shared by the per-child and the
+// per-parent kernels): H (shifted parent, rows padded to nphp + 1) -> U (rows
+// padded to nphc + 1).
 template <int NB>
-__global__ void __launch_bounds__(256, 3) k_down_win(DevLevel<float> P, DevLevel<float> Ch, int B, int Bs)
+__device__ __forceinline__ void down_phi(const float4 *H4, float4 *U4, const float4 *cph, const int *sph,
+                                         const WinDev &wp, int ntp, int nphp, int nphc)
 {
     constexpr int NCP = NB / 2, RL = 32 / NCP, ES = NB / 2;
+    const int hp = nphp + 1, up = nphc + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int cpi = lane % NCP, rl = lane / NCP;
+    // U(tp, v) = sum_f c H(tp, (s + f) mod nphp); lines tp, groups of child phi v
+    const int blocks = (ntp + RL - 1) / RL;
+    for (Items it(warp, nw, wp.groups); it.blk < blocks; it.next()) {
+        const int g = it.g, tp = it.blk * RL + rl;
+        const int tl = min(tp, ntp - 1);
+        float4 acc[kG];
+#pragma unroll
+        for (int r = 0; r < kG; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        win_periodic<ES>(acc, cph + g * wp.tw, wp.tw, sph[g], nphp, H4 + (size_t)tl * hp * NCP + cpi);
+        if (tp < ntp) {
+#pragma unroll
+            for (int r = 0; r < kG; ++r) {
+                const int v = g * kG + r;
+                if (v < nphc) U4[((size_t)tp * up + v) * NCP + cpi] = acc[r];
+            }
+        }
+    }
+}
+
+// The theta anterpolation step: U -> W (unpadded [Kc][NCP]).
+template <int NB>
+__device__ __forceinline__ void down_theta(const float4 *U4, float4 *W4, const float4 *cth, const int *sth,
+                                           const WinDev &wt, int ntp, int nthc, int nphc)
+{
+    constexpr int NCP = NB / 2, RL = 32 / NCP;
+    const int up = nphc + 1, hc = nphc / 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int cpi = lane % NCP, rl = lane / NCP;
+    // theta: W(j, v) = sum_f c U(row of s + f, v or v + pi); lines v, groups of child theta j
+    const int blocks = (nphc + RL - 1) / RL;
+    for (Items it(warp, nw, wt.groups); it.blk < blocks; it.next()) {
+        const int g = it.g, v = it.blk * RL + rl;
+        const int vl = min(v, nphc - 1), vr = vl + hc < nphc ? vl + hc : vl + hc - nphc;
+        float4 acc[kG];
+#pragma unroll
+        for (int r = 0; r < kG; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        win_theta(acc, cth + g * wt.tw, wt.tw, sth[g], ntp, U4 + vl * NCP + cpi, U4 + vr * NCP + cpi, up * NCP);
+        if (v < nphc) {
+#pragma unroll
+            for (int r = 0; r < kG; ++r) {
+                const int j = g * kG + r;
+                if (j < nthc) W4[((size_t)j * nphc + v) * NCP + cpi] = acc[r];
+            }
+        }
+    }
+}
+
+// dst (the child's incoming field, this thread's column pair) += W; the
+// first PF pairs were prefetched into xin.
+template <int NB, int PF>
+__device__ __forceinline__ void down_add(float2 *dst, const float4 *W4, const float4 (&xin)[PF], int Kc, int Bs,
+                                         int cols, bool a16)
+{
+    constexpr int NCP = NB / 2;
+    const int pc = threadIdx.x % NCP, pslot = threadIdx.x / NCP, npslot = blockDim.x / NCP;
+    if (!cols) return;
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        const int q = pslot + k * npslot;
+        if (q < Kc) {
+            const float4 w = W4[q * NCP + pc], x = xin[k];
+            st_pair(dst + (int64_t)q * Bs, make_float4(x.x + w.x, x.y + w.y, x.z + w.z, x.w + w.w), cols, a16);
+        }
+    }
+#pragma unroll 4
+    for (int q = pslot + PF * npslot; q < Kc; q += npslot) {
+        const float4 w = W4[q * NCP + pc], x = ld_pair(dst + (int64_t)q * Bs, cols, a16);
+        st_pair(dst + (int64_t)q * Bs, make_float4(x.x + w.x, x.y + w.y, x.z + w.z, x.w + w.w), cols, a16);
+    }
+}
+
+template <int NB, int PF>
+__device__ __forceinline__ void down_prefetch(float4 (&xin)[PF], const float2 *dst, int Kc, int Bs, int cols, bool a16)
+{
+    constexpr int NCP = NB / 2;
+    const int pslot = threadIdx.x / NCP, npslot = blockDim.x / NCP;
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        const int q = pslot + k * npslot;
+        xin[k] = q < Kc ? ld_pair(dst + (int64_t)q * Bs, cols, a16) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+template <int NB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_down_win(DevLevel<float> P, DevLevel<float> Ch, int B, int Bs)
+{
+    constexpr int NCP = NB / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph, Kp = P.K;
+    const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, ntp = P.nth, nphp = P.nph, Kp = P.K;
     const WinDev wp = P.wd_ph, wt = P.wd_th;
     const int c = blockIdx.x, comp = blockIdx.y, b0 = blockIdx.z * NB;
     const int nb = min(NB, B - b0);
@@ -238,68 +332,74 @@ __global__ void __launch_bounds__(256, 3) k_down_win(DevLevel<float> P, DevLevel
         }
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int cpi = lane % NCP, rl = lane / NCP;
-    // phi: U(tp, v) = sum_f c H(tp, (s + f) mod nphp); lines tp, groups of child phi v
-    {
-        const int blocks = (ntp + RL - 1) / RL;
-        for (Items it(warp, nw, wp.groups); it.blk < blocks; it.next()) {
-            const int g = it.g, tp = it.blk * RL + rl;
-            const int tl = min(tp, ntp - 1);
-            float4 acc[kG];
-#pragma unroll
-            for (int r = 0; r < kG; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-            win_periodic<ES>(acc, cph + g * wp.tw, wp.tw, sph[g], nphp, H4 + (size_t)tl * hp * NCP + cpi);
-            if (tp < ntp) {
-#pragma unroll
-                for (int r = 0; r < kG; ++r) {
-                    const int v = g * kG + r;
-                    if (v < nphc) U4[((size_t)tp * up + v) * NCP + cpi] = acc[r];
-                }
-            }
-        }
-    }
+    down_phi<NB>(H4, U4, cph, sph, wp, ntp, nphp, nphc);
     __syncthreads();
-    float4 xin[kPF];
-#pragma unroll
-    for (int k = 0; k < kPF; ++k) {
-        const int q = pslot + k * npslot;
-        xin[k] = q < Kc ? ld_pair(dst + (int64_t)q * Bs, cols, a16) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    // theta: W(j, v) = sum_f c U(row of s + f, v or v + pi); lines v, groups of child theta j
-    float4 *W4 = H4;
-    {
-        const int blocks = (nphc + RL - 1) / RL;
-        for (Items it(warp, nw, wt.groups); it.blk < blocks; it.next()) {
-            const int g = it.g, v = it.blk * RL + rl;
-            const int vl = min(v, nphc - 1), vr = vl + hc < nphc ? vl + hc : vl + hc - nphc;
-            float4 acc[kG];
-#pragma unroll
-            for (int r = 0; r < kG; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-            win_theta(acc, cth + g * wt.tw, wt.tw, sth[g], ntp, U4 + vl * NCP + cpi, U4 + vr * NCP + cpi, up * NCP);
-            if (v < nphc) {
-#pragma unroll
-                for (int r = 0; r < kG; ++r) {
-                    const int j = g * kG + r;
-                    if (j < nthc) W4[((size_t)j * nphc + v) * NCP + cpi] = acc[r];
-                }
-            }
-        }
-    }
+    constexpr int PF = MINB >= 4 ? 1 : kPF;   // fewer prefetch registers for the tighter budget
+    float4 xin[PF];
+    down_prefetch<NB, PF>(xin, dst, Kc, Bs, cols, a16);
+    down_theta<NB>(U4, H4, cth, sth, wt, ntp, nthc, nphc);
     __syncthreads();
-    if (!cols) return;
-#pragma unroll
-    for (int k = 0; k < kPF; ++k) {
-        const int q = pslot + k * npslot;
-        if (q < Kc) {
-            const float4 w = W4[q * NCP + pc], x = xin[k];
-            st_pair(dst + (int64_t)q * Bs, make_float4(x.x + w.x, x.y + w.y, x.z + w.z, x.w + w.w), cols, a16);
-        }
+    down_add<NB, PF>(dst, H4, xin, Kc, Bs, cols, a16);
+}
+
+// One CTA per (parent box, component, chunk of NB columns), 256 threads:
+// the parent's incoming field is copied into shared memory once (R, rows
+// padded) and each child in turn takes it through the shift (R -> H), the
+// two anterpolation steps and the addition into its own field, so siblings
+// do not fetch the parent again.
+template <int NB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_down_win_pp(DevLevel<float> P, DevLevel<float> Ch, int B, int Bs)
+{
+    constexpr int NCP = NB / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, ntp = P.nth, nphp = P.nph, Kp = P.K;
+    const WinDev wp = P.wd_ph, wt = P.wd_th;
+    const int p = blockIdx.x, comp = blockIdx.y, b0 = blockIdx.z * NB;
+    const int nb = min(NB, B - b0);
+    const int hp = nphp + 1, up = nphc + 1;
+    float4 *R4 = reinterpret_cast<float4 *>(smem_raw);   // [ntp][hp][NCP] the parent as loaded
+    float4 *H4 = R4 + (size_t)ntp * hp * NCP;             // [ntp][hp][NCP] shifted; then W [Kc][NCP]
+    float4 *U4 = H4 + (size_t)ntp * hp * NCP;             // [ntp][up][NCP]
+    float4 *cph = U4 + (size_t)ntp * up * NCP;
+    float4 *cth = cph + wp.groups * wp.tw;
+    int *sph = reinterpret_cast<int *>(cth + wt.groups * wt.tw);
+    int *sth = sph + wp.groups;
+    const int pc = threadIdx.x % NCP, pslot = threadIdx.x / NCP, npslot = blockDim.x / NCP;
+    const int cols = pair_cols(pc, nb);
+    const bool a16 = (Bs % 2) == 0 && ((reinterpret_cast<uintptr_t>(P.G) | reinterpret_cast<uintptr_t>(Ch.G)) & 15) == 0;
+    {
+        const float2 *g = reinterpret_cast<const float2 *>(P.G) + ((int64_t)p * 2 + comp) * Kp * Bs + b0 + 2 * pc;
+        Walk w(pslot, npslot, nphp);
+        for (int q = pslot; q < Kp; q += npslot, w.next()) cp_pair(R4 + (w.t * hp + w.u) * NCP + pc, g + (int64_t)q * Bs, cols, a16);
+        stage_table(wp, cph, sph);
+        stage_table(wt, cth, sth);
+        cp_commit();
     }
+    constexpr int PF = MINB >= 4 ? 1 : kPF;
+    const int c0 = P.child_ptr[p], c1 = P.child_ptr[p + 1];
+    for (int c = c0; c < c1; ++c) {
+        float2 *dst = reinterpret_cast<float2 *>(Ch.G) + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + 2 * pc;
+        const float2 *sh = reinterpret_cast<const float2 *>(P.shift) + (int64_t)Ch.octant[c] * Kp;
+        cp_wait<0>();
+        if (c == c0) __syncthreads();   // the tables (copied by other threads) are in
+        Walk w(pslot, npslot, nphp);
 #pragma unroll 4
-    for (int q = pslot + kPF * npslot; q < Kc; q += npslot) {
-        const float4 w = W4[q * NCP + pc], x = ld_pair(dst + (int64_t)q * Bs, cols, a16);
-        st_pair(dst + (int64_t)q * Bs, make_float4(x.x + w.x, x.y + w.y, x.z + w.z, x.w + w.w), cols, a16);
+        for (int q = pslot; q < Kp; q += npslot, w.next()) {   // the pairs this thread copied
+            const int i = (w.t * hp + w.u) * NCP + pc;
+            const float2 z = sh[q];
+            const float4 h = R4[i];
+            H4[i] = make_float4(fmaf(z.x, h.x, z.y * h.y), fmaf(z.x, h.y, -z.y * h.x), fmaf(z.x, h.z, z.y * h.w),
+                                fmaf(z.x, h.w, -z.y * h.z));
+        }
+        __syncthreads();
+        down_phi<NB>(H4, U4, cph, sph, wp, ntp, nphp, nphc);
+        __syncthreads();
+        float4 xin[PF];
+        down_prefetch<NB, PF>(xin, dst, Kc, Bs, cols, a16);
+        down_theta<NB>(U4, H4, cth, sth, wt, ntp, nthc, nphc);
+        __syncthreads();
+        down_add<NB, PF>(dst, H4, xin, Kc, Bs, cols, a16);
+        __syncthreads();   // W (over H) is read before the next child's shift writes H
     }
 }
 
@@ -312,9 +412,9 @@ __global__ void __launch_bounds__(256, 3) k_down_win(DevLevel<float> P, DevLevel
 // phi index; T rows padded by one element), phi interpolation of T with the
 // shift accumulated into O (lines = band rows; O and Z rows padded); one
 // store of the parent's band at the end.
-template <int NB>
-__global__ void __launch_bounds__(256, 2) k_up_win(DevLevel<float> P, DevLevel<float> Ch, int B, int RS, int Bs,
-                                                   int accumulate)
+template <int NB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_up_win(DevLevel<float> P, DevLevel<float> Ch, int B, int RS, int Bs,
+                                                      int accumulate)
 {
     constexpr int NCP = NB / 2, RL = 32 / NCP, ES = NB / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -457,29 +557,47 @@ size_t up_win_smem(const DevLevel<float> &P, const DevLevel<float> &Ch, int NB, 
            (size_t)nr * (P.nph + 1) * sizeof(float2) + 16 + win_table_bytes(band_t, P.wu_ph);
 }
 
-template <int NB>
+// MINB: CTAs per SM the register budget is set for (3 or 4 for down, 2 or 3 for up)
+template <int NB, int MINB>
 cudaError_t down_win_nb(const DevLevel<float> &P, const DevLevel<float> &Ch, int B, int Bs, cudaStream_t s)
 {
     const size_t smem = down_win_smem(P, Ch, NB);
     if (smem > kWinSmemCap) return cudaErrorInvalidConfiguration;
     dim3 grid(Ch.nbox, 2, (B + NB - 1) / NB);
-    k_down_win<NB><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
+    k_down_win<NB, MINB><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
     return cudaGetLastError();
 }
 
-template <int NB>
+size_t down_win_pp_smem(const DevLevel<float> &P, const DevLevel<float> &Ch, int NB)
+{
+    return ((size_t)2 * P.nth * (P.nph + 1) + (size_t)P.nth * (Ch.nph + 1)) * NB * sizeof(float2) +
+           win_table_bytes(P.wd_ph, P.wd_th);
+}
+
+template <int NB, int MINB>
+cudaError_t down_win_pp_nb(const DevLevel<float> &P, const DevLevel<float> &Ch, int B, int Bs, cudaStream_t s)
+{
+    const size_t smem = down_win_pp_smem(P, Ch, NB);
+    if (smem > kWinSmemCap) return cudaErrorInvalidConfiguration;
+    dim3 grid(P.nbox, 2, (B + NB - 1) / NB);
+    k_down_win_pp<NB, MINB><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
+    return cudaGetLastError();
+}
+
+template <int NB, int MINB>
 cudaError_t up_win_nb(const DevLevel<float> &P, const DevLevel<float> &Ch, int B, int Bs, int acc, cudaStream_t s)
 {
-    // bands of parent theta groups: shared memory for two CTAs per SM, and
+    // bands of parent theta groups: shared memory for MINB CTAs per SM, and
     // enough CTAs to fill the GPU
+    const size_t cap = (size_t)(MINB >= 3 ? 72 : 100) * 1024;
     int RS = 1;
-    while (RS < P.wu_th.groups && up_win_smem(P, Ch, NB, RS) > (size_t)(100 * 1024)) ++RS;
+    while (RS < P.wu_th.groups && up_win_smem(P, Ch, NB, RS) > cap) ++RS;
     const int64_t ctas = (int64_t)P.nbox * 2 * ((B + NB - 1) / NB);
     while (ctas * RS < 4 * 152 && 2 * RS <= P.wu_th.groups) RS *= 2;
     const size_t smem = up_win_smem(P, Ch, NB, RS);
     if (smem > kWinSmemCap) return cudaErrorInvalidConfiguration;
     dim3 grid(P.nbox, 2, ((B + NB - 1) / NB) * RS);
-    k_up_win<NB><<<grid, 256, smem, s>>>(P, Ch, B, RS, Bs, acc);
+    k_up_win<NB, MINB><<<grid, 256, smem, s>>>(P, Ch, B, RS, Bs, acc);
     return cudaGetLastError();
 }
 
@@ -492,9 +610,13 @@ cudaError_t launch_down_win(const DevLevel<float> &P, const DevLevel<float> &Ch,
 {
     if (!win_ok(P.wd_ph, P.wd_th) || B < 1) return cudaErrorInvalidConfiguration;
     switch (nb) {
-    case 4: return down_win_nb<4>(P, Ch, B, Bs, s);
-    case 8: return down_win_nb<8>(P, Ch, B, Bs, s);
-    case 16: return down_win_nb<16>(P, Ch, B, Bs, s);
+    case 4: return down_win_nb<4, 3>(P, Ch, B, Bs, s);
+    case 8: return down_win_nb<8, 3>(P, Ch, B, Bs, s);
+    case 16: return down_win_nb<16, 3>(P, Ch, B, Bs, s);
+    case 104: return down_win_nb<4, 4>(P, Ch, B, Bs, s);
+    case 108: return down_win_nb<8, 4>(P, Ch, B, Bs, s);
+    case 204: return down_win_pp_nb<4, 3>(P, Ch, B, Bs, s);
+    case 208: return down_win_pp_nb<8, 2>(P, Ch, B, Bs, s);
     default: return cudaErrorInvalidConfiguration;
     }
 }
@@ -504,9 +626,11 @@ cudaError_t launch_up_win(const DevLevel<float> &P, const DevLevel<float> &Ch, i
 {
     if (!win_ok(P.wu_th, P.wu_ph) || B < 1) return cudaErrorInvalidConfiguration;
     switch (nb) {
-    case 4: return up_win_nb<4>(P, Ch, B, Bs, acc, s);
-    case 8: return up_win_nb<8>(P, Ch, B, Bs, acc, s);
-    case 16: return up_win_nb<16>(P, Ch, B, Bs, acc, s);
+    case 4: return up_win_nb<4, 2>(P, Ch, B, Bs, acc, s);
+    case 8: return up_win_nb<8, 2>(P, Ch, B, Bs, acc, s);
+    case 16: return up_win_nb<16, 2>(P, Ch, B, Bs, acc, s);
+    case 104: return up_win_nb<4, 3>(P, Ch, B, Bs, acc, s);
+    case 108: return up_win_nb<8, 3>(P, Ch, B, Bs, acc, s);
     default: return cudaErrorInvalidConfiguration;
     }
 }
@@ -515,8 +639,11 @@ cudaError_t prime_win_kernels()
 {
     cudaError_t e;
 #define ALLOW(k) do { if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmemCap)) != cudaSuccess) return e; } while (0)
-    ALLOW(k_down_win<4>); ALLOW(k_down_win<8>); ALLOW(k_down_win<16>);
-    ALLOW(k_up_win<4>); ALLOW(k_up_win<8>); ALLOW(k_up_win<16>);
+    ALLOW((k_down_win<4, 3>)); ALLOW((k_down_win<8, 3>)); ALLOW((k_down_win<16, 3>));
+    ALLOW((k_down_win<4, 4>)); ALLOW((k_down_win<8, 4>));
+    ALLOW((k_down_win_pp<4, 3>)); ALLOW((k_down_win_pp<8, 2>));
+    ALLOW((k_up_win<4, 2>)); ALLOW((k_up_win<8, 2>)); ALLOW((k_up_win<16, 2>));
+    ALLOW((k_up_win<4, 3>)); ALLOW((k_up_win<8, 3>));
 #undef ALLOW
     return cudaSuccess;
 }

@@ -1,5 +1,6 @@
 """FP32 windowed interpolation and anterpolation kernels (tune values 304 /
-308 / 316, 4 / 8 / 16 columns per CTA): the stencil rows of Section III-C in
+308 / 316, 4 / 8 / 16 columns per CTA; 404 / 408 with a register budget for
+one more CTA per SM; down pass 504 / 508 with one CTA per parent): the stencil rows of Section III-C in
 groups of four on windows of consecutive source samples, the theta windows
 running over the pole reflections.  The tables are pinned on CPU
 (test_plan_host.py: they rebuild the row stencils exactly); here the kernels
@@ -26,7 +27,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_1412_1756_gb300 import mlfma as M  # noqa: E402
 
-WIN = (304, 308, 316)
+WIN = (304, 308, 316, 404, 408)
 
 
 def rel(a, b):
@@ -60,9 +61,9 @@ def test_each_stage_matches_builtin(name, B, cplx):
     y0 = P.matvec(xd).cpu().numpy()
     info = P.info()
     for l in range(2, info["leaf_level"]):
-        for field in (3 + l, 3 + M.MAX_LEVELS + l):
+        for field, shapes in ((3 + l, WIN), (3 + M.MAX_LEVELS + l, WIN + (504, 508))):
             ran = []
-            for c in WIN:
+            for c in shapes:
                 pin(P, B, [(field, c)], complex_x=cplx)
                 try:
                     y = P.matvec(xd).cpu().numpy()
@@ -88,8 +89,8 @@ def test_all_levels_fields_and_oracle_rows():
     info = P.info()
     P.matvec(torch.from_numpy(x).to("cuda", torch.float64))
     f64 = {(w, l): P.export_field(M.FP64, w, l, B) for l in range(2, info["leaf_level"] + 1) for w in (0, 1)}
-    for c in (304, 308):   # 16 columns do not fit the down kernel at this plate's level 2
-        pin(P, B, all_levels(info, c))
+    for c in (304, 308, 404, 504):   # 16 columns do not fit the down kernel at this plate's level 2
+        pin(P, B, all_levels(info, c) if c < 500 else [(3 + M.MAX_LEVELS + l, c) for l in range(2, info["leaf_level"])])
         y = P.matvec(torch.from_numpy(x).to("cuda", torch.float32)).cpu().numpy()
         for (w, l), ref in f64.items():
             e = rel(P.export_field(M.FP32, w, l, B).astype(np.complex128), ref)
