@@ -143,8 +143,9 @@ __global__ void __launch_bounds__(256) k_near(DevNear nr, const typename Cx<R>::
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *xs = reinterpret_cast<R *>(smem_raw);
     __shared__ C red[256];
-    const int box = blockIdx.x;
-    const int b0 = blockIdx.y * BT;
+    // column chunk fastest in the grid: the CTAs that share a row's DRAM lines run together
+    const int nch = (B + BT - 1) / BT, box = blockIdx.x / nch;
+    const int b0 = (blockIdx.x - box * nch) * BT;
     const int nb = min(BT, B - b0);
     const int r0 = nr.box_ptr[box];
     const int nrow = nr.box_ptr[box + 1] - r0;
@@ -318,8 +319,9 @@ __global__ void __launch_bounds__(256) k_radiate(const int32_t *__restrict__ box
     using C4 = typename Cx<R>::T4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *xs = reinterpret_cast<R *>(smem_raw);
-    const int box = blockIdx.x;
-    const int b0 = blockIdx.y * Bt;
+    // column chunk fastest in the grid: the CTAs that share a row's DRAM lines run together
+    const int nch = (B + Bt - 1) / Bt, box = blockIdx.x / nch;
+    const int b0 = (blockIdx.x - box * nch) * Bt;
     const int nb = min(Bt, B - b0);
     const int j0 = box_ptr[box], nj = box_ptr[box + 1] - j0;
     for (int e = threadIdx.x; e < nj * nb; e += blockDim.x)
@@ -635,9 +637,10 @@ __global__ void __launch_bounds__(256) k_up(DevLevel<R> P, DevLevel<R> Ch, int B
     constexpr int PF = 8;   // prefetch registers per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Kc = Ch.K, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph;
-    const int p = blockIdx.x, comp = blockIdx.y;
-    const int nbc = (B + NB - 1) / NB;
-    const int b0 = (blockIdx.z % nbc) * NB, rs = blockIdx.z / nbc;
+    // column chunk fastest in the grid, then the band, then the parent
+    const int comp = blockIdx.y;
+    const int nbc = (B + NB - 1) / NB, p = blockIdx.x / (nbc * RS), rem = blockIdx.x - p * (nbc * RS);
+    const int rs = rem / nbc, b0 = (rem - rs * nbc) * NB;
     const int rows = up_band_rows(ntp, RS, RB), t0 = rs * rows, t1 = min(ntp, t0 + rows);
     if (t0 >= t1) return;
     const int nr = t1 - t0;
@@ -807,8 +810,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 && TM <= 20) ? (RB == 1 ?
     constexpr int CP = ColPair<R, NB>::CP, NL = NB / CP, PW = NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph, Kp = P.K;
-    const int c = blockIdx.x, comp = blockIdx.y;
-    const int b0 = blockIdx.z * NB;
+    // column chunk fastest in the grid: the CTAs that share a row's DRAM lines run together
+    const int nbc = (B + NB - 1) / NB, c = blockIdx.x / nbc, comp = blockIdx.y;
+    const int b0 = (blockIdx.x - c * nbc) * NB;
     const int nb = min(NB, B - b0);
     const int hp = nphp + 1;                   // H row pitch per parent theta row (one pad row)
     C *H = reinterpret_cast<C *>(smem_raw);   // [ntp][hp][PW]; later the child result [Kc][PW]
@@ -957,7 +961,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 && TM <= 20) ? 2 : 1)
     constexpr int CP = ColPair<R, NB>::CP, NL = NB / CP, PW = NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph, Kp = P.K;
-    const int p = blockIdx.x, comp = blockIdx.y, b0 = blockIdx.z * NB;
+    const int nbc = (B + NB - 1) / NB, p = blockIdx.x / nbc, comp = blockIdx.y, b0 = (blockIdx.x - p * nbc) * NB;
     const int nb = min(NB, B - b0);
     const int hp = nphp + 1;
     C *Gp = reinterpret_cast<C *>(smem_raw);   // [Kp][PW] the parent's field
@@ -1079,8 +1083,9 @@ __global__ void __launch_bounds__(256) k_receive(const int32_t *__restrict__ box
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *Gs = reinterpret_cast<C *>(smem_raw);   // [2][K][LB]
     const int K = lf.K;
-    const int box = blockIdx.x;
-    const int b0 = blockIdx.y * LB;
+    // column chunk fastest in the grid: the CTAs that share a row's DRAM lines run together
+    const int nch = (B + LB - 1) / LB, box = blockIdx.x / nch;
+    const int b0 = (blockIdx.x - box * nch) * LB;
     const int nb = min(LB, B - b0);
     const C *G = reinterpret_cast<const C *>(lf.G) + (int64_t)box * 2 * K * Bs + b0;
     for (int e = threadIdx.x; e < 2 * K * LB; e += blockDim.x) {
@@ -1138,8 +1143,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_receive_tiled(c
     C *Gbuf = reinterpret_cast<C *>(Vbuf + 2 * VSZ);             // [2][GSZ]
     R *Wbuf = reinterpret_cast<R *>(Gbuf + 2 * GSZ);             // [2][QT]
     const int K = lf.K;
-    const int box = blockIdx.x;
-    const int b0 = blockIdx.y * NB;
+    // column chunk fastest in the grid: the CTAs that share a row's DRAM lines run together
+    const int nch = (B + NB - 1) / NB, box = blockIdx.x / nch;
+    const int b0 = (blockIdx.x - box * nch) * NB;
     const int bb = threadIdx.x % NB, grp = threadIdx.x / NB;
     const bool bok = b0 + bb < B;
     const int i0 = box_ptr[box], nrows = box_ptr[box + 1] - i0;
@@ -1233,8 +1239,9 @@ __global__ void __launch_bounds__(256) k_radiate_tiled(const int32_t *__restrict
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *xs = reinterpret_cast<R *>(smem_raw);   // [nj][NB]
     constexpr int NS = 256 / NB;
-    const int box = blockIdx.x;
-    const int b0 = blockIdx.y * NB;
+    // column chunk fastest in the grid: the CTAs that share a row's DRAM lines run together
+    const int nch = (B + NB - 1) / NB, box = blockIdx.x / nch;
+    const int b0 = (blockIdx.x - box * nch) * NB;
     const int bb = threadIdx.x % NB, slot = threadIdx.x / NB;
     const int j0 = box_ptr[box], nj = box_ptr[box + 1] - j0;
     for (int e = threadIdx.x; e < nj * NB; e += blockDim.x) {
@@ -1366,7 +1373,7 @@ template <class R, int BT>
 cudaError_t launch_near_bt(const ProductArgs<R> &a, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
-    dim3 grid(a.nr.nleaf, (a.B + BT - 1) / BT);
+    dim3 grid(a.nr.nleaf * ((a.B + BT - 1) / BT));
     const size_t smem = (size_t)a.nr.max_cols * BT * sizeof(R);
     if (smem <= (size_t)kStageCap) {
         k_near<R, BT, true><<<grid, 256, smem, s>>>(a.nr, reinterpret_cast<const C *>(a.near_val), a.xp,
@@ -1416,7 +1423,7 @@ cudaError_t launch_radiate_tiled(const ProductArgs<R> &a, int Bs, cudaStream_t s
     const DevLevel<R> &Lf = a.lv[a.leaf];
     const size_t smem = (size_t)a.nr.max_rows * NB * sizeof(R);
     if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
-    dim3 grid(Lf.nbox, (a.B + NB - 1) / NB);
+    dim3 grid(Lf.nbox * ((a.B + NB - 1) / NB));
     k_radiate_tiled<R, NB, QB><<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), a.xp,
                                                        reinterpret_cast<C *>(Lf.S), Lf.K, a.B, Bs);
     return cudaGetLastError();
@@ -1453,7 +1460,7 @@ cudaError_t launch_radiate(const ProductArgs<R> &a, int Bs, cudaStream_t s, int 
     int Bt = std::min(a.B, 32);
     while (Bt > 1 && (size_t)a.nr.max_rows * Bt * sizeof(R) > (size_t)kStageCap) Bt /= 2;
     const size_t smem = (size_t)a.nr.max_rows * Bt * sizeof(R);
-    dim3 grid(Lf.nbox, (a.B + Bt - 1) / Bt);
+    dim3 grid(Lf.nbox * ((a.B + Bt - 1) / Bt));
     k_radiate<R><<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), a.xp,
                                          reinterpret_cast<C *>(Lf.S), Lf.K, a.B, Bt, Bs);
     return cudaGetLastError();
@@ -1465,7 +1472,7 @@ cudaError_t launch_receive_lb(const ProductArgs<R> &a, int Bs, cudaStream_t s)
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
     const DevLevel<R> &Lf = a.lv[a.leaf];
-    dim3 grid(Lf.nbox, (a.B + LB - 1) / LB);
+    dim3 grid(Lf.nbox * ((a.B + LB - 1) / LB));
     const size_t smem = (size_t)2 * Lf.K * LB * sizeof(C);
     k_receive<R, LB><<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), Lf,
                                              reinterpret_cast<C *>(a.yp), a.B, Bs);
@@ -1478,7 +1485,7 @@ cudaError_t launch_receive_tiled(const ProductArgs<R> &a, int Bs, cudaStream_t s
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
     const DevLevel<R> &Lf = a.lv[a.leaf];
-    dim3 grid(Lf.nbox, (a.B + NB - 1) / NB);
+    dim3 grid(Lf.nbox * ((a.B + NB - 1) / NB));
     constexpr int NG = 256 / NB, MAXR = NB / 4, QT = 16;
     const size_t smem = 2 * ((size_t)NG * MAXR * (QT + 1) * sizeof(C4) + (size_t)2 * QT * NB * sizeof(C) + QT * sizeof(R));
     k_receive_tiled<R, NB, MAXR><<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const C4 *>(a.V), Lf,
@@ -1522,7 +1529,7 @@ cudaError_t launch_up_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int
     if (smem_of(RS) > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
     const int64_t ctas = (int64_t)P.nbox * 2 * ((B + NB - 1) / NB);
     while (ctas * RS < 8 * 152 && 2 * RS <= P.nth / 2) RS *= 2;
-    dim3 grid(P.nbox, 2, ((B + NB - 1) / NB) * RS);
+    dim3 grid(P.nbox * ((B + NB - 1) / NB) * RS, 2);
     k_up<R, NB, PO, RB><<<grid, 256, smem_of(RS), s>>>(P, Ch, B, RS, Bs, acc);
     return cudaGetLastError();
 }
@@ -1658,7 +1665,7 @@ cudaError_t launch_translate(const DevLevel<R> &Lv, int B, int Bs, int acc, cuda
 template <class R, int NB, int TM, int RB>
 cudaError_t launch_down_nb(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs, size_t smem, cudaStream_t s)
 {
-    dim3 grid(Ch.nbox, 2, (B + NB - 1) / NB);
+    dim3 grid(Ch.nbox * ((B + NB - 1) / NB), 2);
     k_down<R, NB, TM, RB><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
     return cudaGetLastError();
 }
@@ -1697,7 +1704,7 @@ cudaError_t launch_down_pp(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, i
     const size_t per_col = ((size_t)2 * P.K + (size_t)P.nth + (size_t)P.nth * Ch.nph + (size_t)Ch.K) * sizeof(C);
     const size_t smem = per_col * NB;
     if (smem > (size_t)kSmemCap) return cudaErrorInvalidConfiguration;
-    dim3 grid(P.nbox, 2, (B + NB - 1) / NB);
+    dim3 grid(P.nbox * ((B + NB - 1) / NB), 2);
     switch (P.dn_taps) {
     case 16: k_down_pp<R, NB, 16><<<grid, 256, smem, s>>>(P, Ch, B, Bs); break;
     case 20: k_down_pp<R, NB, 20><<<grid, 256, smem, s>>>(P, Ch, B, Bs); break;

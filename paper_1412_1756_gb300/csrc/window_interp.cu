@@ -298,7 +298,8 @@ __global__ void __launch_bounds__(256, MINB) k_down_win(DevLevel<float> P, DevLe
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, ntp = P.nth, nphp = P.nph, Kp = P.K;
     const WinDev wp = P.wd_ph, wt = P.wd_th;
-    const int c = blockIdx.x, comp = blockIdx.y, b0 = blockIdx.z * NB;
+    // column chunk fastest in the grid: the CTAs that share a field row's DRAM lines run together
+    const int nbc = (B + NB - 1) / NB, c = blockIdx.x / nbc, comp = blockIdx.y, b0 = (blockIdx.x - c * nbc) * NB;
     const int nb = min(NB, B - b0);
     const int hp = nphp + 1, up = nphc + 1;
     float4 *H4 = reinterpret_cast<float4 *>(smem_raw);   // [ntp][hp][NCP]; then W [Kc][NCP]
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(256, MINB) k_down_win_pp(DevLevel<float> P, De
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, ntp = P.nth, nphp = P.nph, Kp = P.K;
     const WinDev wp = P.wd_ph, wt = P.wd_th;
-    const int p = blockIdx.x, comp = blockIdx.y, b0 = blockIdx.z * NB;
+    const int nbc = (B + NB - 1) / NB, p = blockIdx.x / nbc, comp = blockIdx.y, b0 = (blockIdx.x - p * nbc) * NB;
     const int nb = min(NB, B - b0);
     const int hp = nphp + 1, up = nphc + 1;
     float4 *R4 = reinterpret_cast<float4 *>(smem_raw);   // [ntp][hp][NCP] the parent as loaded
@@ -420,8 +421,9 @@ __global__ void __launch_bounds__(256, MINB) k_up_win(DevLevel<float> P, DevLeve
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, hc = nphc / 2, ntp = P.nth, nphp = P.nph, Kp = P.K;
     const WinDev wt = P.wu_th, wp = P.wu_ph;
-    const int p = blockIdx.x, comp = blockIdx.y;
-    const int nbc = (B + NB - 1) / NB, b0 = (blockIdx.z % nbc) * NB, band = blockIdx.z / nbc;
+    // column chunk fastest in the grid, then the band, then the parent
+    const int nbc = (B + NB - 1) / NB, comp = blockIdx.y;
+    const int p = blockIdx.x / (nbc * RS), rem = blockIdx.x - p * (nbc * RS), band = rem / nbc, b0 = (rem - band * nbc) * NB;
     const int gpb = (wt.groups + RS - 1) / RS, g0 = band * gpb, g1 = min(wt.groups, g0 + gpb);
     if (g0 >= g1) return;
     const int t0 = g0 * kG, t1 = min(ntp, g1 * kG), nr = t1 - t0;
@@ -563,7 +565,7 @@ cudaError_t down_win_nb(const DevLevel<float> &P, const DevLevel<float> &Ch, int
 {
     const size_t smem = down_win_smem(P, Ch, NB);
     if (smem > kWinSmemCap) return cudaErrorInvalidConfiguration;
-    dim3 grid(Ch.nbox, 2, (B + NB - 1) / NB);
+    dim3 grid(Ch.nbox * ((B + NB - 1) / NB), 2);
     k_down_win<NB, MINB><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
     return cudaGetLastError();
 }
@@ -579,7 +581,7 @@ cudaError_t down_win_pp_nb(const DevLevel<float> &P, const DevLevel<float> &Ch, 
 {
     const size_t smem = down_win_pp_smem(P, Ch, NB);
     if (smem > kWinSmemCap) return cudaErrorInvalidConfiguration;
-    dim3 grid(P.nbox, 2, (B + NB - 1) / NB);
+    dim3 grid(P.nbox * ((B + NB - 1) / NB), 2);
     k_down_win_pp<NB, MINB><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
     return cudaGetLastError();
 }
@@ -596,7 +598,7 @@ cudaError_t up_win_nb(const DevLevel<float> &P, const DevLevel<float> &Ch, int B
     while (ctas * RS < 4 * 152 && 2 * RS <= P.wu_th.groups) RS *= 2;
     const size_t smem = up_win_smem(P, Ch, NB, RS);
     if (smem > kWinSmemCap) return cudaErrorInvalidConfiguration;
-    dim3 grid(P.nbox, 2, ((B + NB - 1) / NB) * RS);
+    dim3 grid(P.nbox * ((B + NB - 1) / NB) * RS, 2);
     k_up_win<NB, MINB><<<grid, 256, smem, s>>>(P, Ch, B, RS, Bs, acc);
     return cudaGetLastError();
 }
