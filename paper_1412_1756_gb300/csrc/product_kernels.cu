@@ -1498,6 +1498,10 @@ template <class R>
 cudaError_t launch_receive(const ProductArgs<R> &a, int Bs, cudaStream_t s, int choice = 0)
 {
     using C = typename Cx<R>::T;
+    if (choice >= 4 && choice <= 6) {   // two columns per thread, 64 / 32 / 16 columns per CTA (FP32)
+        if constexpr (sizeof(R) == 4) return launch_receive_pairs(a, Bs, 64 >> (choice - 4), s);
+        else return cudaErrorInvalidConfiguration;
+    }
     if (choice == 1) return a.B >= 32 ? launch_receive_tiled<R, 32>(a, Bs, s) : cudaErrorInvalidConfiguration;
     if (choice == 2) return a.B >= 16 ? launch_receive_tiled<R, 16>(a, Bs, s) : cudaErrorInvalidConfiguration;
     if (choice == 3) return a.B >= 8 ? launch_receive_tiled<R, 8>(a, Bs, s) : cudaErrorInvalidConfiguration;
@@ -1776,6 +1780,7 @@ cudaError_t prime_kernels()
 #undef ALLOW
     if (sizeof(R) == 4) {
         if ((e = prime_win_kernels()) != cudaSuccess) return e;
+        if ((e = prime_receive_pairs()) != cudaSuccess) return e;
         return prime_translate_quad();
     }
     return cudaSuccess;

@@ -72,6 +72,8 @@ def test_every_candidate_shape_computes_the_same_product(dt, prec, tol):
     ref = P.matvec(x).cpu().numpy()
     L = 22
     cands = [(0, c) for c in (1, 2, 3)] + [(1, c) for c in (1, 2, 3, 4)] + [(2, c) for c in (1, 2, 3)]
+    if prec == M.FP32:   # reception with two columns per thread
+        cands += [(2, c) for c in (4, 5, 6)]
     for l in (2, 3, 4):
         cands += [(3 + 2 * L + l, c) for c in range(1, 12 if prec == M.FP32 else 9)]
         if l < 4:
