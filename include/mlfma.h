@@ -241,7 +241,9 @@ mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec
  * MLFMA_TUNE_FIELDS int32 values (0 = the built-in choice):
  *   [0] near field: 1 / 2 one CTA per strip with 8 / 16 columns per thread,
  *       3 chunks of 16 columns
- *   [1] radiation: 1 one CTA per box, 2 / 3 / 4 tiles of 32 / 16 / 8 columns
+ *   [1] radiation: 1 one CTA per box, 2 / 3 / 4 tiles of 32 / 16 / 8 columns,
+ *       5 four columns and two samples per thread, 64 columns per CTA (FP32
+ *       only)
  *   [2] reception: 1 / 2 / 3 tiles of 32 / 16 / 8 columns; 4 / 5 / 6 two
  *       columns per thread with the field tile scaled by the weights as it
  *       is staged, 64 / 32 / 16 columns per CTA (FP32 only)

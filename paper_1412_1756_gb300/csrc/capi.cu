@@ -864,7 +864,7 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
     };
     pick(STAGE_NEAR, {1, 2, 3}, best.near);
     if (a.leaf >= a.coarsest) {
-        pick(STAGE_RADIATE, {1, 2, 3, 4}, best.radiate);
+        pick(STAGE_RADIATE, {1, 2, 3, 4, 5}, best.radiate);
         pick(STAGE_RECEIVE, {1, 2, 3, 4, 5, 6}, best.receive);
         for (int l = a.coarsest; l <= a.leaf; ++l) {
             pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11}, best.tr[l]);
@@ -1380,7 +1380,7 @@ mlfma_status mlfma_tune_set(mlfma_plan_t p, int64_t B, int xc, int prec, const i
     {
         // every value must be 0 (built-in) or one of the documented shapes
         auto pow2 = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
-        bool ok = choices[0] >= 0 && choices[0] <= 3 && choices[1] >= 0 && choices[1] <= 4 &&
+        bool ok = choices[0] >= 0 && choices[0] <= 3 && choices[1] >= 0 && choices[1] <= 5 &&
                   choices[2] >= 0 && choices[2] <= 6;
         for (int l = 0; l < MLFMA_MAX_LEVELS && ok; ++l) {
             const int u = choices[3 + l], d = choices[3 + MLFMA_MAX_LEVELS + l], r = choices[3 + 2 * MLFMA_MAX_LEVELS + l];

@@ -268,9 +268,12 @@ cudaError_t launch_translate_quad(const DevLevel<float> &lv, int B, int Bs, int 
 cudaError_t prime_translate_quad();
 
 // Reception of FP32 fields, two columns per thread with the field tile
-// scaled by the weights as it is staged (receive_pairs.cu), NB = 16, 32 or
+// scaled by the weights as it is staged (leaf_pairs.cu), NB = 16, 32 or
 // 64 columns per CTA.
 cudaError_t launch_receive_pairs(const ProductArgs<float> &a, int Bs, int nb, cudaStream_t s);
+// Radiation of FP32 fields, four columns and two samples per thread, 64
+// columns per CTA (leaf_pairs.cu).
+cudaError_t launch_radiate_quads(const ProductArgs<float> &a, int Bs, cudaStream_t s);
 cudaError_t prime_receive_pairs();
 
 }  // namespace mlfma

@@ -1,8 +1,17 @@
-// Reception of FP32 fields at the leaf level (the disaggregation of Section
-// III: y_i += sum_q w_q conj(V_i(q)) . G_m(q) over the samples q of leaf box
-// m, both tangential components, for the unknowns i of the box; w_q carries
-// the quadrature weight and the far constant).
+// Radiation and reception of FP32 fields at the leaf level (Section III:
+// the aggregation S_m(q) = sum_i V_i(q) x_i over the unknowns i of leaf box
+// m, and the disaggregation y_i += sum_q w_q conj(V_i(q)) . G_m(q) over the
+// samples q, both tangential components; w_q carries the quadrature weight
+// and the far constant).
 //
+// Radiation: one CTA per (leaf box, chunk of 64 columns), 256 threads:
+// thread = (four adjacent columns, two samples).  The box's x rows are staged
+// once; the patterns stream through shared memory in steps of (32 samples,
+// 32 rows) by cp.async one step ahead, one barrier per step.  Per row a
+// thread's x quad (one 16-byte load) feeds both samples and both components:
+// 32 FMAs per three 16-byte loads.
+//
+// Reception:
 // One CTA per (leaf box, chunk of 2 NCP columns), 256 threads: thread =
 // (column pair, row group), rows i = group + k * groups.  Tiles of QT
 // samples: the field tile is loaded into registers one tile ahead, scaled by
@@ -153,6 +162,117 @@ __global__ void __launch_bounds__(256) k_receive_pairs(const int32_t *__restrict
     }
 }
 
+constexpr int kRQ = 32;   // samples per radiation step
+constexpr int kRR = 32;   // rows per radiation step
+
+__global__ void __launch_bounds__(256) k_radiate_quads(const int32_t *__restrict__ box_ptr, const float4 *__restrict__ V4,
+                                                       const float *__restrict__ xp, float2 *__restrict__ S, int K,
+                                                       int B, int Bs)
+{
+    constexpr int NQD = 16, NB = 4 * NQD;   // column quads, columns per CTA
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *Vs = reinterpret_cast<float4 *>(smem_raw);   // [2][kRR][kRQ]
+    float4 *xs = Vs + 2 * kRR * kRQ;                     // [rows][NQD] (x of the box, four columns per float4)
+    const int nch = (B + NB - 1) / NB, box = blockIdx.x / nch, b0 = (blockIdx.x - box * nch) * NB;
+    const int nb = min(NB, B - b0);
+    const int qd = threadIdx.x % NQD, ql = threadIdx.x / NQD;   // samples ql and ql + 16 of a step
+    const int cols = max(0, min(4, nb - 4 * qd));
+    const int j0 = box_ptr[box], nj = box_ptr[box + 1] - j0;
+    const bool a16 = (B % 4) == 0 && (Bs % 2) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(xp) | reinterpret_cast<uintptr_t>(S)) & 15) == 0;
+    // x rows of the box (zero past the chunk's columns)
+    for (int e = threadIdx.x; e < nj * NQD; e += blockDim.x) {
+        const int j = e / NQD, d = e - j * NQD, c = max(0, min(4, nb - 4 * d));
+        const float *src = xp + (int64_t)(j0 + j) * B + b0 + 4 * d;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c == 4 && a16) v = *reinterpret_cast<const float4 *>(src);
+        else {
+            if (c > 0) v.x = src[0];
+            if (c > 1) v.y = src[1];
+            if (c > 2) v.z = src[2];
+            if (c > 3) v.w = src[3];
+        }
+        xs[e] = v;
+    }
+    const int ntile = (K + kRQ - 1) / kRQ, nchk = max(1, (nj + kRR - 1) / kRR), nstep = ntile * nchk;
+    auto stage = [&](int step) {
+        const int tile = step / nchk, chk = step - tile * nchk;
+        const int q0 = tile * kRQ, r0 = chk * kRR, nr = min(kRR, nj - r0);
+        float4 *d = Vs + (step & 1) * kRR * kRQ;
+        for (int e = threadIdx.x; e < kRR * kRQ; e += blockDim.x) {
+            const int r = e / kRQ, qx = e - r * kRQ;
+            if (r < nr && q0 + qx < K) cp16r(d + e, V4 + (int64_t)(j0 + r0 + r) * K + q0 + qx);
+            else d[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        commit_r();
+    };
+    float4 acc[2][2][2];   // [sample][component] (four columns as two float4 of complex pairs)
+    auto zero = [&]() {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int m = 0; m < 2; ++m) acc[a][m][0] = acc[a][m][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    zero();
+    stage(0);
+    for (int step = 0; step < nstep; ++step) {
+        wait_all_r();
+        __syncthreads();   // step's patterns in; everyone is done with the other buffer
+        if (step + 1 < nstep) stage(step + 1);
+        const int tile = step / nchk, chk = step - tile * nchk;
+        const int r0 = chk * kRR, nr = min(kRR, nj - r0);
+        const float4 *vs = Vs + (step & 1) * kRR * kRQ;
+        const float4 *xr = xs + r0 * NQD + qd;
+#pragma unroll 4
+        for (int r = 0; r < nr; ++r) {
+            const float4 x = xr[r * NQD];
+            const float4 va = vs[r * kRQ + ql], vb = vs[r * kRQ + ql + 16];
+            const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const float4 v = s2 ? vb : va;   // (theta re, im, phi re, im) of the row at this sample
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float4 &a0 = acc[s2][0][h], &a1 = acc[s2][1][h];
+                    a0.x = fmaf(v.x, xv[2 * h], a0.x);
+                    a0.y = fmaf(v.y, xv[2 * h], a0.y);
+                    a0.z = fmaf(v.x, xv[2 * h + 1], a0.z);
+                    a0.w = fmaf(v.y, xv[2 * h + 1], a0.w);
+                    a1.x = fmaf(v.z, xv[2 * h], a1.x);
+                    a1.y = fmaf(v.w, xv[2 * h], a1.y);
+                    a1.z = fmaf(v.z, xv[2 * h + 1], a1.z);
+                    a1.w = fmaf(v.w, xv[2 * h + 1], a1.w);
+                }
+            }
+        }
+        if (chk == nchk - 1) {   // the tile's sums are complete: store and restart
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int q = tile * kRQ + ql + 16 * s2;
+                if (q < K && cols) {
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {
+                        float2 *o = S + (((int64_t)box * 2 + m) * K + q) * Bs + b0 + 4 * qd;
+                        if (cols == 4 && a16) {
+                            reinterpret_cast<float4 *>(o)[0] = acc[s2][m][0];
+                            reinterpret_cast<float4 *>(o)[1] = acc[s2][m][1];
+                        } else {
+                            const float2 v4[4] = {make_float2(acc[s2][m][0].x, acc[s2][m][0].y),
+                                                  make_float2(acc[s2][m][0].z, acc[s2][m][0].w),
+                                                  make_float2(acc[s2][m][1].x, acc[s2][m][1].y),
+                                                  make_float2(acc[s2][m][1].z, acc[s2][m][1].w)};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (k < cols) o[k] = v4[k];
+                        }
+                    }
+                }
+            }
+            zero();
+        }
+    }
+}
+
 template <int NCP, int MAXR>
 cudaError_t receive_pairs_nb(const ProductArgs<float> &a, int Bs, cudaStream_t s)
 {
@@ -177,8 +297,21 @@ cudaError_t launch_receive_pairs(const ProductArgs<float> &a, int Bs, int nb, cu
     }
 }
 
+cudaError_t launch_radiate_quads(const ProductArgs<float> &a, int Bs, cudaStream_t s)
+{
+    const DevLevel<float> &Lf = a.lv[a.leaf];
+    const size_t smem = ((size_t)2 * kRR * kRQ + (size_t)a.nr.max_rows * 16) * sizeof(float4);
+    if (smem > (size_t)(96 * 1024)) return cudaErrorInvalidConfiguration;
+    dim3 grid(Lf.nbox * ((a.B + 63) / 64));
+    k_radiate_quads<<<grid, 256, smem, s>>>(a.nr.box_ptr, reinterpret_cast<const float4 *>(a.V), a.xp,
+                                            reinterpret_cast<float2 *>(Lf.S), Lf.K, a.B, Bs);
+    return cudaGetLastError();
+}
+
 cudaError_t prime_receive_pairs()
 {
+    if (cudaError_t e0 = cudaFuncSetAttribute(k_radiate_quads, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024))
+        return e0;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_receive_pairs<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_receive_pairs<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)) != cudaSuccess) return e;

@@ -1436,6 +1436,10 @@ cudaError_t launch_radiate(const ProductArgs<R> &a, int Bs, cudaStream_t s, int 
     using C = typename Cx<R>::T;
     using C4 = typename Cx<R>::T4;
     const DevLevel<R> &Lf = a.lv[a.leaf];
+    if (choice == 5) {   // four columns and two samples per thread, 64 columns per CTA (FP32)
+        if constexpr (sizeof(R) == 4) return launch_radiate_quads(a, Bs, s);
+        else return cudaErrorInvalidConfiguration;
+    }
     if (choice >= 2 && choice <= 4) {
         const int nb = choice == 2 ? 32 : choice == 3 ? 16 : 8;
         if (a.B < nb || (size_t)a.nr.max_rows * nb * sizeof(R) > (size_t)kStageCap) return cudaErrorInvalidConfiguration;

@@ -72,8 +72,8 @@ def test_every_candidate_shape_computes_the_same_product(dt, prec, tol):
     ref = P.matvec(x).cpu().numpy()
     L = 22
     cands = [(0, c) for c in (1, 2, 3)] + [(1, c) for c in (1, 2, 3, 4)] + [(2, c) for c in (1, 2, 3)]
-    if prec == M.FP32:   # reception with two columns per thread
-        cands += [(2, c) for c in (4, 5, 6)]
+    if prec == M.FP32:   # reception with two columns per thread, radiation with four
+        cands += [(2, c) for c in (4, 5, 6)] + [(1, 5)]
     for l in (2, 3, 4):
         cands += [(3 + 2 * L + l, c) for c in range(1, 12 if prec == M.FP32 else 9)]
         if l < 4:
@@ -118,7 +118,7 @@ def test_tune_set_rejects_undocumented_shapes():
     v, t = W.mesh()
     P = M.MlfmaPlan(v, t, W.k, W.levels, W.digits, max_batch=8)
     good = P.tune_get(4, M.FP32)
-    for field, value in ((0, 4), (1, 5), (2, -1), (3 + 2, 3), (3 + 22 + 2, 100), (3 + 44 + 2, 12)):
+    for field, value in ((0, 4), (1, 6), (2, 7), (3 + 2, 3), (3 + 22 + 2, 100), (3 + 44 + 2, 12)):
         bad = good.copy()
         bad[field] = value
         with pytest.raises(M.MlfmaError):
