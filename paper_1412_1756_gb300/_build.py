@@ -18,7 +18,7 @@ LIB_NAME = "libmlfma_gb300.so"
 LIB = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["plan_host.cpp", "setup_kernels.cu", "product_kernels.cu", "capi.cu", "noalloc.cu", "cm_solver.cpp",
-           "plan_set.cu", "krylov.cu", "block_krylov.cu", "umma_interp.cu", "window_interp.cu", "translate_quad.cu", "leaf_pairs.cu"]
+           "plan_set.cu", "krylov.cu", "block_krylov.cu", "umma_interp.cu", "window_interp.cu", "translate_quad.cu", "leaf_pairs.cu", "arnoldi_device.cu"]
 
 
 def _nvcc():

@@ -785,16 +785,22 @@ extern "C" mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opt
         return MLFMA_OK;
     };
 
+    // the Arnoldi basis V_0..V_m lives on the device (FP64); the host keeps the
+    // vector the next operator application needs and the Hessenberg matrix
     const int m = o.ncv, k = o.nev;
-    std::vector<std::vector<cd>> V(m + 1, std::vector<cd>(n));
+    std::string derr;
+    std::unique_ptr<DeviceArnoldi, void (*)(DeviceArnoldi *)> arn(arnoldi_create(plan, n, m, derr), arnoldi_destroy);
+    if (!arn) return fail(MLFMA_ECUDA, derr);
+    std::vector<cd> vj(n), wv(n), hcol(m + 1);
     std::vector<cd> Hm((size_t)(m + 1) * m, 0.0);   // (m+1) x m, row-major
     std::mt19937_64 rng(o.seed);
     std::normal_distribution<double> nd(0.0, 1.0);
-    for (int64_t i = 0; i < n; ++i) V[0][i] = nd(rng);
+    for (int64_t i = 0; i < n; ++i) vj[i] = nd(rng);
     {
-        const double v0 = nrm2(V[0]);
-        for (auto &z : V[0]) z /= v0;
+        const double v0 = nrm2(vj);
+        for (auto &z : vj) z /= v0;
     }
+    if (!arnoldi_set(arn.get(), 0, vj.data(), derr)) return fail(MLFMA_ECUDA, derr);
     int kstart = 0, restarts = 0;
     bool converged = false;
     std::vector<cd> w, X;
@@ -802,23 +808,19 @@ extern "C" mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opt
     mlfma_status st;
     for (; restarts < o.max_restarts; ++restarts) {
         for (int j = kstart; j < m; ++j) {   // extend the Arnoldi factorisation to m steps
-            if ((st = op(V[j].data(), V[j + 1].data()))) return st;
-            for (int pass = 0; pass < 2; ++pass)
-                for (int i = 0; i <= j; ++i) {
-                    const cd h = dotc(V[i].data(), V[j + 1].data(), n);
-                    Hm[(size_t)i * m + j] += h;
-                    for (int64_t q = 0; q < n; ++q) V[j + 1][q] -= h * V[i][q];
-                }
-            const double hn = nrm2(V[j + 1]);
+            if ((st = op(vj.data(), wv.data()))) return st;
+            std::fill(hcol.begin(), hcol.end(), cd(0.0));
+            double hn = 0;
+            if (!arnoldi_extend(arn.get(), j, wv.data(), hcol.data(), &hn, j + 1 < m ? vj.data() : nullptr, derr))
+                return fail(MLFMA_ECUDA, derr);
+            for (int i = 0; i <= j; ++i) Hm[(size_t)i * m + j] += hcol[i];
             Hm[(size_t)(j + 1) * m + j] = hn;
-            if (hn > 0)
-                for (auto &z : V[j + 1]) z /= hn;
         }
         std::vector<cd> Hsq(Hm.begin(), Hm.begin() + (size_t)m * m);
         if (!hessenberg_eig(m, Hsq, w, X)) return fail(MLFMA_ENOTCONV, "Hessenberg eigenvalue iteration failed");
         order.resize(m);
         for (int i = 0; i < m; ++i) order[i] = i;
-        std::sort(order.begin(), order.end(), [&](int a, int b) { return std::abs(w[a]) > std::abs(w[b]); });
+        std::sort(order.begin(), order.end(), [&](int a2, int b2) { return std::abs(w[a2]) > std::abs(w[b2]); });
         const double beta = std::abs(Hm[(size_t)m * m + (m - 1)]);
         converged = true;
         for (int i = 0; i < k; ++i) {
@@ -832,24 +834,21 @@ extern "C" mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opt
         for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
         std::vector<cd> Hw(Hm.begin(), Hm.begin() + (size_t)m * m);
         for (int i = k; i < m; ++i) qr_sweep(m, Hw, Q, 0, m - 1, w[order[i]]);
-        // f_k = V Q e_{k} * H+(k, k-1) + f_m * Q(m-1, k-1),  f_m = H(m, m-1) v_m
-        std::vector<std::vector<cd>> Vn(k + 1, std::vector<cd>(n, 0.0));
-        for (int j = 0; j <= k; ++j)
-            for (int i = 0; i < m; ++i) {
-                const cd q = Q[(size_t)i * m + j];
-                if (q != 0.0)
-                    for (int64_t r = 0; r < n; ++r) Vn[j][r] += q * V[i][r];
-            }
-        std::vector<cd> f(n);
+        // V_j <- V Q e_j (j < k);  V_k <- f_k = V Q e_k * H+(k, k-1) + V_m * H(m, m-1) Q(m-1, k-1),
+        // normalised: one recombination of the old basis on the device
         const cd hk = Hw[(size_t)k * m + (k - 1)], fm = Hm[(size_t)m * m + (m - 1)] * Q[(size_t)(m - 1) * m + (k - 1)];
-        for (int64_t r = 0; r < n; ++r) f[r] = Vn[k][r] * hk + V[m][r] * fm;
+        std::vector<cd> coef((size_t)(m + 1) * (k + 1), 0.0);
+        for (int i = 0; i < m; ++i)
+            for (int c = 0; c <= k; ++c) coef[(size_t)i * (k + 1) + c] = Q[(size_t)i * m + c] * (c == k ? hk : cd(1.0));
+        coef[(size_t)m * (k + 1) + k] = fm;
+        if (!arnoldi_recombine(arn.get(), m + 1, k + 1, coef.data(), derr)) return fail(MLFMA_ECUDA, derr);
+        double fn = 0;
+        if (!arnoldi_normalise(arn.get(), k, &fn, derr)) return fail(MLFMA_ECUDA, derr);
         std::fill(Hm.begin(), Hm.end(), 0.0);
         for (int i = 0; i < k; ++i)
             for (int j = 0; j < k; ++j) Hm[(size_t)i * m + j] = Hw[(size_t)i * m + j];
-        const double fn = nrm2(f);
-        for (int j = 0; j < k; ++j) V[j] = Vn[j];
         Hm[(size_t)k * m + (k - 1)] = fn;
-        for (int64_t r = 0; r < n; ++r) V[k][r] = fn > 0 ? f[r] / fn : 0.0;
+        if (!arnoldi_get(arn.get(), k, vj.data(), derr)) return fail(MLFMA_ECUDA, derr);
         kstart = k;
     }
     // Ritz pairs -> characteristic values and real currents
@@ -859,24 +858,23 @@ extern "C" mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opt
         const double l = o.op == MLFMA_CM_ZINV_R ? ((1.0 / mu - 1.0) / cd(0, 1)).real() : (1.0 / mu).real();
         lam.push_back({l, order[i]});
     }
-    std::sort(lam.begin(), lam.end(), [](const auto &a, const auto &b) { return std::abs(a.first) < std::abs(b.first); });
+    std::sort(lam.begin(), lam.end(), [](const auto &a2, const auto &b2) { return std::abs(a2.first) < std::abs(b2.first); });
     for (int i = 0; i < k; ++i) lambda[i] = lam[i].first;
     if (J) {
-        std::vector<cd> v(n);
+        // Ritz vectors V X e (the wanted columns in output order) on the device
+        std::vector<cd> coef((size_t)m * k), vs((size_t)k * n);
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < k; ++i) coef[(size_t)j * k + i] = X[(size_t)j * m + lam[i].second];
+        if (!arnoldi_combine(arn.get(), m, k, coef.data(), vs.data(), derr)) return fail(MLFMA_ECUDA, derr);
         for (int i = 0; i < k; ++i) {
-            const int e = lam[i].second;
-            std::fill(v.begin(), v.end(), 0.0);
-            for (int j = 0; j < m; ++j) {
-                const cd s = X[(size_t)j * m + e];
-                for (int64_t r = 0; r < n; ++r) v[r] += s * V[j][r];
-            }
+            const cd *v = vs.data() + (size_t)i * n;
             // characteristic currents are real up to a phase: rotate to the
             // phase that maximises the real part's norm, normalise
             cd s2 = 0;
-            for (const cd &z : v) s2 += z * z;
+            for (int64_t r = 0; r < n; ++r) s2 += v[r] * v[r];
             const cd ph = std::polar(1.0, -0.5 * std::arg(s2));
             double nn = 0;
-            for (const cd &z : v) nn += std::pow((z * ph).real(), 2);
+            for (int64_t r = 0; r < n; ++r) nn += std::pow((v[r] * ph).real(), 2);
             nn = std::sqrt(nn);
             for (int64_t r = 0; r < n; ++r) J[r * k + i] = (v[r] * ph).real() / nn;
         }

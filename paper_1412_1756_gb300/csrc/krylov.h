@@ -45,4 +45,25 @@ void block_gmres_destroy(BlockGmres *g);
 int block_gmres_run(BlockGmres *g, const double *B, double *D, int guess, double tol, int maxit, int *conv,
                     double *relres, std::string &err);
 
+// Outer Arnoldi basis of cm_ira_solve on the plan's device (arnoldi_device.cu):
+// m + 1 complex FP64 vectors of length n.  Host vectors are canonical-order
+// complex; each call returns false with err set on a CUDA failure.
+class DeviceArnoldi;
+DeviceArnoldi *arnoldi_create(mlfma_plan_t p, int64_t n, int m, std::string &err);
+void arnoldi_destroy(DeviceArnoldi *a);
+bool arnoldi_set(DeviceArnoldi *a, int j, const std::complex<double> *v, std::string &err);   // V_j = v
+bool arnoldi_get(DeviceArnoldi *a, int j, std::complex<double> *v, std::string &err);         // v = V_j
+// w orthogonalised against V_0..V_j (classical Gram-Schmidt twice): h[i] += the
+// coefficients of both passes, *hn = the remaining norm, V_{j+1} = w / *hn,
+// and out (when not null) = V_{j+1}.
+bool arnoldi_extend(DeviceArnoldi *a, int j, const std::complex<double> *w, std::complex<double> *h, double *hn,
+                    std::complex<double> *out, std::string &err);
+// V_c <- sum_{i < rows} coef[i * cols + c] V_i for c < cols (all from the old basis)
+bool arnoldi_recombine(DeviceArnoldi *a, int rows, int cols, const std::complex<double> *coef, std::string &err);
+// V_j <- V_j / ||V_j||, *nrm = ||V_j||
+bool arnoldi_normalise(DeviceArnoldi *a, int j, double *nrm, std::string &err);
+// out[c] (host, n values each) = sum_{i < rows} coef[i * cols + c] V_i
+bool arnoldi_combine(DeviceArnoldi *a, int rows, int cols, const std::complex<double> *coef, std::complex<double> *out,
+                     std::string &err);
+
 }  // namespace mlfma
