@@ -253,7 +253,10 @@ mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec
  *                 windowed kernel (rows in groups of four on windows of
  *                 consecutive source samples, MLFMA_X_WIN_SHAPE) with
  *                 4 / 8 / 16 columns, 404 / 408 the same with 4 / 8 columns
- *                 and a register budget for one more CTA per SM (FP32 only)
+ *                 and a register budget for one more CTA per SM, 704 / 708 /
+ *                 716 the windowed kernel with the children that differ only
+ *                 in z sharing one phi step (the shift split into a theta-only
+ *                 z factor and the rest), 4 / 8 / 16 columns (FP32 only)
  *   [3 + 22 + l]  down pass from level l: columns per CTA 1..16 (one CTA per
  *                 child), 104 / 108 one CTA per parent with 4 / 8 columns,
  *                 204 / 208 / 216 one CTA per child with 4 / 8 / 16 columns and

@@ -277,6 +277,8 @@ cudaError_t upload_parent_tables(DevMem &M, const PlanHost &H, const Level &Lv, 
 {
     cudaError_t e;
     if ((e = upload_pairs<R>(M, Lv.shift, &D.shift)) != cudaSuccess) return e;
+    if ((e = upload_pairs<R>(M, Lv.shift_xy, &D.shift_xy)) != cudaSuccess) return e;
+    if ((e = upload_pairs<R>(M, Lv.gam, &D.gam)) != cudaSuccess) return e;
     auto pack = [](const Stencil &st) {
         std::vector<Tap<R>> t(st.idx.size());
         for (size_t i = 0; i < t.size(); ++i) {
@@ -869,7 +871,7 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
         for (int l = a.coarsest; l <= a.leaf; ++l) {
             pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11}, best.tr[l]);
             if (l < a.leaf) {
-                pick(STAGE_UP + l, {1, 2, 4, 8, 16, 202, 204, 208, 216, 304, 308, 316, 404, 408}, best.up_nb[l]);
+                pick(STAGE_UP + l, {1, 2, 4, 8, 16, 202, 204, 208, 216, 304, 308, 316, 404, 408, 704, 708, 716}, best.up_nb[l]);
                 pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108, 204, 208, 216, 304, 308, 316, 404, 408, 504, 508},
                      best.down_nb[l]);
             }
@@ -1385,7 +1387,8 @@ mlfma_status mlfma_tune_set(mlfma_plan_t p, int64_t B, int xc, int prec, const i
         for (int l = 0; l < MLFMA_MAX_LEVELS && ok; ++l) {
             const int u = choices[3 + l], d = choices[3 + MLFMA_MAX_LEVELS + l], r = choices[3 + 2 * MLFMA_MAX_LEVELS + l];
             auto win = [](int x) { return x == 304 || x == 308 || x == 316 || x == 404 || x == 408; };
-            ok = (u == 0 || pow2(u) || u == 202 || u == 204 || u == 208 || u == 216 || win(u)) &&
+            ok = (u == 0 || pow2(u) || u == 202 || u == 204 || u == 208 || u == 216 || win(u) || u == 704 || u == 708 ||
+                  u == 716) &&
                  (d == 0 || pow2(d) || d == 104 || d == 108 || d == 204 || d == 208 || d == 216 || win(d) || d == 504 ||
                   d == 508) &&
                  r >= 0 && r <= 11;

@@ -99,6 +99,8 @@ struct DevLevel {
     const int32_t *child_ptr = nullptr;  // [nbox+1] into level l+1
     const R *shift = nullptr;            // [8][K][2] (parents only)
     const R *shift_dk = nullptr;         // [8][K][2] d shift / dk (parents only, when set up)
+    const R *shift_xy = nullptr;         // [8][K][2] shift without its z factor (parents only)
+    const R *gam = nullptr;              // [8][nth][2] the z factor, a function of theta (parents only)
     // to children (parents only): up stencils rows = this level's nth / nph;
     // down stencils rows = child nth / nph
     const int32_t *thu_ptr = nullptr, *thu_idx = nullptr, *thu_refl = nullptr;

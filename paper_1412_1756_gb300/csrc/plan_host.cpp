@@ -747,6 +747,8 @@ std::string build_plan_host(PlanHost &P, const double *verts, int64_t nv, const 
         win_stencil(Pa.th_dn, Pa.nth, true, kWinMax, Pa.wd_th);
         Pa.shift.resize((size_t)8 * Pa.K);
         Pa.shift_dk.resize((size_t)8 * Pa.K);
+        Pa.shift_xy.resize((size_t)8 * Pa.K);
+        Pa.gam.resize((size_t)8 * Pa.nth);
         for (int o = 0; o < 8; ++o) {
             const double h = 0.5 * C.a;
             double d[3] = {-h * (((o >> 2) & 1) ? 1 : -1), -h * (((o >> 1) & 1) ? 1 : -1), -h * ((o & 1) ? 1 : -1)};
@@ -757,6 +759,12 @@ std::string build_plan_host(PlanHost &P, const double *verts, int64_t nv, const 
                 double ph = k * kd;
                 Pa.shift[(size_t)o * Pa.K + q] = cd(std::cos(ph), std::sin(ph));
                 Pa.shift_dk[(size_t)o * Pa.K + q] = cd(0.0, kd) * cd(std::cos(ph), std::sin(ph));
+                const double pxy = k * (kh[0] * d[0] + kh[1] * d[1]);
+                Pa.shift_xy[(size_t)o * Pa.K + q] = cd(std::cos(pxy), std::sin(pxy));
+            }
+            for (int t = 0; t < Pa.nth; ++t) {
+                const double pz = k * Pa.ct[t] * d[2];
+                Pa.gam[(size_t)o * Pa.nth + t] = cd(std::cos(pz), std::sin(pz));
             }
         }
     }

@@ -84,6 +84,11 @@ struct Level {
     // to/from children (2 <= l < leaf)
     std::vector<cd> shift;          // [8][K]: exp(i k khat.(r_parent - r_child))
     std::vector<cd> shift_dk;       // [8][K]: d shift / dk = i khat.(r_parent - r_child) shift
+    // the shift split as shift = shift_xy(theta, phi) * gam(theta): the factor of
+    // the z offset depends on theta alone, so two children that differ only in
+    // z can share the phi interpolation (after theta, before phi)
+    std::vector<cd> shift_xy;       // [8][K]: exp(i k (khat_x d_x + khat_y d_y))
+    std::vector<cd> gam;            // [8][nth]: exp(i k cos(theta) d_z)
     Stencil th_up, ph_up;           // child grid -> this grid (rows: nth / nph of this level)
     Stencil ph_dn, th_dn;           // weighted transposes (rows: child nph / child nth)
     WinStencil wu_th, wu_ph, wd_ph, wd_th;   // the four stencils above on windows (kernels that take taps at fixed offsets)

@@ -1586,7 +1586,8 @@ cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs
 {
     using C = typename Cx<R>::T;
     if (nb_choice > 300) {   // 304, 308, 316 windowed FP32 kernel with 4 / 8 / 16 columns per CTA; 404, 408 the
-                             // same with 4 / 8 columns and registers for one more CTA per SM
+                             // same with 4 / 8 columns and registers for one more CTA per SM; 704, 708, 716
+                             // with the children that differ only in z sharing one phi step
         if constexpr (sizeof(R) == 4) return launch_up_win(P, Ch, B, Bs, acc, nb_choice - 300, s);
         else return cudaErrorInvalidConfiguration;
     }

@@ -413,7 +413,12 @@ __global__ void __launch_bounds__(256, MINB) k_down_win_pp(DevLevel<float> P, De
 // phi index; T rows padded by one element), phi interpolation of T with the
 // shift accumulated into O (lines = band rows; O and Z rows padded); one
 // store of the parent's band at the end.
-template <int NB, int MINB>
+// PAIR: two children that differ only in their z octant bit (adjacent in the
+// child order) share one phi step.  The shift factors as shift_xy(theta, phi)
+// * gam(theta), and gam commutes with the phi interpolation, so the first
+// child's T is scaled by its gam, the second's is scaled and added, and the
+// phi step of the sum is accumulated with the pair's common shift_xy.
+template <int NB, int MINB, bool PAIR = false>
 __global__ void __launch_bounds__(256, MINB) k_up_win(DevLevel<float> P, DevLevel<float> Ch, int B, int RS, int Bs,
                                                       int accumulate)
 {
@@ -443,14 +448,24 @@ __global__ void __launch_bounds__(256, MINB) k_up_win(DevLevel<float> P, DevLeve
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const float2 *S = reinterpret_cast<const float2 *>(Ch.S);
     const float2 *shift = reinterpret_cast<const float2 *>(P.shift) + (int64_t)t0 * nphp;
+    const float2 *shift_xy = reinterpret_cast<const float2 *>(P.shift_xy) + (int64_t)t0 * nphp;
+    const float2 *gam = reinterpret_cast<const float2 *>(P.gam) + t0;
     for (int e = threadIdx.x; e < nr * opit * NCP; e += blockDim.x) O4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     const int c0 = P.child_ptr[p], c1 = P.child_ptr[p + 1];
+    // the child's part in a z pair: 0 none, 1 first, 2 second
+    auto role = [&](int c) -> int {
+        if (!PAIR) return 0;
+        const int o = Ch.octant[c];
+        if (!(o & 1) && c + 1 < c1 && Ch.octant[c + 1] == o + 1) return 1;
+        if ((o & 1) && c > c0 && Ch.octant[c - 1] == o - 1) return 2;
+        return 0;
+    };
     auto fetch_A = [&](int c) {
         const float2 *src = S + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + 2 * pc;
         for (int q = pslot; q < Kc; q += npslot) cp_pair(A4 + q * NCP + pc, src + (int64_t)q * Bs, cols, a16);
     };
-    auto fetch_Z = [&](int c) {
-        const float2 *z = shift + (int64_t)Ch.octant[c] * Kp;
+    auto fetch_Z = [&](int c) {   // the table of the next phi step: the child's own, or its pair's shift_xy
+        const float2 *z = (role(c) ? shift_xy : shift) + (int64_t)Ch.octant[c] * Kp;
         for (int tt = warp; tt < nr; tt += nw)
             for (int u = lane; u < nphp; u += 32) cp8(Z + tt * opit + u, z + tt * nphp + u);
     };
@@ -464,8 +479,11 @@ __global__ void __launch_bounds__(256, MINB) k_up_win(DevLevel<float> P, DevLeve
         cp_commit();
     }
     const int cpi = lane % NCP, rl = lane / NCP;
+    bool prev_phi = true;   // the previous child ran a phi step (its Z fetch is the newest group)
     for (int c = c0; c < c1; ++c) {
-        cp_wait<1>();   // A(c) (and the tables) are in; Z(c) may still be in flight
+        const int rc = role(c);
+        if (prev_phi) cp_wait<1>();   // A(c) (and the tables) are in; Z(c) may still be in flight
+        else cp_wait<0>();            // A(c) is the newest group
         __syncthreads();
         // theta: T(t, v) = sum_f c A(row of s + f, v or v + pi); lines v, groups of band rows t
         {
@@ -482,7 +500,20 @@ __global__ void __launch_bounds__(256, MINB) k_up_win(DevLevel<float> P, DevLeve
 #pragma unroll
                     for (int r = 0; r < kG; ++r) {
                         const int tt = gl * kG + r;
-                        if (tt < nr) T4[((size_t)tt * tpit + v) * NCP + cpi] = acc[r];
+                        if (tt < nr) {
+                            float4 val = acc[r];
+                            float4 *t4 = T4 + ((size_t)tt * tpit + v) * NCP + cpi;
+                            if (PAIR && rc) {   // scale by the z factor of this child's shift; the second adds
+                                const float2 gz = gam[(int64_t)Ch.octant[c] * ntp + tt];
+                                val = make_float4(gz.x * val.x - gz.y * val.y, gz.x * val.y + gz.y * val.x,
+                                                  gz.x * val.z - gz.y * val.w, gz.x * val.w + gz.y * val.z);
+                                if (rc == 2) {
+                                    const float4 old = *t4;
+                                    val.x += old.x; val.y += old.y; val.z += old.z; val.w += old.w;
+                                }
+                            }
+                            *t4 = val;
+                        }
                     }
                 }
             }
@@ -490,6 +521,10 @@ __global__ void __launch_bounds__(256, MINB) k_up_win(DevLevel<float> P, DevLeve
         __syncthreads();
         if (c + 1 < c1) fetch_A(c + 1);
         cp_commit();
+        if (PAIR && rc == 1) {   // the pair's phi step comes with its second child
+            prev_phi = false;
+            continue;
+        }
         cp_wait<1>();   // Z(c) is in; A(c + 1) may still be in flight
         __syncthreads();
         // phi: O(t, u) += Z(t, u) sum_f c T(t, (s + f) mod nphc); lines t, groups of parent phi u
@@ -524,6 +559,7 @@ __global__ void __launch_bounds__(256, MINB) k_up_win(DevLevel<float> P, DevLeve
         __syncthreads();
         if (c + 1 < c1) fetch_Z(c + 1);
         cp_commit();
+        prev_phi = true;
     }
     cp_wait<0>();
     if (!cols) return;
@@ -586,9 +622,10 @@ cudaError_t down_win_pp_nb(const DevLevel<float> &P, const DevLevel<float> &Ch, 
     return cudaGetLastError();
 }
 
-template <int NB, int MINB>
+template <int NB, int MINB, bool PAIR = false>
 cudaError_t up_win_nb(const DevLevel<float> &P, const DevLevel<float> &Ch, int B, int Bs, int acc, cudaStream_t s)
 {
+    if (PAIR && (!P.shift_xy || !P.gam)) return cudaErrorInvalidConfiguration;
     // bands of parent theta groups: shared memory for MINB CTAs per SM, and
     // enough CTAs to fill the GPU
     const size_t cap = (size_t)(MINB >= 3 ? 72 : 100) * 1024;
@@ -599,7 +636,7 @@ cudaError_t up_win_nb(const DevLevel<float> &P, const DevLevel<float> &Ch, int B
     const size_t smem = up_win_smem(P, Ch, NB, RS);
     if (smem > kWinSmemCap) return cudaErrorInvalidConfiguration;
     dim3 grid(P.nbox * ((B + NB - 1) / NB) * RS, 2);
-    k_up_win<NB, MINB><<<grid, 256, smem, s>>>(P, Ch, B, RS, Bs, acc);
+    k_up_win<NB, MINB, PAIR><<<grid, 256, smem, s>>>(P, Ch, B, RS, Bs, acc);
     return cudaGetLastError();
 }
 
@@ -633,6 +670,9 @@ cudaError_t launch_up_win(const DevLevel<float> &P, const DevLevel<float> &Ch, i
     case 16: return up_win_nb<16, 2>(P, Ch, B, Bs, acc, s);
     case 104: return up_win_nb<4, 3>(P, Ch, B, Bs, acc, s);
     case 108: return up_win_nb<8, 3>(P, Ch, B, Bs, acc, s);
+    case 404: return up_win_nb<4, 2, true>(P, Ch, B, Bs, acc, s);
+    case 408: return up_win_nb<8, 2, true>(P, Ch, B, Bs, acc, s);
+    case 416: return up_win_nb<16, 2, true>(P, Ch, B, Bs, acc, s);
     default: return cudaErrorInvalidConfiguration;
     }
 }
@@ -646,6 +686,7 @@ cudaError_t prime_win_kernels()
     ALLOW((k_down_win_pp<4, 3>)); ALLOW((k_down_win_pp<8, 2>));
     ALLOW((k_up_win<4, 2>)); ALLOW((k_up_win<8, 2>)); ALLOW((k_up_win<16, 2>));
     ALLOW((k_up_win<4, 3>)); ALLOW((k_up_win<8, 3>));
+    ALLOW((k_up_win<4, 2, true>)); ALLOW((k_up_win<8, 2, true>)); ALLOW((k_up_win<16, 2, true>));
 #undef ALLOW
     return cudaSuccess;
 }
