@@ -265,7 +265,9 @@ mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec
  *                 404 / 408 with 4 / 8 columns and a register budget for one
  *                 more CTA per SM, 504 / 508 the windowed kernel with one CTA
  *                 per parent (its field loaded once for all its children),
- *                 4 / 8 columns (FP32 only)
+ *                 4 / 8 columns, 804 / 808 one CTA per pair of children that
+ *                 differ only in z, sharing one phi step (4 / 8 columns; FP32
+ *                 only)
  *   [3 + 44 + l]  translation at level l: 1 two columns per thread; 2..6 one
  *                 column with 1, 2, 4, 8, 16 lanes per output; 7 / 8 one warp
  *                 per (child, sample) with 2 / 1 columns per lane; 9 / 10 / 11

@@ -279,6 +279,23 @@ cudaError_t upload_parent_tables(DevMem &M, const PlanHost &H, const Level &Lv, 
     if ((e = upload_pairs<R>(M, Lv.shift, &D.shift)) != cudaSuccess) return e;
     if ((e = upload_pairs<R>(M, Lv.shift_xy, &D.shift_xy)) != cudaSuccess) return e;
     if ((e = upload_pairs<R>(M, Lv.gam, &D.gam)) != cudaSuccess) return e;
+    {
+        // down-pass groups over the child level: siblings with octants o (even) and o + 1 pair up
+        const Level &Cl = H.lv[Lv.l + 1];
+        std::vector<int2> g;
+        const int nc = Cl.nbox();
+        for (int i = 0; i < nc;) {
+            if (i + 1 < nc && Cl.parent[i + 1] == Cl.parent[i] && !(Cl.octant[i] & 1) && Cl.octant[i + 1] == Cl.octant[i] + 1) {
+                g.push_back(make_int2(i, i + 1));
+                i += 2;
+            } else {
+                g.push_back(make_int2(i, -1));
+                i += 1;
+            }
+        }
+        if ((e = M.upload(g, &D.dgrp)) != cudaSuccess) return e;
+        D.ndgrp = (int)g.size();
+    }
     auto pack = [](const Stencil &st) {
         std::vector<Tap<R>> t(st.idx.size());
         for (size_t i = 0; i < t.size(); ++i) {
@@ -872,7 +889,7 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
             pick(STAGE_TRANSLATE + l, {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11}, best.tr[l]);
             if (l < a.leaf) {
                 pick(STAGE_UP + l, {1, 2, 4, 8, 16, 202, 204, 208, 216, 304, 308, 316, 404, 408, 704, 708, 716}, best.up_nb[l]);
-                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108, 204, 208, 216, 304, 308, 316, 404, 408, 504, 508},
+                pick(STAGE_DOWN + l, {1, 2, 4, 8, 16, 104, 108, 204, 208, 216, 304, 308, 316, 404, 408, 504, 508, 804, 808},
                      best.down_nb[l]);
             }
         }
@@ -1390,7 +1407,7 @@ mlfma_status mlfma_tune_set(mlfma_plan_t p, int64_t B, int xc, int prec, const i
             ok = (u == 0 || pow2(u) || u == 202 || u == 204 || u == 208 || u == 216 || win(u) || u == 704 || u == 708 ||
                   u == 716) &&
                  (d == 0 || pow2(d) || d == 104 || d == 108 || d == 204 || d == 208 || d == 216 || win(d) || d == 504 ||
-                  d == 508) &&
+                  d == 508 || d == 804 || d == 808) &&
                  r >= 0 && r <= 11;
         }
         if (!ok) return fail(MLFMA_EINVAL, "a launch-shape choice is outside its documented set");

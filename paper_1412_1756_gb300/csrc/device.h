@@ -101,6 +101,10 @@ struct DevLevel {
     const R *shift_dk = nullptr;         // [8][K][2] d shift / dk (parents only, when set up)
     const R *shift_xy = nullptr;         // [8][K][2] shift without its z factor (parents only)
     const R *gam = nullptr;              // [8][nth][2] the z factor, a function of theta (parents only)
+    // the children in down-pass groups (parents only): a pair of siblings that
+    // differ only in z (first, second), or one child (first, -1)
+    const int2 *dgrp = nullptr;
+    int ndgrp = 0;
     // to children (parents only): up stencils rows = this level's nth / nph;
     // down stencils rows = child nth / nph
     const int32_t *thu_ptr = nullptr, *thu_idx = nullptr, *thu_refl = nullptr;

@@ -1728,7 +1728,8 @@ cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int 
 {
     if (nb_choice > 300) {   // 304, 308, 316 windowed FP32 kernel with 4 / 8 / 16 columns per CTA; 404, 408 the
                              // same with 4 / 8 columns and registers for one more CTA per SM; 504, 508 one
-                             // CTA per parent (its field loaded once for all children), 4 / 8 columns
+                             // CTA per parent (its field loaded once for all children), 4 / 8 columns; 804, 808
+                             // per pair of children that differ only in z (one phi step for both)
         if constexpr (sizeof(R) == 4) return launch_down_win(P, Ch, B, Bs, nb_choice - 300, s);
         else return cudaErrorInvalidConfiguration;
     }

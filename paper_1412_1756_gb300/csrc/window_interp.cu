@@ -291,7 +291,12 @@ __device__ __forceinline__ void down_prefetch(float4 (&xin)[PF], const float2 *d
     }
 }
 
-template <int NB, int MINB>
+// PAIR: a CTA takes a down-pass group of the parent level (two siblings that
+// differ only in z, or one child).  The conjugate shift factors as
+// conj(shift_xy) * conj(gam(theta)); the parent is shifted by the pair's
+// common conj(shift_xy) and anterpolated in phi once, and each child's theta
+// step runs on U with its rows scaled by that child's conj(gam).
+template <int NB, int MINB, bool PAIR = false>
 __global__ void __launch_bounds__(256, MINB) k_down_win(DevLevel<float> P, DevLevel<float> Ch, int B, int Bs)
 {
     constexpr int NCP = NB / 2;
@@ -299,7 +304,13 @@ __global__ void __launch_bounds__(256, MINB) k_down_win(DevLevel<float> P, DevLe
     const int Kc = Ch.K, nthc = Ch.nth, nphc = Ch.nph, ntp = P.nth, nphp = P.nph, Kp = P.K;
     const WinDev wp = P.wd_ph, wt = P.wd_th;
     // column chunk fastest in the grid: the CTAs that share a field row's DRAM lines run together
-    const int nbc = (B + NB - 1) / NB, c = blockIdx.x / nbc, comp = blockIdx.y, b0 = (blockIdx.x - c * nbc) * NB;
+    const int nbc = (B + NB - 1) / NB, item = blockIdx.x / nbc, comp = blockIdx.y, b0 = (blockIdx.x - item * nbc) * NB;
+    int ca = item, cb = -1;
+    if (PAIR) {
+        const int2 gp = P.dgrp[item];
+        ca = gp.x;
+        cb = gp.y;
+    }
     const int nb = min(NB, B - b0);
     const int hp = nphp + 1, up = nphc + 1;
     float4 *H4 = reinterpret_cast<float4 *>(smem_raw);   // [ntp][hp][NCP]; then W [Kc][NCP]
@@ -311,16 +322,16 @@ __global__ void __launch_bounds__(256, MINB) k_down_win(DevLevel<float> P, DevLe
     const int pc = threadIdx.x % NCP, pslot = threadIdx.x / NCP, npslot = blockDim.x / NCP;
     const int cols = pair_cols(pc, nb);
     const bool a16 = (Bs % 2) == 0 && ((reinterpret_cast<uintptr_t>(P.G) | reinterpret_cast<uintptr_t>(Ch.G)) & 15) == 0;
-    float2 *dst = reinterpret_cast<float2 *>(Ch.G) + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + 2 * pc;
+    const bool pair = PAIR && cb >= 0;
     {
-        const int par = Ch.parent[c];
+        const int par = Ch.parent[ca];
         const float2 *g = reinterpret_cast<const float2 *>(P.G) + ((int64_t)par * 2 + comp) * Kp * Bs + b0 + 2 * pc;
         Walk w(pslot, npslot, nphp);
         for (int q = pslot; q < Kp; q += npslot, w.next()) cp_pair(H4 + (w.t * hp + w.u) * NCP + pc, g + (int64_t)q * Bs, cols, a16);
         stage_table(wp, cph, sph);
         stage_table(wt, cth, sth);
         cp_commit();
-        const float2 *sh = reinterpret_cast<const float2 *>(P.shift) + (int64_t)Ch.octant[c] * Kp;
+        const float2 *sh = reinterpret_cast<const float2 *>(pair ? P.shift_xy : P.shift) + (int64_t)Ch.octant[ca] * Kp;
         cp_wait<0>();
         Walk w2(pslot, npslot, nphp);
 #pragma unroll 4
@@ -336,11 +347,38 @@ __global__ void __launch_bounds__(256, MINB) k_down_win(DevLevel<float> P, DevLe
     down_phi<NB>(H4, U4, cph, sph, wp, ntp, nphp, nphc);
     __syncthreads();
     constexpr int PF = MINB >= 4 ? 1 : kPF;   // fewer prefetch registers for the tighter budget
-    float4 xin[PF];
-    down_prefetch<NB, PF>(xin, dst, Kc, Bs, cols, a16);
-    down_theta<NB>(U4, H4, cth, sth, wt, ntp, nthc, nphc);
-    __syncthreads();
-    down_add<NB, PF>(dst, H4, xin, Kc, Bs, cols, a16);
+    const int nch = pair ? 2 : 1;
+    for (int k = 0; k < nch; ++k) {
+        const int c = k ? cb : ca;
+        float2 *dst = reinterpret_cast<float2 *>(Ch.G) + ((int64_t)c * 2 + comp) * Kc * Bs + b0 + 2 * pc;
+        if (pair) {
+            // U rows times conj(gam_a) for the first child, then times gam_a conj(gam_b) for the second
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            const float2 *ga = reinterpret_cast<const float2 *>(P.gam) + (int64_t)Ch.octant[ca] * ntp;
+            const float2 *gb = reinterpret_cast<const float2 *>(P.gam) + (int64_t)Ch.octant[cb] * ntp;
+            for (int t = warp; t < ntp; t += nw) {
+                const float2 a = ga[t];
+                float2 f = make_float2(a.x, -a.y);
+                if (k) {
+                    const float2 b = gb[t];   // a * conj(b)
+                    f = make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+                }
+                float4 *row = U4 + (size_t)t * up * NCP;
+                for (int i = lane; i < nphc * NCP; i += 32) {
+                    const float4 u = row[i];
+                    row[i] = make_float4(f.x * u.x - f.y * u.y, f.x * u.y + f.y * u.x, f.x * u.z - f.y * u.w,
+                                         f.x * u.w + f.y * u.z);
+                }
+            }
+            __syncthreads();
+        }
+        float4 xin[PF];
+        down_prefetch<NB, PF>(xin, dst, Kc, Bs, cols, a16);
+        down_theta<NB>(U4, H4, cth, sth, wt, ntp, nthc, nphc);
+        __syncthreads();
+        down_add<NB, PF>(dst, H4, xin, Kc, Bs, cols, a16);
+        if (k + 1 < nch) __syncthreads();   // W (over H) and U are read before the second child rewrites them
+    }
 }
 
 // One CTA per (parent box, component, chunk of NB columns), 256 threads:
@@ -596,13 +634,14 @@ size_t up_win_smem(const DevLevel<float> &P, const DevLevel<float> &Ch, int NB, 
 }
 
 // MINB: CTAs per SM the register budget is set for (3 or 4 for down, 2 or 3 for up)
-template <int NB, int MINB>
+template <int NB, int MINB, bool PAIR = false>
 cudaError_t down_win_nb(const DevLevel<float> &P, const DevLevel<float> &Ch, int B, int Bs, cudaStream_t s)
 {
     const size_t smem = down_win_smem(P, Ch, NB);
     if (smem > kWinSmemCap) return cudaErrorInvalidConfiguration;
-    dim3 grid(Ch.nbox * ((B + NB - 1) / NB), 2);
-    k_down_win<NB, MINB><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
+    if (PAIR && (!P.dgrp || !P.shift_xy || !P.gam)) return cudaErrorInvalidConfiguration;
+    dim3 grid((PAIR ? P.ndgrp : Ch.nbox) * ((B + NB - 1) / NB), 2);
+    k_down_win<NB, MINB, PAIR><<<grid, 256, smem, s>>>(P, Ch, B, Bs);
     return cudaGetLastError();
 }
 
@@ -654,6 +693,8 @@ cudaError_t launch_down_win(const DevLevel<float> &P, const DevLevel<float> &Ch,
     case 16: return down_win_nb<16, 3>(P, Ch, B, Bs, s);
     case 104: return down_win_nb<4, 4>(P, Ch, B, Bs, s);
     case 108: return down_win_nb<8, 4>(P, Ch, B, Bs, s);
+    case 504: return down_win_nb<4, 3, true>(P, Ch, B, Bs, s);
+    case 508: return down_win_nb<8, 3, true>(P, Ch, B, Bs, s);
     case 204: return down_win_pp_nb<4, 3>(P, Ch, B, Bs, s);
     case 208: return down_win_pp_nb<8, 2>(P, Ch, B, Bs, s);
     default: return cudaErrorInvalidConfiguration;
@@ -684,6 +725,7 @@ cudaError_t prime_win_kernels()
     ALLOW((k_down_win<4, 3>)); ALLOW((k_down_win<8, 3>)); ALLOW((k_down_win<16, 3>));
     ALLOW((k_down_win<4, 4>)); ALLOW((k_down_win<8, 4>));
     ALLOW((k_down_win_pp<4, 3>)); ALLOW((k_down_win_pp<8, 2>));
+    ALLOW((k_down_win<4, 3, true>)); ALLOW((k_down_win<8, 3, true>));
     ALLOW((k_up_win<4, 2>)); ALLOW((k_up_win<8, 2>)); ALLOW((k_up_win<16, 2>));
     ALLOW((k_up_win<4, 3>)); ALLOW((k_up_win<8, 3>));
     ALLOW((k_up_win<4, 2, true>)); ALLOW((k_up_win<8, 2, true>)); ALLOW((k_up_win<16, 2, true>));

@@ -80,7 +80,7 @@ def test_every_candidate_shape_computes_the_same_product(dt, prec, tol):
             cands += [(3 + l, c) for c in (1, 2, 4, 8, 16)] + [(3 + L + l, c) for c in (1, 2, 4, 8, 16, 104, 108)]
             if prec == M.FP32:   # rows in pairs; rows in groups of four on windows
                 cands += [(3 + l, c) for c in (202, 204, 208, 216)] + [(3 + L + l, c) for c in (204, 208, 216)]
-                cands += [(3 + l, c) for c in (304, 308, 316, 404, 408, 704, 708, 716)] + [(3 + L + l, c) for c in (304, 308, 316, 404, 408, 504, 508)]
+                cands += [(3 + l, c) for c in (304, 308, 316, 404, 408, 704, 708, 716)] + [(3 + L + l, c) for c in (304, 308, 316, 404, 408, 504, 508, 804, 808)]
     for field, c in cands:
         ch = np.zeros(M.TUNE_FIELDS, np.int32)
         ch[field] = c

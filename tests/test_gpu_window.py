@@ -61,7 +61,7 @@ def test_each_stage_matches_builtin(name, B, cplx):
     y0 = P.matvec(xd).cpu().numpy()
     info = P.info()
     for l in range(2, info["leaf_level"]):
-        for field, shapes in ((3 + l, WIN + (704, 708, 716)), (3 + M.MAX_LEVELS + l, WIN + (504, 508))):
+        for field, shapes in ((3 + l, WIN + (704, 708, 716)), (3 + M.MAX_LEVELS + l, WIN + (504, 508, 804, 808))):
             ran = []
             for c in shapes:
                 pin(P, B, [(field, c)], complex_x=cplx)
@@ -89,10 +89,10 @@ def test_all_levels_fields_and_oracle_rows():
     info = P.info()
     P.matvec(torch.from_numpy(x).to("cuda", torch.float64))
     f64 = {(w, l): P.export_field(M.FP64, w, l, B) for l in range(2, info["leaf_level"] + 1) for w in (0, 1)}
-    for c in (304, 308, 404, 504, 708):   # 16 columns do not fit the down kernel at this plate's level 2
+    for c in (304, 308, 404, 504, 708, 804):   # 16 columns do not fit the down kernel at this plate's level 2
         if c < 500:
             pairs = all_levels(info, c)
-        elif c < 700:   # per-parent down pass
+        elif c < 700 or c > 800:   # per-parent or z-pair down pass
             pairs = [(3 + M.MAX_LEVELS + l, c) for l in range(2, info["leaf_level"])]
         else:           # up pass with z pairs
             pairs = [(3 + l, c) for l in range(2, info["leaf_level"])]
