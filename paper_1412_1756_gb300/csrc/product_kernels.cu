@@ -1440,6 +1440,12 @@ cudaError_t launch_radiate(const ProductArgs<R> &a, int Bs, cudaStream_t s, int 
         if constexpr (sizeof(R) == 4) return launch_radiate_quads(a, Bs, s);
         else return cudaErrorInvalidConfiguration;
     }
+    if constexpr (sizeof(R) == 4) {
+        if (choice == 0 && a.B >= 32) {   // built-in for wide batches
+            const cudaError_t e = launch_radiate_quads(a, Bs, s);
+            if (e != cudaErrorInvalidConfiguration) return e;
+        }
+    }
     if (choice >= 2 && choice <= 4) {
         const int nb = choice == 2 ? 32 : choice == 3 ? 16 : 8;
         if (a.B < nb || (size_t)a.nr.max_rows * nb * sizeof(R) > (size_t)kStageCap) return cudaErrorInvalidConfiguration;
@@ -1506,6 +1512,8 @@ cudaError_t launch_receive(const ProductArgs<R> &a, int Bs, cudaStream_t s, int 
         if constexpr (sizeof(R) == 4) return launch_receive_pairs(a, Bs, 64 >> (choice - 4), s);
         else return cudaErrorInvalidConfiguration;
     }
+    if constexpr (sizeof(R) == 4)
+        if (choice == 0 && a.B >= 32) return launch_receive_pairs(a, Bs, 32, s);   // built-in for wide batches
     if (choice == 1) return a.B >= 32 ? launch_receive_tiled<R, 32>(a, Bs, s) : cudaErrorInvalidConfiguration;
     if (choice == 2) return a.B >= 16 ? launch_receive_tiled<R, 16>(a, Bs, s) : cudaErrorInvalidConfiguration;
     if (choice == 3) return a.B >= 8 ? launch_receive_tiled<R, 8>(a, Bs, s) : cudaErrorInvalidConfiguration;
@@ -1591,6 +1599,12 @@ cudaError_t launch_up(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int Bs
         if constexpr (sizeof(R) == 4) return launch_up_win(P, Ch, B, Bs, acc, nb_choice - 300, s);
         else return cudaErrorInvalidConfiguration;
     }
+    if constexpr (sizeof(R) == 4) {
+        if (nb_choice == 0 && B >= 16) {   // built-in for wide batches: windowed with z pairs, 8 columns per CTA
+            const cudaError_t e = launch_up_win(P, Ch, B, Bs, acc, 408, s);
+            if (e != cudaErrorInvalidConfiguration) return e;
+        }
+    }
     const int order = P.up_order;
     int nb = column_chunk<R>(B, ((size_t)Ch.K + (size_t)P.nth * (Ch.nph + P.nph)) * sizeof(C));
     int rb = 1;
@@ -1635,6 +1649,12 @@ cudaError_t launch_translate(const DevLevel<R> &Lv, int B, int Bs, int acc, cuda
     if (choice >= 9 && choice <= 11) {   // four columns per thread, 64 / 32 / 16 columns per CTA
         if constexpr (sizeof(R) == 4) return launch_translate_quad(Lv, B, Bs, acc, 64 >> (choice - 9), s);
         else return cudaErrorInvalidConfiguration;
+    }
+    if constexpr (sizeof(R) == 4) {
+        if (choice == 0 && B >= 16) {   // built-in for wide batches: four columns per thread
+            const cudaError_t e = launch_translate_quad(Lv, B, Bs, acc, B >= 64 ? 64 : (B >= 32 ? 32 : 16), s);
+            if (e != cudaErrorInvalidConfiguration) return e;
+        }
     }
     if (choice == 7 || choice == 8) {
         using C = typename Cx<R>::T;
@@ -1732,6 +1752,14 @@ cudaError_t launch_down(const DevLevel<R> &P, const DevLevel<R> &Ch, int B, int 
                              // per pair of children that differ only in z (one phi step for both)
         if constexpr (sizeof(R) == 4) return launch_down_win(P, Ch, B, Bs, nb_choice - 300, s);
         else return cudaErrorInvalidConfiguration;
+    }
+    if constexpr (sizeof(R) == 4) {
+        if (nb_choice == 0 && B >= 16) {   // built-in for wide batches: windowed with z pairs, 8 then 4 columns
+            cudaError_t e = launch_down_win(P, Ch, B, Bs, 508, s);
+            if (e != cudaErrorInvalidConfiguration) return e;
+            e = launch_down_win(P, Ch, B, Bs, 504, s);
+            if (e != cudaErrorInvalidConfiguration) return e;
+        }
     }
     if (nb_choice == 104) return launch_down_pp<R, 4>(P, Ch, B, Bs, s);
     if (nb_choice == 108) return launch_down_pp<R, 8>(P, Ch, B, Bs, s);
@@ -1972,6 +2000,8 @@ cudaError_t launch_core_dk(const ProductArgs<R> &a, cudaStream_t s, StageClock *
         TRY(launch_up<R>(a.lv[l], a.lv[l + 1], Bs, Bs, 0, s));
         DevLevel<R> px = a.lv[l];
         px.shift = a.lv[l].shift_dk;
+        px.shift_xy = px.gam = nullptr;   // the split shift is the value's: no pair kernels here
+        px.dgrp = nullptr;
         px.S = tangent(a.lv[l].S);
         TRY(launch_up<R>(px, a.lv[l + 1], T, Bs, 1, s));
         TRY(tick(clk, STAGE_UP + l, s));
@@ -1981,6 +2011,8 @@ cudaError_t launch_core_dk(const ProductArgs<R> &a, cudaStream_t s, StageClock *
         TRY(launch_down<R>(a.lv[l], a.lv[l + 1], Bs, Bs, s));
         DevLevel<R> px = a.lv[l], cx = a.lv[l + 1];
         px.shift = a.lv[l].shift_dk;
+        px.shift_xy = px.gam = nullptr;   // the split shift is the value's: no pair kernels here
+        px.dgrp = nullptr;
         cx.G = tangent(a.lv[l + 1].G);
         TRY(launch_down<R>(px, cx, T, Bs, s));
         TRY(tick(clk, STAGE_DOWN + l, s));
