@@ -176,7 +176,7 @@ def kernel_digest():
 # at B = 64: {(workload, stage, kernel source digest): bytes}.  Summaries in
 # profiles/ (k_down_cube8m-6lv_B64.md).
 NCU_TRAFFIC = {
-    ("cube8m-6lv", "down4", "2e95d8727f67456b"): 2_410_161_000 + 1_650_604_000,
+    ("cube8m-6lv", "translate5", "69c5ad055ed0013e"): 1_764_694_000 + 1_666_001_000,
 }
 
 
