@@ -174,9 +174,9 @@ def kernel_digest():
 
 # DRAM bytes (read + write) per launch of the dominant stage measured by ncu
 # at B = 64: {(workload, stage, kernel source digest): bytes}.  Summaries in
-# profiles/ (k_down_cube8m-6lv_B64.md).
+# profiles/ (k_translate_q4_cube8m-6lv_B64.md).
 NCU_TRAFFIC = {
-    ("cube8m-6lv", "translate5", "69c5ad055ed0013e"): 1_764_694_000 + 1_666_001_000,
+    ("cube8m-6lv", "translate5", "b97f4d857de6ec42"): 1_764_623_000 + 1_666_409_000,
 }
 
 

@@ -853,17 +853,18 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
         cudaEventDestroy(e0);
         return e;
     }
+    // a candidate that does not apply to this plan (its launcher refuses it,
+    // or its launch is rejected) is skipped and its launch error cleared
     auto time_stage = [&](int stage, int choice) -> double {
-        if (launch_stage<R>(a, stage, choice, s) != cudaSuccess) {
+        bool ok = launch_stage<R>(a, stage, choice, s) == cudaSuccess && cudaEventRecord(e0, s) == cudaSuccess;
+        for (int r = 0; ok && r < 3; ++r) ok = launch_stage<R>(a, stage, choice, s) == cudaSuccess;
+        ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0;
+        ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (!ok) {
             cudaGetLastError();
             return -1.0;
         }
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < 3; ++r) launch_stage<R>(a, stage, choice, s);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
         return ms / 3.0;
     };
     double tb = 0, ta = 0;
@@ -898,7 +899,7 @@ cudaError_t tune_args(ProductArgs<R> a, cudaStream_t s, Tuning &best, double *be
     cudaEventDestroy(e1);
     if (before) *before = tb;
     if (after) *after = ta;
-    return cudaGetLastError();
+    return cudaStreamSynchronize(s);   // a fault of any timed launch surfaces here
 }
 
 mlfma_status check_plan(mlfma_plan_t p)

@@ -66,7 +66,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-constexpr int kSmemCap = 200 * 1024;  // dynamic shared memory a kernel may ask for (227 KB per CTA on sm_103a)
+constexpr int kSmemCap = 227 * 1024;  // shared memory a CTA may use on sm_103a (static and dynamic together)
 constexpr int kStageCap = 96 * 1024;  // staging budget of the near / leaf kernels (keeps >= 2 CTAs per SM)
 
 inline int blocks_for(int64_t total, int threads)
@@ -78,10 +78,19 @@ inline int blocks_for(int64_t total, int threads)
 #define GRID_STRIDE(idx, total) \
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (total); idx += (int64_t)gridDim.x * blockDim.x)
 
+// Lets `kernel` ask for the CTA's whole shared memory (the device's opt-in
+// limit, at most kSmemCap) less what it declares statically.
 template <class K>
 cudaError_t allow_smem(K kernel)
 {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int cap = std::min(kSmemCap, optin) - (int)fa.sharedSizeBytes;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 
 // ------------------------------------------------------------ prepare ---

@@ -73,7 +73,10 @@ __device__ __forceinline__ void st_quad(float2 *p, int cols, bool a16, float4 lo
         }
 }
 
-template <int NB>
+// FULL: every thread's four columns exist and are 16-byte aligned (B a
+// multiple of NB, even row stride, aligned fields), so the loads and stores
+// take the two-vector path without a run-time test.
+template <int NB, bool FULL = false>
 __global__ void __launch_bounds__(kThreads) k_translate_q4(DevLevel<float> lv, int B, int Bs, int accumulate)
 {
     constexpr int NQD = NB / 4, QB = kThreads / NQD;
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(kThreads) k_translate_q4(DevLevel<float> lv, i
     const int e0 = lv.grp_ptr[P], ne = lv.grp_ptr[P + 1] - e0;
     const int m0 = lv.pchild_ptr[P], nc = lv.pchild_ptr[P + 1] - m0;
     const int l0 = lv.lty_ptr[P], nl = lv.lty_ptr[P + 1] - l0;
-    const bool a16 = (Bs % 2) == 0 && ((reinterpret_cast<uintptr_t>(lv.S) | reinterpret_cast<uintptr_t>(lv.G)) & 15) == 0;
+    const bool a16 = FULL || ((Bs % 2) == 0 && ((reinterpret_cast<uintptr_t>(lv.S) | reinterpret_cast<uintptr_t>(lv.G)) & 15) == 0);
     const float2 *al = reinterpret_cast<const float2 *>(lv.alpha);
     for (int i = threadIdx.x; i < nl * QB; i += blockDim.x) {
         const int lt = i / QB, qq = i - lt * QB;
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) k_translate_q4(DevLevel<float> lv, i
     for (int e = threadIdx.x; e < ne * 8; e += blockDim.x) s_ty[e] = lv.grp_lty[(int64_t)e0 * 8 + e];
     __syncthreads();
     const int qq = threadIdx.x / NQD, qd = threadIdx.x - qq * NQD;
-    const int cols = qq < nq ? max(0, min(4, ncols - 4 * qd)) : 0;
+    const int cols = qq < nq ? (FULL ? 4 : max(0, min(4, ncols - 4 * qd))) : 0;
     if (!cols) return;
     const int64_t KB = (int64_t)K * Bs;
     const float2 *S = reinterpret_cast<const float2 *>(lv.S) + (int64_t)(q0 + qq) * Bs + b0 + 4 * qd;
@@ -113,8 +116,16 @@ __global__ void __launch_bounds__(kThreads) k_translate_q4(DevLevel<float> lv, i
         for (int e = 0; e < ne; ++e) {
             const float2 *src = S + (int64_t)s_src[e] * 2 * KB;
             float4 s[2][2];
-            ld_quad(src, cols, a16, s[0][0], s[0][1]);
-            ld_quad(src + KB, cols, a16, s[1][0], s[1][1]);
+            if (FULL) {
+                const float4 *p4 = reinterpret_cast<const float4 *>(src), *q4 = reinterpret_cast<const float4 *>(src + KB);
+                s[0][0] = p4[0];
+                s[0][1] = p4[1];
+                s[1][0] = q4[0];
+                s[1][1] = q4[1];
+            } else {
+                ld_quad(src, cols, a16, s[0][0], s[0][1]);
+                ld_quad(src + KB, cols, a16, s[1][0], s[1][1]);
+            }
             // the four children's type slots (16-bit each) of this pass
             const int2 tyv = *reinterpret_cast<const int2 *>(&s_ty[e * 8 + c0]);
             const int tw[2] = {tyv.x, tyv.y};
@@ -146,12 +157,15 @@ __global__ void __launch_bounds__(kThreads) k_translate_q4(DevLevel<float> lv, i
 template <int NB>
 cudaError_t translate_q4_nb(const DevLevel<float> &lv, int B, int Bs, int acc, cudaStream_t s)
 {
+    const bool full = B % NB == 0 && Bs % 2 == 0 &&
+                      ((reinterpret_cast<uintptr_t>(lv.S) | reinterpret_cast<uintptr_t>(lv.G)) & 15) == 0;
     constexpr int QB = kThreads / (NB / 4);
     if (!lv.lty || !lv.grp_lty || lv.max_grp > kMaxEntries) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)lv.max_lty * QB * sizeof(float2);
     if (smem > (size_t)(96 * 1024)) return cudaErrorInvalidConfiguration;
     dim3 grid(lv.nparent, (lv.K + QB - 1) / QB, (B + NB - 1) / NB);
-    k_translate_q4<NB><<<grid, kThreads, smem, s>>>(lv, B, Bs, acc);
+    if (full) k_translate_q4<NB, true><<<grid, kThreads, smem, s>>>(lv, B, Bs, acc);
+    else k_translate_q4<NB, false><<<grid, kThreads, smem, s>>>(lv, B, Bs, acc);
     return cudaGetLastError();
 }
 
@@ -171,9 +185,11 @@ cudaError_t launch_translate_quad(const DevLevel<float> &lv, int B, int Bs, int 
 cudaError_t prime_translate_quad()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_translate_q4<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_translate_q4<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_translate_q4<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+#define ALLOW(k) do { if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)) != cudaSuccess) return e; } while (0)
+    ALLOW((k_translate_q4<16, false>)); ALLOW((k_translate_q4<32, false>)); ALLOW((k_translate_q4<64, false>));
+    ALLOW((k_translate_q4<16, true>)); ALLOW((k_translate_q4<32, true>)); ALLOW((k_translate_q4<64, true>));
+#undef ALLOW
+    return cudaSuccess;
 }
 
 }  // namespace mlfma
