@@ -318,9 +318,9 @@ mlfma_status mlfma_profile_stages(mlfma_plan_t plan, const void *x, int x_is_com
  *   bytes needed; so is B > max_batch.
  * - The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current and keeps it for the
- *   life of the process; make that first call before any stream capture
- *   begins, and do not call this entry point across a cudaDeviceReset of
- *   the device (the kept address belongs to the old context).
+ *   life of the process; do not call this entry point across a
+ *   cudaDeviceReset of the device (the kept address belongs to the old
+ *   context).
  * - Every call, on every plan, shares the one array and leaves its contents
  *   behind.  Nothing in it needs to start at zero: each pass writes every
  *   scratch value before reading it.  Calls whose work overlaps on the GPU
