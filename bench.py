@@ -176,7 +176,7 @@ def kernel_digest():
 # at B = 64: {(workload, stage, kernel source digest): bytes}.  Summaries in
 # profiles/ (k_translate_q4_cube8m-6lv_B64.md).
 NCU_TRAFFIC = {
-    ("cube8m-6lv", "translate5", "b97f4d857de6ec42"): 1_764_623_000 + 1_666_409_000,
+    ("cube8m-6lv", "translate5", "d39c757f68fed696"): 1_764_666_000 + 1_665_967_000,
 }
 
 

@@ -29,6 +29,7 @@ __device__ __forceinline__ void cmac2(float4 &acc, float2 a, float4 s)
 constexpr int kThreads = 128;
 constexpr int kMaxEntries = 216;   // entries of one parent (the plan's bound)
 constexpr int kCh = 4;             // children per pass
+constexpr unsigned kNone = 0xffffu;   // (entry, child) slot without a translation
 
 // Four columns of one field row: two 16-byte loads when all four exist and
 // are aligned, else the existing ones (zero past the end).
@@ -82,9 +83,10 @@ __global__ void __launch_bounds__(kThreads) k_translate_q4(DevLevel<float> lv, i
     constexpr int NQD = NB / 4, QB = kThreads / NQD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *s_al = reinterpret_cast<float2 *>(smem_raw);   // [local type][QB]
-    __shared__ int s_src[kMaxEntries];
-    __shared__ __align__(16) int16_t s_ty[kMaxEntries * 8];
+    __shared__ int64_t s_off[kMaxEntries];                  // offset of each entry's source field
+    __shared__ __align__(16) uint16_t s_ty[kMaxEntries * 8];   // per (entry, child): its row of s_al, or kNone
     const int K = lv.K;
+    const int64_t KB = (int64_t)K * Bs;
     const int P = blockIdx.x, q0 = blockIdx.y * QB, b0 = blockIdx.z * NB;
     const int nq = min(QB, K - q0), ncols = min(NB, B - b0);
     const int e0 = lv.grp_ptr[P], ne = lv.grp_ptr[P + 1] - e0;
@@ -96,13 +98,15 @@ __global__ void __launch_bounds__(kThreads) k_translate_q4(DevLevel<float> lv, i
         const int lt = i / QB, qq = i - lt * QB;
         s_al[i] = qq < nq ? al[(int64_t)lv.lty[l0 + lt] * K + q0 + qq] : make_float2(0.f, 0.f);
     }
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) s_src[e] = lv.grp_src[e0 + e];
-    for (int e = threadIdx.x; e < ne * 8; e += blockDim.x) s_ty[e] = lv.grp_lty[(int64_t)e0 * 8 + e];
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) s_off[e] = (int64_t)lv.grp_src[e0 + e] * 2 * KB;
+    for (int e = threadIdx.x; e < ne * 8; e += blockDim.x) {
+        const int t = lv.grp_lty[(int64_t)e0 * 8 + e];
+        s_ty[e] = (uint16_t)(t < 0 ? kNone : (unsigned)(t * QB));   // t * QB < 2^16 (launcher's shared-memory bound)
+    }
     __syncthreads();
     const int qq = threadIdx.x / NQD, qd = threadIdx.x - qq * NQD;
     const int cols = qq < nq ? (FULL ? 4 : max(0, min(4, ncols - 4 * qd))) : 0;
     if (!cols) return;
-    const int64_t KB = (int64_t)K * Bs;
     const float2 *S = reinterpret_cast<const float2 *>(lv.S) + (int64_t)(q0 + qq) * Bs + b0 + 4 * qd;
     const float2 *alq = s_al + qq;
     for (int c0 = 0; c0 < nc; c0 += kCh) {
@@ -114,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_translate_q4(DevLevel<float> lv, i
         const int nch = min(kCh, nc - c0);
 #pragma unroll 2
         for (int e = 0; e < ne; ++e) {
-            const float2 *src = S + (int64_t)s_src[e] * 2 * KB;
+            const float2 *src = S + s_off[e];
             float4 s[2][2];
             if (FULL) {
                 const float4 *p4 = reinterpret_cast<const float4 *>(src), *q4 = reinterpret_cast<const float4 *>(src + KB);
@@ -126,15 +130,15 @@ __global__ void __launch_bounds__(kThreads) k_translate_q4(DevLevel<float> lv, i
                 ld_quad(src, cols, a16, s[0][0], s[0][1]);
                 ld_quad(src + KB, cols, a16, s[1][0], s[1][1]);
             }
-            // the four children's type slots (16-bit each) of this pass
-            const int2 tyv = *reinterpret_cast<const int2 *>(&s_ty[e * 8 + c0]);
-            const int tw[2] = {tyv.x, tyv.y};
+            // the four children's coefficient rows (16-bit each) of this pass
+            const uint2 tyv = *reinterpret_cast<const uint2 *>(&s_ty[e * 8 + c0]);
+            const unsigned tw[2] = {tyv.x, tyv.y};
 #pragma unroll
             for (int c = 0; c < kCh; ++c) {
                 if (c >= nch) break;
-                const int ty = (int)(int16_t)((tw[c >> 1] >> (16 * (c & 1))) & 0xffff);
-                if (ty >= 0) {
-                    const float2 a = alq[ty * QB];
+                const unsigned off = (tw[c >> 1] >> (16 * (c & 1))) & 0xffffu;
+                if (off != kNone) {
+                    const float2 a = alq[off];
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
                         cmac2(acc[c][m][0], a, s[m][0]);
