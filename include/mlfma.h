@@ -53,7 +53,7 @@ typedef enum {
     MLFMA_ECUDA = 3,     /* a CUDA runtime call failed; message has the CUDA error */
     MLFMA_ENOTCONV = 4,  /* reserved for iterative solvers */
     MLFMA_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
-    MLFMA_ENOTSUP = 6    /* valid request this build does not support */
+    MLFMA_ENOTSUP = 6    /* valid request the library does not support */
 } mlfma_status;
 
 /* Arithmetic of a product.  MLFMA_FP64: complex FP64 everywhere (near field,
