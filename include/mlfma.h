@@ -550,6 +550,15 @@ mlfma_status mlfma_plan_info(mlfma_plan_t plan, mlfma_info *info);
  *   MLFMA_X_WIN_ANTERP float64 [K_child][K_parent]  the same for MLFMA_X_ANTERP
  *   MLFMA_X_WIN_SHAPE  int32 [8]       (groups, window width) of the four windowed
  *                                      stencils: up theta, up phi, down phi, down theta
+ *   MLFMA_X_SHIFT      float64 [8][K][2] phase shift exp(i k khat . (r_parent -
+ *                                      r_child)) of the aggregation into `level`
+ *                                      (1..leaf-1) per child octant o (bit 2: the
+ *                                      child lies at +x, bit 1: +y, bit 0: +z)
+ *   MLFMA_X_SHIFT_XY   float64 [8][K][2] its x and y part (the z pair kernels'
+ *                                      table: octants o and o ^ 1 share it)
+ *   MLFMA_X_SHIFT_Z    float64 [8][nth][2] its z part, one value per theta row
+ *                                      (MLFMA_X_SHIFT = SHIFT_XY x SHIFT_Z of the
+ *                                      sample's row)
  * The grid of level 1 exists for plans with at least 3 levels (it serves the
  * sibling scheme only).
  */
@@ -557,7 +566,8 @@ enum {
     MLFMA_X_PERM = 1, MLFMA_X_LEAF_BOX = 2, MLFMA_X_GRID = 3, MLFMA_X_ALPHA = 4,
     MLFMA_X_ALPHA_OFFS = 5, MLFMA_X_INTERP = 6, MLFMA_X_BOX_CENTERS = 7, MLFMA_X_NEAR_COUNT = 8,
     MLFMA_X_ANTERP = 9, MLFMA_X_ALPHA_J = 10, MLFMA_X_ALPHA_Y = 11, MLFMA_X_SIB_ALPHA = 12,
-    MLFMA_X_SIB_OFFS = 13, MLFMA_X_WIN_INTERP = 14, MLFMA_X_WIN_ANTERP = 15, MLFMA_X_WIN_SHAPE = 16
+    MLFMA_X_SIB_OFFS = 13, MLFMA_X_WIN_INTERP = 14, MLFMA_X_WIN_ANTERP = 15, MLFMA_X_WIN_SHAPE = 16,
+    MLFMA_X_SHIFT = 17, MLFMA_X_SHIFT_XY = 18, MLFMA_X_SHIFT_Z = 19
 };
 mlfma_status mlfma_export(mlfma_plan_t plan, int what, int level, void *dst, int64_t cap,
                           int64_t *needed);

@@ -1566,6 +1566,15 @@ mlfma_status mlfma_export(mlfma_plan_t p, int what, int level, void *dst, int64_
         else
             put(H.sib[level].type_off.data(), H.sib[level].type_off.size() * sizeof(int32_t));
         break;
+    case MLFMA_X_SHIFT:
+    case MLFMA_X_SHIFT_XY:
+    case MLFMA_X_SHIFT_Z: {
+        if (!(level >= 1 && level < H.leaf)) return fail(MLFMA_EINVAL, "no child-to-parent shift into this level");
+        const Level &Lv = H.lv[level];
+        const std::vector<cd> &t = what == MLFMA_X_SHIFT ? Lv.shift : what == MLFMA_X_SHIFT_XY ? Lv.shift_xy : Lv.gam;
+        put(t.data(), t.size() * sizeof(cd));
+        break;
+    }
     case MLFMA_X_INTERP: {
         if (!(level >= 2 && level < H.leaf)) return fail(MLFMA_EINVAL, "no interpolation into this level");
         const Level &Pa = H.lv[level], &C = H.lv[level + 1];

@@ -20,7 +20,8 @@ MIXED_3XTF32 = 3    # FP32 product, tensor-core (3xTF32 split) interpolation
 MAX_LEVELS = 22
 
 (X_PERM, X_LEAF_BOX, X_GRID, X_ALPHA, X_ALPHA_OFFS, X_INTERP, X_BOX_CENTERS, X_NEAR_COUNT, X_ANTERP, X_ALPHA_J,
- X_ALPHA_Y, X_SIB_ALPHA, X_SIB_OFFS, X_WIN_INTERP, X_WIN_ANTERP, X_WIN_SHAPE) = range(1, 17)
+ X_ALPHA_Y, X_SIB_ALPHA, X_SIB_OFFS, X_WIN_INTERP, X_WIN_ANTERP, X_WIN_SHAPE, X_SHIFT, X_SHIFT_XY,
+ X_SHIFT_Z) = range(1, 20)
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ENOTSUP"}
 
@@ -219,6 +220,8 @@ class MlfmaPlan:
             return buf.view(np.float64).reshape(-1, 4)
         if what in (X_ALPHA, X_ALPHA_J, X_ALPHA_Y, X_SIB_ALPHA):
             return buf.view(np.complex128)
+        if what in (X_SHIFT, X_SHIFT_XY, X_SHIFT_Z):   # [octant][sample or theta row]
+            return buf.view(np.complex128).reshape(8, -1)
         if what == X_BOX_CENTERS:
             return buf.view(np.float64).reshape(-1, 3)
         return buf.view(np.float64)

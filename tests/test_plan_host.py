@@ -230,6 +230,47 @@ def test_windowed_tables_rebuild_the_stencils(name, order):
             assert np.abs(a - b).max() <= 1e-15 * np.abs(b).max()
 
 
+@pytest.mark.parametrize("name", ["sphere-r2m-ico5", "cube8m-6lv"])
+def test_aggregation_shift_and_its_z_split(name):
+    """The phase shift of the aggregation from a child box to its parent
+    (Section III-C: a child's pattern about its own centre, times
+    exp(i k khat . (r_parent - r_child)), is its pattern about the parent's
+    centre) matches each child's offset taken from the plan's box centres at
+    every parent sample; it factors into an x-y part and a theta-row z part,
+    and the x-y part is the same for the two children that differ only in z
+    (the sharing the z-pair up and down kernels rely on)."""
+    W, v, t, P = host_plan(name)
+    leaf = P.info()["leaf_level"]
+    for l in range(2, leaf):
+        g, kh, _, _ = _grid(P, l)
+        nth = len(np.unique(g[:, 0]))
+        nph = g.shape[0] // nth
+        S, Sxy, Sz = (P.export(w, l) for w in (M.X_SHIFT, M.X_SHIFT_XY, M.X_SHIFT_Z))
+        assert S.shape == (8, g.shape[0]) and Sxy.shape == (8, g.shape[0]) and Sz.shape == (8, nth)
+        # every child's offset from its parent, from the exported centres
+        cp, cc = P.export(M.X_BOX_CENTERS, l), P.export(M.X_BOX_CENTERS, l + 1)
+        h = P.info()["root_side"] / 2 ** (l + 2)
+        seen = set()
+        for c in np.random.default_rng(l).choice(len(cc), min(len(cc), 200), replace=False):
+            p = np.argmin(np.abs(cp - cc[c]).sum(1))
+            d = cp[p] - cc[c]                                   # r_parent - r_child
+            assert np.allclose(np.abs(d), h, rtol=1e-12, atol=0)
+            o = 4 * (d[0] < 0) + 2 * (d[1] < 0) + (d[2] < 0)    # the child lies at +x / +y / +z
+            seen.add(o)
+            ref = np.exp(1j * W.k * (kh @ d))
+            assert np.abs(S[o] - ref).max() < 1e-12, (l, o)
+        assert len(seen) >= 2
+        assert np.abs(np.abs(S) - 1).max() < 1e-14
+        assert np.abs(S - Sxy * np.repeat(Sz, nph, axis=1)).max() < 1e-14
+        for o in range(0, 8, 2):
+            assert np.array_equal(Sxy[o], Sxy[o + 1])
+            assert np.array_equal(Sz[o], Sz[0]) and np.array_equal(Sz[o + 1], Sz[1])
+        assert np.abs(Sz[0] * Sz[1] - 1).max() < 1e-14     # the two z parts are conjugate
+    for bad in (0, leaf):   # no aggregation into the root or into the leaf level
+        with pytest.raises(M.MlfmaError):
+            P.export(M.X_SHIFT, bad)
+
+
 def test_tune_cache_key_and_file(tmp_path):
     """The tuned-shape cache: keys separate GPUs, trees, columns and
     precisions; the file round-trips and a damaged file reads as empty."""
