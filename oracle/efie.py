@@ -20,27 +20,32 @@ ETA0 = 376.730313668  # free-space impedance, ohm
 _lib = None
 
 
+def load(path: str):
+    """Open an oracle library compiled from efie_oracle.c at `path` and
+    declare its entry points (lib() opens the package's own build)."""
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i = ctypes.c_int
+    d = ctypes.c_double
+    L.oracle_zfill.argtypes = [i, P, i, P, i, P, P, P, d, d, P, i]
+    L.oracle_dzfill.argtypes = [i, P, i, P, i, P, P, P, d, d, P, i]
+    L.oracle_zrows.argtypes = [i, P, i, P, i, P, P, P, d, d, i, P, P, i]
+    L.oracle_dzrows.argtypes = [i, P, i, P, i, P, P, P, d, d, i, P, P, i]
+    L.oracle_tri_potential.argtypes = [i, P, i, P, P, i, d, i, P]
+    L.oracle_static_potential.argtypes = [P, P, P, P, P]
+    L.oracle_pair_is_singular.argtypes = [i, P, i, P, i, i]
+    L.oracle_rule7.argtypes = [P]
+    for f in ("oracle_zfill", "oracle_dzfill", "oracle_zrows", "oracle_dzrows", "oracle_tri_potential",
+              "oracle_static_potential", "oracle_pair_is_singular", "oracle_rule7",
+              "oracle_num_threads"):
+        getattr(L, f).restype = ctypes.c_int
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        P = ctypes.c_void_p
-        i = ctypes.c_int
-        d = ctypes.c_double
-        L.oracle_zfill.argtypes = [i, P, i, P, i, P, P, P, d, d, P, i]
-        L.oracle_dzfill.argtypes = [i, P, i, P, i, P, P, P, d, d, P, i]
-        L.oracle_zrows.argtypes = [i, P, i, P, i, P, P, P, d, d, i, P, P, i]
-        L.oracle_dzrows.argtypes = [i, P, i, P, i, P, P, P, d, d, i, P, P, i]
-        L.oracle_tri_potential.argtypes = [i, P, i, P, P, i, d, i, P]
-        L.oracle_static_potential.argtypes = [P, P, P, P, P]
-        L.oracle_pair_is_singular.argtypes = [i, P, i, P, i, i]
-        L.oracle_rule7.argtypes = [P]
-        for f in ("oracle_zfill", "oracle_dzfill", "oracle_zrows", "oracle_dzrows", "oracle_tri_potential",
-                  "oracle_static_potential", "oracle_pair_is_singular", "oracle_rule7",
-                  "oracle_num_threads"):
-            getattr(L, f).restype = ctypes.c_int
-        _lib = L
+        _lib = load(_build.build())
     return _lib
 
 
