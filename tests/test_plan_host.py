@@ -331,3 +331,57 @@ def test_overlapping_x_and_y_rejected():
         for y in (x + xbytes, x - ybytes):
             st = fn(P._h, ctypes.c_void_p(x), 0, ctypes.c_void_p(y), B, M.FP64, None)
             assert st == 1 and b"overlap" not in lib.mlfma_last_error(), (fn, y - x)
+
+
+def test_host_only_plan_refuses_device_work():
+    """A host-only plan (tables, no device memory) answers every product,
+    the tuner and the field export with MLFMA_EINVAL and a message naming
+    the reason, before any CUDA call; so do a NULL plan, a NULL buffer and
+    B < 1.  Waiting on it (mlfma_sync) has nothing to wait for."""
+    import ctypes
+    W, v, t, P = host_plan("sphere-r0.5m-ico2")
+    lib = M.load()
+    n, B = P.n, 2
+    x, y = np.zeros((n, B)), np.zeros((n, B), complex)
+    xp, yp = ctypes.c_void_p(x.ctypes.data), ctypes.c_void_p(y.ctypes.data)
+    for fn in (lib.mlfma_matvec, lib.mlfma_matvec_adjoint, lib.mlfma_matvec_dk, lib.mlfma_matvec_dk_adjoint,
+               lib.mlfma_matvec_x, lib.mlfma_matvec_r, lib.mlfma_matvec_host, lib.mlfma_matvec_noalloc):
+        assert fn(P._h, xp, 0, yp, B, M.FP64, None) == 1 and b"host-only" in lib.mlfma_last_error(), fn
+        assert fn(None, xp, 0, yp, B, M.FP64, None) == 1, fn
+        assert fn(P._h, None, 0, yp, B, M.FP64, None) == 1 and b"NULL" in lib.mlfma_last_error(), fn
+        assert fn(P._h, xp, 0, yp, 0, M.FP64, None) == 1 and b"B must be" in lib.mlfma_last_error(), fn
+    ms = (ctypes.c_double * 64)()
+    assert lib.mlfma_profile_stages(P._h, xp, 0, yp, B, M.FP64, None, ms) == 1
+    d0, d1 = ctypes.c_double(), ctypes.c_double()
+    assert lib.mlfma_tune(P._h, B, 0, M.FP64, None, ctypes.byref(d0), ctypes.byref(d1)) == 1
+    assert b"host-only" in lib.mlfma_last_error()
+    need = ctypes.c_int64()
+    assert lib.mlfma_export_field(P._h, M.FP64, 0, 2, 1, None, 0, ctypes.byref(need)) == 1
+    assert lib.mlfma_sync(P._h, None) == 0
+
+
+def test_tune_set_keeps_documented_shapes_only():
+    """mlfma_tune_set / mlfma_tune_get (host logic): every documented value
+    of each field round-trips per (columns, precision), other column counts
+    keep the built-in shapes, and a value outside a field's documented set is
+    MLFMA_EINVAL (include/mlfma.h lists the sets)."""
+    W, v, t, P = host_plan("sphere-r2m-ico5")
+    L = M.MAX_LEVELS
+    up = [0, 1, 2, 4, 8, 16, 202, 204, 208, 216, 304, 308, 316, 404, 408, 704, 708, 716]
+    down = [0, 1, 2, 4, 8, 16, 104, 108, 204, 208, 216, 304, 308, 316, 404, 408, 504, 508, 804, 808]
+    fields = [(0, range(4)), (1, range(6)), (2, range(7)), (3 + 2, up), (3 + L + 3, down), (3 + 2 * L + 4, range(12))]
+    for f, values in fields:
+        for val in values:
+            ch = np.zeros(M.TUNE_FIELDS, np.int32)
+            ch[f] = val
+            P.tune_set(16, ch, M.FP32)
+            assert np.array_equal(P.tune_get(16, M.FP32), ch), (f, val)
+    assert not P.tune_get(32, M.FP32).any() and not P.tune_get(16, M.FP64).any()
+    for f, bad in ((0, 4), (1, 6), (2, 7), (3 + 2, 3), (3 + 2, 416), (3 + 2, 804), (3 + L + 3, 416),
+                   (3 + L + 3, 704), (3 + 2 * L + 4, 12), (3 + 2 * L + 4, -1)):
+        ch = np.zeros(M.TUNE_FIELDS, np.int32)
+        ch[f] = bad
+        with pytest.raises(M.MlfmaError):
+            P.tune_set(16, ch, M.FP32)
+    with pytest.raises(M.MlfmaError):
+        P.tune_set(0, np.zeros(M.TUNE_FIELDS, np.int32), M.FP32)
