@@ -64,6 +64,52 @@ def test_rwg_canonical_order_and_orientation():
     assert np.allclose(r["length"], np.linalg.norm(v[ev[:, 1]] - v[ev[:, 0]], axis=1))
 
 
+@pytest.mark.parametrize("mesh", [lambda: workloads.icosphere(2, 0.5), lambda: workloads.cube(1.0, 3)])
+def test_rwg_normal_continuity_and_divergence(mesh):
+    """The defining identities of the RWG functions the oracle uses
+    (f = +-l / (2 A+-) (r - v+-) on T+-, div f = +-l / A+-): across the common
+    edge the normal component is 1 from both triangles (no line charge);
+    along the two other edges of each triangle f is tangential (no flux
+    leaves the support); and the surface divergence of the vector field,
+    taken by finite differences in the triangle's plane, is the +-l / A+-
+    that the scalar-potential term of Eq. (5) uses."""
+    v, t = mesh()
+    r = rwg_list(v, t)
+    for e in range(r["tri"].shape[0]):
+        lo, hi = v[r["edge_v"][e]]
+        lhat = (hi - lo) / np.linalg.norm(hi - lo)
+        for side, sgn in ((0, 1.0), (1, -1.0)):
+            tri = r["tri"][e, side]
+            vf = v[r["vfree"][e, side]]
+            P = v[t[tri]]
+            nrm = np.cross(P[1] - P[0], P[2] - P[0])
+            A = 0.5 * np.linalg.norm(nrm)
+            nhat = nrm / (2 * A)
+            c = sgn * r["length"][e] / (2 * A)
+            f = lambda x: c * (x - vf)
+            # in-plane unit normal of the common edge in this triangle, pointing
+            # from T+ into T- (away from v+ on T+, towards v- on T-)
+            d = (lo - vf) if side == 0 else (vf - lo)
+            mp = d - np.dot(d, lhat) * lhat
+            mp /= np.linalg.norm(mp)
+            for s_ in (0.2, 0.5, 0.9):
+                x = lo + s_ * (hi - lo)
+                assert abs(np.dot(f(x), mp) - 1.0) < 1e-12
+            # the other two edges: from the free vertex to each end of the common edge
+            for end in (lo, hi):
+                dvec = end - vf
+                nout = np.cross(dvec, nhat)
+                for s_ in (0.3, 0.7):
+                    assert abs(np.dot(f(vf + s_ * dvec), nout)) < 1e-12 * abs(c) * np.linalg.norm(dvec) * np.linalg.norm(nout)
+            # surface divergence by central differences along two in-plane directions
+            u1 = lhat
+            u2 = np.cross(nhat, u1)
+            x0 = P.mean(0)
+            h = 1e-4 * np.sqrt(A)
+            div = sum(np.dot(f(x0 + h * u) - f(x0 - h * u), u) / (2 * h) for u in (u1, u2))
+            assert abs(div - sgn * r["length"][e] / A) < 1e-7 * r["length"][e] / A
+
+
 def test_rwg_rejects_bad_meshes():
     v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1]], float)
     with pytest.raises(MeshError):   # edge 0-1 on three triangles

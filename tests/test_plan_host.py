@@ -385,3 +385,45 @@ def test_tune_set_keeps_documented_shapes_only():
             P.tune_set(16, ch, M.FP32)
     with pytest.raises(M.MlfmaError):
         P.tune_set(0, np.zeros(M.TUNE_FIELDS, np.int32), M.FP32)
+
+
+def test_translation_tables_match_scipy_series():
+    """Eq. (8)'s translation function, its j_l and y_l halves (the sin- and
+    cos-kernel tables of Section V, Eqs. (SinKer), (CosKer)) and the sibling
+    sin-kernel table, as the library builds them with its own spherical
+    Bessel and Legendre recurrences, against SciPy's spherical_jn,
+    spherical_yn and eval_legendre at every sample of each level.  The r = 8 m
+    sphere puts L = 57 on 4-wavelength boxes, so the nearest offsets reach
+    orders well above kr (where an upward j_l recurrence would fail)."""
+    from scipy.special import eval_legendre, spherical_jn, spherical_yn
+    v, t = workloads.icosphere(3, 8.0)
+    k = 2 * math.pi
+    P = M.MlfmaPlan(v, t, k, 4, 3.0, host_only=True)
+    inf = P.info()
+    assert inf["trunc_L"][2] == 57
+    for l in range(2, inf["leaf_level"] + 1):
+        _, kh, _, _ = _grid(P, l)
+        L = inf["trunc_L"][l]
+        a = inf["root_side"] / 2 ** l
+        ls = np.arange(L + 1)
+        il = (1j ** ls) * (2 * ls + 1)
+        tables = [(M.X_ALPHA_OFFS, M.X_ALPHA_J, M.X_ALPHA_Y, M.X_ALPHA), (M.X_SIB_OFFS, M.X_SIB_ALPHA, None, None)]
+        for offs_code, jcode, ycode, full in tables:
+            offs = P.export(offs_code, l)
+            aj = P.export(jcode, l).reshape(len(offs), -1)
+            ay = P.export(ycode, l).reshape(len(offs), -1) if ycode else None
+            al = P.export(full, l).reshape(len(offs), -1) if full else None
+            order = np.argsort(np.linalg.norm(offs, axis=1))
+            pick = np.unique(np.concatenate([order[:6], order[-4:],
+                                             np.random.default_rng(l).choice(len(offs), min(6, len(offs)), False)]))
+            for ti in pick:
+                r = a * offs[ti]
+                rn = np.linalg.norm(r)
+                Pl = eval_legendre(ls[:, None], (kh @ r / rn)[None, :])
+                jl, yl = spherical_jn(ls, k * rn), spherical_yn(ls, k * rn)
+                sj = np.sum((2 * ls + 1) * np.abs(jl))
+                assert np.abs(aj[ti] - (il * jl) @ Pl).max() <= 1e-11 * sj, (l, offs[ti])
+                if ay is not None:
+                    sy = np.sum((2 * ls + 1) * np.abs(yl))
+                    assert np.abs(ay[ti] - (il * yl) @ Pl).max() <= 1e-11 * sy, (l, offs[ti])
+                    assert np.abs(al[ti] - (aj[ti] + 1j * ay[ti])).max() <= 1e-14 * (sj + sy)
