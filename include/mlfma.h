@@ -551,7 +551,7 @@ mlfma_status mlfma_plan_info(mlfma_plan_t plan, mlfma_info *info);
  *   MLFMA_X_WIN_SHAPE  int32 [8]       (groups, window width) of the four windowed
  *                                      stencils: up theta, up phi, down phi, down theta
  *   MLFMA_X_SHIFT      float64 [8][K][2] phase shift exp(i k khat . (r_parent -
- *                                      r_child)) of the aggregation into `level`
+ *                                      r_child)) of the aggregation (Section III-C) into `level`
  *                                      (1..leaf-1) per child octant o (bit 2: the
  *                                      child lies at +x, bit 1: +y, bit 0: +z)
  *   MLFMA_X_SHIFT_XY   float64 [8][K][2] its x and y part (the z pair kernels'
