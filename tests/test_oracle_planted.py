@@ -6,7 +6,11 @@ compiled on the CPU, and at least one of the oracle's own pins
 semidefinite resistance, the plane-wave identity for Re Z, the sphere's
 closed-form characteristic values, brute-force quadrature of the 1/R and
 exp(ikR)/R potentials, central differences in k) must fail against it.  The
-unchanged source passes all of them."""
+unchanged source passes all of them.  The eigen half of the oracle
+(oracle/cm.py: the pencil of Eq. (GEP), its symmetric reduction and the
+first-order slopes) gets the same treatment with a planted copy of the
+module, against the sphere's closed-form values and slopes."""
+import importlib.util
 import math
 import re
 
@@ -94,3 +98,69 @@ def test_planted_mistake_fails_a_pin(tmp_path, monkeypatch, slip, fname, old, ne
     lib = efie.load(obuild.compile_source(str(tmp_path / "planted.c"), str(tmp_path / "libplanted.so")))
     monkeypatch.setattr(efie, "_lib", lib)
     assert _pins(), slip
+
+
+# (slip, function of oracle/cm.py it goes into, text there, planted text)
+CM_PLANTS = [
+    ("resistance taken as +Re Z", "cm_values", "R = -Z.real", "R = Z.real"),
+    ("pencil inverted (mu returned as lambda)", "cm_values", "lam = 1.0 / mu[idx]", "lam = mu[idx]"),
+    ("values farthest from zero selected", "cm_values", "np.argsort(-np.abs(mu))[:nev]", "np.argsort(np.abs(mu))[:nev]"),
+    ("R factored as U D instead of U D^1/2", "cm_values_symmetric",
+     "np.sqrt(np.clip(d, 0.0, None))", "np.clip(d, 0.0, None)"),
+    ("X^-1 dropped from the reduction", "cm_values_symmetric",
+     "M = U.T @ scipy.linalg.lu_solve(lu, U, check_finite=False)", "M = U.T @ U"),
+    ("slope: wrong sign of lambda R'", "cm_derivatives", "- lam[m] * (v @ (Rd @ v))", "+ lam[m] * (v @ (Rd @ v))"),
+    ("slope: normalised by J^T X J", "cm_derivatives", "/ (v @ (R @ v))", "/ (v @ (X @ v))"),
+    ("slope: real part of dZ/dk as X'", "cm_derivatives", "Xd = dZ.imag", "Xd = dZ.real"),
+]
+
+
+def _py_scope(src, fname):
+    m = re.search(r"^def %s\(" % fname, src, re.M)
+    assert m, fname
+    nxt = re.search(r"^def ", src[m.end():], re.M)
+    return m.start(), (m.end() + nxt.start()) if nxt else len(src)
+
+
+def _cm_pins(stop_at_first=True):
+    from oracle import cm  # noqa: F401  (the pins look their functions up on the module)
+    failed = []
+
+    def check(name, fn, *args):
+        if failed and stop_at_first:
+            return
+        try:
+            fn(*args)
+        except Exception:
+            failed.append(name)
+
+    v, t = workloads.icosphere(2, 0.5)
+    P = efie.Problem(v, t, 2 * math.pi)
+    sphere = (P, P.dense())
+    check("symmetric reduction on a random semidefinite pencil", tm.test_symmetric_reduction_random_semidefinite_pencil)
+    check("sphere characteristic values vs the closed form", tm.test_sphere_cm_values_coarse, sphere)
+    check("symmetric reduction equals the QZ route", tm.test_symmetric_reduction_equals_qz, sphere)
+    check("sphere slopes vs the closed form", td.test_sphere_dlambda_dk_against_closed_form,
+          2, (0.05, 0.03, 0.16), "dense")
+    return failed
+
+
+def test_unchanged_eigen_oracle_passes_every_pin():
+    assert _cm_pins(stop_at_first=False) == []
+
+
+@pytest.mark.parametrize("slip,fname,old,new", CM_PLANTS, ids=[p[0] for p in CM_PLANTS])
+def test_planted_eigen_mistake_fails_a_pin(tmp_path, monkeypatch, slip, fname, old, new):
+    from oracle import cm
+    src = open(cm.__file__).read()
+    a, b = _py_scope(src, fname)
+    body = src[a:b]
+    assert body.count(old) == 1, (fname, old)
+    path = tmp_path / "planted_cm.py"
+    path.write_text(src[:a] + body.replace(old, new) + src[b:])
+    spec = importlib.util.spec_from_file_location("planted_cm", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    for name in ("cm_values", "cm_values_arnoldi", "cm_values_symmetric", "cm_derivatives"):
+        monkeypatch.setattr(cm, name, getattr(mod, name))
+    assert _cm_pins(), slip
