@@ -9,7 +9,9 @@ exp(ikR)/R potentials, central differences in k) must fail against it.  The
 unchanged source passes all of them.  The eigen half of the oracle
 (oracle/cm.py: the pencil of Eq. (GEP), its symmetric reduction and the
 first-order slopes) gets the same treatment with a planted copy of the
-module, against the sphere's closed-form values and slopes."""
+module, against the sphere's closed-form values and slopes, and so does the
+RWG list (oracle/rwg.py), against its counts, order, orientation, the RWG
+identities and the library's own list."""
 import importlib.util
 import math
 import re
@@ -22,6 +24,7 @@ from oracle import efie
 from tests import test_oracle_dk as td
 from tests import test_oracle_matrix as tm
 from tests import test_oracle_quadrature as tq
+from tests import test_plan_host as th
 
 # (slip, function it goes into, text there, planted text)
 PLANTS = [
@@ -164,3 +167,50 @@ def test_planted_eigen_mistake_fails_a_pin(tmp_path, monkeypatch, slip, fname, o
     for name in ("cm_values", "cm_values_arnoldi", "cm_values_symmetric", "cm_derivatives"):
         monkeypatch.setattr(cm, name, getattr(mod, name))
     assert _cm_pins(), slip
+
+
+# (slip, text in oracle/rwg.py's rwg_list, planted text)
+RWG_PLANTS = [
+    ("edges sorted by the larger vertex first", "np.lexsort((~fwd, hi, lo))", "np.lexsort((~fwd, lo, hi))"),
+    ("free vertex taken from the edge itself", "opp = tris[:, [2, 0, 1]]", "opp = tris[:, [1, 2, 0]]"),
+    ("T+ and T- swapped (free vertices not)", "tp, tm = tid[two], tid[two + 1]", "tp, tm = tid[two + 1], tid[two]"),
+    ("edges that share their smaller vertex merged", "(lo[1:] != lo[:-1]) | (hi[1:] != hi[:-1])", "(lo[1:] != lo[:-1])"),
+    ("edge length halved", "axis=1)\n    return", "axis=1) / 2\n    return"),
+]
+
+
+def _rwg_pins():
+    failed = []
+
+    def check(name, fn, *args):
+        if failed:
+            return
+        try:
+            fn(*args)
+        except Exception:
+            failed.append(name)
+
+    check("counts", tm.test_rwg_counts, lambda: workloads.icosphere(3, 1.0), 1920)
+    check("canonical order and orientation", tm.test_rwg_canonical_order_and_orientation)
+    check("RWG identities", tm.test_rwg_normal_continuity_and_divergence, lambda: workloads.icosphere(2, 0.5))
+    check("the library's own list", th.test_rwg_list_matches_oracle, "sphere-r0.5m-ico3")
+    return failed
+
+
+@pytest.mark.parametrize("slip,old,new", RWG_PLANTS, ids=[p[0] for p in RWG_PLANTS])
+def test_planted_rwg_mistake_fails_a_pin(tmp_path, monkeypatch, slip, old, new):
+    from oracle import rwg
+    src = open(rwg.__file__).read()
+    assert src.count(old) == 1, old
+    path = tmp_path / "planted_rwg.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("planted_rwg", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    for m in (rwg, tm, th, efie):
+        monkeypatch.setattr(m, "rwg_list", mod.rwg_list)
+    assert _rwg_pins(), slip
+
+
+def test_unchanged_rwg_list_passes_every_pin():
+    assert _rwg_pins() == []
