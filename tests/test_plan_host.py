@@ -427,3 +427,40 @@ def test_translation_tables_match_scipy_series():
                     sy = np.sum((2 * ls + 1) * np.abs(yl))
                     assert np.abs(ay[ti] - (il * yl) @ Pl).max() <= 1e-11 * sy, (l, offs[ti])
                     assert np.abs(al[ti] - (aj[ti] + 1j * ay[ti])).max() <= 1e-14 * (sj + sy)
+
+
+@pytest.mark.parametrize("case", ["nan vertex", "inf vertex", "digits 0", "digits nan", "k nan", "k inf", "levels 23",
+                                  "max_batch 0", "interp 0", "interp 40", "negative index", "empty", "zero area"])
+def test_plan_arguments_rejected(case):
+    """mlfma_plan answers each invalid argument with MLFMA_EINVAL (status 1)
+    and a message, before any device work: non-finite coordinates or
+    wavenumber, digits outside 1..15, levels outside 2..21, max_batch
+    outside 1..4096, an odd or out-of-range interpolation order, a vertex
+    index out of range, an empty mesh, a triangle of zero area."""
+    v, t = workloads.icosphere(2, 0.5)
+    k, kw, levels, digits = 2 * math.pi, {}, 3, 3.0
+    if case in ("nan vertex", "inf vertex"):
+        v = v.copy()
+        v[0, 0] = np.nan if case == "nan vertex" else np.inf
+    elif case == "digits 0":
+        digits = 0.0
+    elif case == "digits nan":
+        digits = float("nan")
+    elif case in ("k nan", "k inf"):
+        k = float("nan") if case == "k nan" else float("inf")
+    elif case == "levels 23":
+        levels = 23
+    elif case == "max_batch 0":
+        kw["max_batch"] = 0
+    elif case in ("interp 0", "interp 40"):
+        kw["interp_order"] = 0 if case == "interp 0" else 40
+    elif case == "negative index":
+        t = np.where(t == 0, -1, t)
+    elif case == "empty":
+        t = t[:0]
+    elif case == "zero area":
+        v = np.vstack([v, v[:1]])
+        t = np.vstack([t, [[0, len(v) - 1, t[0, 1]]]])
+    with pytest.raises(M.MlfmaError) as e:
+        M.MlfmaPlan(v, t, k, levels, digits, host_only=True, **kw)
+    assert e.value.status == 1 and str(e.value)
