@@ -230,8 +230,13 @@ mlfma_status mlfma_matvec_host(mlfma_plan_t plan, const void *x, int x_is_comple
  * and the fastest kept for later mlfma_matvec / adjoint / profile calls
  * with the same (prec, columns); a captured graph for them is re-captured.
  * ms_default / ms_tuned (may be NULL) receive the sums of the stage times
- * with the built-in and with the chosen shapes.  Synchronous; overwrites the
- * plan's internal buffers.  Errors: EINVAL, ECUDA.
+ * with the built-in and with the chosen shapes.  A candidate that does not
+ * apply to the plan (its launcher refuses it or the launch is rejected) is
+ * skipped; the call fails only when the built-in pass fails or a timed
+ * launch faults.  A built-in shape is kept unless a candidate is at least
+ * 2 % faster.  Synchronous; overwrites the plan's internal buffers.
+ * Errors: EINVAL (host-only plan, B outside 1..max_batch, precision not set
+ * up), ECUDA.
  */
 mlfma_status mlfma_tune(mlfma_plan_t plan, int64_t B, int x_is_complex, int prec, void *stream,
                         double *ms_default, double *ms_tuned);
