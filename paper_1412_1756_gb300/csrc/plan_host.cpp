@@ -400,7 +400,7 @@ std::string build_plan_host(PlanHost &P, const double *verts, int64_t nv, const 
     if (!(k > 0) || !std::isfinite(k)) return "k must be positive and finite";
     if (levels < 2 || levels > 21) return "levels must be in 2..21";
     if (!(digits >= 1 && digits <= 15)) return "digits must be in 1..15";
-    if (order < 2 || order > 12 || (order & 1)) return "interp_order must be even, 2..12";
+    if (order < 4 || order > 12 || (order & 1)) return "interp_order must be even, 4..12";
     if (nt > (int64_t)1 << 30 || nv > (int64_t)1 << 30) return "mesh too large";
     P.k = k; P.digits = digits; P.levels = levels; P.leaf = levels - 1; P.order = order; P.eta = eta;
     P.V.assign(verts, verts + 3 * nv);

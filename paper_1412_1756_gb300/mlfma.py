@@ -38,17 +38,23 @@ TUNE_FIELDS = 3 + 3 * 22
 
 
 class MlfmaError(RuntimeError):
+    """A C-ABI call returned a status other than MLFMA_OK: `status` is the
+    code (1 EINVAL, 2 ENOMEM, 3 ECUDA, 4 ENOTCONV, 5 ETIMEOUT, 6 ENOTSUP),
+    the message is mlfma_last_error()."""
+
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS.get(status, status), msg))
         self.status = status
 
 
 class Opts(ctypes.Structure):
+    """mlfma_opts (include/mlfma.h)."""
     _fields_ = [("interp_order", ctypes.c_int), ("max_batch", ctypes.c_int), ("precisions", ctypes.c_int),
                 ("host_only", ctypes.c_int), ("device", ctypes.c_int), ("eta", ctypes.c_double)]
 
 
 class CmOpts(ctypes.Structure):
+    """mlfma_cm_opts: options of cm_ira_solve / cm_block_solve."""
     _fields_ = [("nev", ctypes.c_int), ("ncv", ctypes.c_int), ("op", ctypes.c_int), ("prec", ctypes.c_int),
                 ("tol", ctypes.c_double), ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("max_inner", ctypes.c_int), ("max_restarts", ctypes.c_int), ("use_sai", ctypes.c_int),
@@ -56,11 +62,13 @@ class CmOpts(ctypes.Structure):
 
 
 class CmStats(ctypes.Structure):
+    """mlfma_cm_stats: counters of an eigensolve."""
     _fields_ = [("restarts", ctypes.c_int), ("inner_iterations", ctypes.c_int64), ("products", ctypes.c_int64),
                 ("converged", ctypes.c_int), ("inner_converged", ctypes.c_int), ("seconds", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
+    """mlfma_info: tree and table sizes of a plan (mlfma_plan_info)."""
     _fields_ = [("n", ctypes.c_int64), ("levels", ctypes.c_int), ("leaf_level", ctypes.c_int),
                 ("root_side", ctypes.c_double), ("root_center", ctypes.c_double * 3),
                 ("near_nnz", ctypes.c_int64), ("leaf_boxes", ctypes.c_int64), ("max_leaf_unknowns", ctypes.c_int),
@@ -73,6 +81,7 @@ _lib = None
 
 
 def library_path() -> str:
+    """Path of the in-tree compiled library."""
     return _build.LIB
 
 
@@ -183,6 +192,8 @@ class MlfmaPlan:
 
     # ------------------------------------------------------------ queries
     def info(self) -> dict:
+        """Tree and table sizes (mlfma_plan_info) as a dict; per-level lists
+        are indexed by level, 0 = root."""
         inf = Info()
         _check(self._lib.mlfma_plan_info(self._h, ctypes.byref(inf)))
         nl = inf.levels
@@ -196,12 +207,16 @@ class MlfmaPlan:
         }
 
     def rwg_edges(self):
+        """(edge_v [N, 2], tri_pm [N, 2]): each unknown's edge vertices and its
+        T+ / T- triangles, canonical order (mlfma_rwg_edges)."""
         ev = np.zeros((self.n, 2), np.int32)
         tp = np.zeros((self.n, 2), np.int32)
         _check(self._lib.mlfma_rwg_edges(self._h, _np_ptr(ev), _np_ptr(tp)))
         return ev, tp
 
     def export(self, what: int, level: int = 0) -> np.ndarray:
+        """A plan table (mlfma_export, an X_* code) as a NumPy array of the
+        layout include/mlfma.h gives for that code."""
         need = ctypes.c_int64()
         _check(self._lib.mlfma_export(self._h, what, level, None, 0, ctypes.byref(need)))
         buf = np.zeros(need.value, np.uint8)
@@ -442,9 +457,12 @@ class MlfmaPlan:
         return out
 
     def sync(self, stream=None):
+        """Wait for the plan's work on `stream` and raise a pending device-side
+        error (mlfma_sync)."""
         _check(self._lib.mlfma_sync(self._h, ctypes.c_void_p(stream or 0)))
 
     def close(self):
+        """Release the plan (mlfma_destroy) unless it belongs to a set."""
         if getattr(self, "_h", None):
             if getattr(self, "_owned", True):
                 self._lib.mlfma_destroy(self._h)
@@ -602,6 +620,8 @@ class MlfmaPlanSet:
         self.n = int(n.value)
 
     def info(self) -> dict:
+        """Waves, each wavenumber's wave, and estimated and actual device
+        bytes per plan (mlfma_set_info)."""
         nk = len(self.ks)
         waves = ctypes.c_int()
         wave_of = np.zeros(nk, np.int32)
@@ -613,6 +633,7 @@ class MlfmaPlanSet:
                 "device_bytes": dev.tolist()}
 
     def plan(self, f: int) -> "MlfmaPlan":
+        """The set's plan of wavenumber f (owned by the set)."""
         h = ctypes.c_void_p()
         _check(self._lib.mlfma_set_plan(self._h, int(f), ctypes.byref(h)))
         return MlfmaPlan(None, None, self.ks[f], 0, max_batch=self.max_batch, _handle=h)
@@ -637,6 +658,7 @@ class MlfmaPlanSet:
         return y
 
     def close(self):
+        """Release the set and all its plans (mlfma_set_destroy)."""
         if getattr(self, "_h", None):
             self._lib.mlfma_set_destroy(self._h)
             self._h = None

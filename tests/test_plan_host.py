@@ -430,12 +430,12 @@ def test_translation_tables_match_scipy_series():
 
 
 @pytest.mark.parametrize("case", ["nan vertex", "inf vertex", "digits 0", "digits nan", "k nan", "k inf", "levels 23",
-                                  "max_batch 0", "interp 0", "interp 40", "negative index", "empty", "zero area"])
+                                  "max_batch 0", "interp 0", "interp 2", "interp 40", "negative index", "empty", "zero area"])
 def test_plan_arguments_rejected(case):
     """mlfma_plan answers each invalid argument with MLFMA_EINVAL (status 1)
     and a message, before any device work: non-finite coordinates or
     wavenumber, digits outside 1..15, levels outside 2..21, max_batch
-    outside 1..4096, an odd or out-of-range interpolation order, a vertex
+    outside 1..4096, an odd interpolation order or one outside 4..12, a vertex
     index out of range, an empty mesh, a triangle of zero area."""
     v, t = workloads.icosphere(2, 0.5)
     k, kw, levels, digits = 2 * math.pi, {}, 3, 3.0
@@ -452,8 +452,8 @@ def test_plan_arguments_rejected(case):
         levels = 23
     elif case == "max_batch 0":
         kw["max_batch"] = 0
-    elif case in ("interp 0", "interp 40"):
-        kw["interp_order"] = 0 if case == "interp 0" else 40
+    elif case in ("interp 0", "interp 2", "interp 40"):
+        kw["interp_order"] = int(case.split()[1])
     elif case == "negative index":
         t = np.where(t == 0, -1, t)
     elif case == "empty":
