@@ -358,7 +358,13 @@ mlfma_status mlfma_sync(mlfma_plan_t plan, void *stream);
  * so the whole near pattern is kept); all products run
  * through the GPU MLFMA in `prec`, an inner solve done with FP32 products is
  * checked with an FP64 product when the plan has FP64 and refined if needed.
- * Arnoldi vectors, Hessenberg matrices and Ritz pairs are FP64 on the host.
+ * The Arnoldi basis (ncv + 1 complex FP64 vectors) lives on the device:
+ * classical Gram-Schmidt twice, normalisation, the restart's recombination
+ * and the Ritz vectors are FP64 kernels; the Hessenberg matrix and its Ritz
+ * pairs are FP64 on the host.  The options are checked before any device
+ * work: EINVAL for nev < 1, ncv outside nev + 2..N, an unknown op or prec,
+ * tol or gmres_tol not positive, gmres_restart < 2, max_inner or
+ * max_restarts < 1, and for a host-only plan.
  *  lambda  host [nev], sorted by |lambda|
  *  J       host [N][nev] real characteristic currents (unit 2-norm), canonical
  *          RWG order; may be NULL

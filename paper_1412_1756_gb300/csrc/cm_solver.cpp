@@ -738,8 +738,8 @@ extern "C" mlfma_status cm_ira_solve(mlfma_plan_t plan, const mlfma_cm_opts *opt
     if (o.nev < 1 || o.ncv <= o.nev + 1 || o.ncv > n) return fail(MLFMA_EINVAL, "need 1 <= nev < ncv - 1 and ncv <= N");
     if (o.op != MLFMA_CM_ZINV_R && o.op != MLFMA_CM_XINV_R) return fail(MLFMA_EINVAL, "unknown operator");
     if (o.prec != MLFMA_FP32 && o.prec != MLFMA_FP64) return fail(MLFMA_EINVAL, "unknown precision");
-    if (!(o.gmres_tol > 0) || o.gmres_restart < 2 || o.max_inner < 1 || o.max_restarts < 1)
-        return fail(MLFMA_EINVAL, "bad GMRES settings");
+    if (!(o.tol > 0) || !(o.gmres_tol > 0) || o.gmres_restart < 2 || o.max_inner < 1 || o.max_restarts < 1)
+        return fail(MLFMA_EINVAL, "bad tolerance or iteration limits");
     std::vector<cd> near;
     const PlanHost *H = nullptr;
     if (!plan_near_host(plan, near, &H)) return fail(MLFMA_EINVAL, "plan is host-only or its near field is unreadable");

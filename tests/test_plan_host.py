@@ -464,3 +464,22 @@ def test_plan_arguments_rejected(case):
     with pytest.raises(M.MlfmaError) as e:
         M.MlfmaPlan(v, t, k, levels, digits, host_only=True, **kw)
     assert e.value.status == 1 and str(e.value)
+
+
+@pytest.mark.parametrize("bad", [dict(nev=0), dict(nev=10, ncv=11), dict(ncv=10 ** 6), dict(op=7), dict(prec=2),
+                                 dict(tol=0.0), dict(gmres_tol=-1.0), dict(gmres_restart=1), dict(max_inner=0),
+                                 dict(max_restarts=0)])
+def test_cm_solve_options_checked_before_device_work(bad):
+    """cm_ira_solve refuses each invalid option with EINVAL on a host-only
+    plan, before it looks for the device; valid options on that plan are
+    refused for the plan itself.  cm_block_solve refuses a host-only plan."""
+    W, v, t, P = host_plan("sphere-r0.5m-ico2")
+    with pytest.raises(M.MlfmaError) as e:
+        P.cm_solve(**bad, vectors=False)
+    assert e.value.status == 1 and "host-only" not in str(e.value), str(e.value)
+    with pytest.raises(M.MlfmaError) as e:
+        P.cm_solve(vectors=False)
+    assert e.value.status == 1 and "host-only" in str(e.value)
+    with pytest.raises(M.MlfmaError) as e:
+        P.cm_block_solve(nev=4, block=8, vectors=False)
+    assert e.value.status == 1 and "device plan" in str(e.value)
