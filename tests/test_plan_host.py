@@ -483,3 +483,27 @@ def test_cm_solve_options_checked_before_device_work(bad):
     with pytest.raises(M.MlfmaError) as e:
         P.cm_block_solve(nev=4, block=8, vectors=False)
     assert e.value.status == 1 and "device plan" in str(e.value)
+
+
+def test_export_refuses_unknown_tables_levels_and_short_buffers():
+    """mlfma_export: an unknown table code or a level the table does not
+    have is EINVAL; a destination smaller than the table is EINVAL with
+    *needed still set to the table's size; asking with dst = NULL only
+    reports the size."""
+    import ctypes
+    W, v, t, P = host_plan("sphere-r2m-ico5")
+    lib = M.load()
+    for code in (0, 99):
+        with pytest.raises(M.MlfmaError):
+            P.export(code, 2)
+    for code, level in ((M.X_ALPHA, 1), (M.X_INTERP, P.info()["leaf_level"]), (M.X_BOX_CENTERS, 9)):
+        with pytest.raises(M.MlfmaError):
+            P.export(code, level)
+    need = ctypes.c_int64(-1)
+    assert lib.mlfma_export(P._h, M.X_GRID, 2, None, 0, ctypes.byref(need)) == 0
+    assert need.value == 4 * 8 * P.info()["samples_K"][2]
+    buf = np.zeros(need.value // 8 - 1)
+    need2 = ctypes.c_int64(-1)
+    assert lib.mlfma_export(P._h, M.X_GRID, 2, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes,
+                            ctypes.byref(need2)) == 1
+    assert b"too small" in lib.mlfma_last_error() and need2.value == need.value
