@@ -507,3 +507,19 @@ def test_export_refuses_unknown_tables_levels_and_short_buffers():
     assert lib.mlfma_export(P._h, M.X_GRID, 2, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes,
                             ctypes.byref(need2)) == 1
     assert b"too small" in lib.mlfma_last_error() and need2.value == need.value
+
+
+def test_sweep_admission_refusals_are_host_logic():
+    """mlfma_set_create (frequency sweeps): the memory admission compares each
+    plan's estimate, made from its host tables, with the budget before any
+    device allocation; a plan above the budget is ENOMEM with both sizes in
+    the message.  An empty wavenumber list and a non-positive wavenumber are
+    EINVAL."""
+    v, t = workloads.icosphere(2, 0.5)
+    with pytest.raises(M.MlfmaError) as e:
+        M.MlfmaPlanSet(v, t, [2 * math.pi, 2.2 * math.pi], 3, device=0, budget_bytes=1 << 20)
+    assert e.value.status == 2 and "admission budget is 1 MiB" in str(e.value)
+    for ks in ([], [2 * math.pi, -1.0]):
+        with pytest.raises(M.MlfmaError) as e:
+            M.MlfmaPlanSet(v, t, ks, 3, device=0, budget_bytes=1 << 30)
+        assert e.value.status == 1
