@@ -80,6 +80,16 @@ class Info(ctypes.Structure):
 _lib = None
 
 
+def _check_device_pair(x, y=None):
+    """The products read x and write y on the GPU, so both must be CUDA
+    tensors on one device: a host buffer handed to the library would be
+    accessed by the kernels as if it were device memory."""
+    if not x.is_cuda:
+        raise ValueError("x must be a CUDA tensor (use matvec_host for host arrays)")
+    if y is not None and (not y.is_cuda or y.device != x.device):
+        raise ValueError("y must be a CUDA tensor on x's device")
+
+
 def library_path() -> str:
     """Path of the in-tree compiled library."""
     return _build.LIB
@@ -253,8 +263,7 @@ class MlfmaPlan:
 
     def _product(self, fn, x, y, stream, prec=None):
         import torch
-        if not x.is_cuda:
-            raise ValueError("x must be a CUDA tensor (use matvec_host for host arrays)")
+        _check_device_pair(x)
         squeeze = x.dim() == 1
         x2 = x.reshape(self.n, -1) if squeeze else x
         if x2.dim() != 2 or x2.shape[0] != self.n:
@@ -273,6 +282,7 @@ class MlfmaPlan:
             y = torch.empty((self.n, B), dtype=cdt, device=x2.device)
         if y.dtype != cdt or not y.is_contiguous() or y.numel() != self.n * B:
             raise ValueError("y must be a contiguous %s tensor with N*B elements" % cdt)
+        _check_device_pair(x2, y)
         s = torch.cuda.current_stream(x2.device).cuda_stream if stream is None else stream
         _check(fn(self._h, ctypes.c_void_p(x2.data_ptr()), xc, ctypes.c_void_p(y.data_ptr()), B, prec,
                   ctypes.c_void_p(s)))
@@ -331,6 +341,8 @@ class MlfmaPlan:
         B = x2.shape[1]
         if y is None:
             y = np.empty((self.n, B), dtype=cdt)
+        if y.dtype != cdt or not y.flags.c_contiguous or y.size != self.n * B:
+            raise ValueError("y must be a C-contiguous %s array with N*B elements" % np.dtype(cdt))
         _check(self._lib.mlfma_matvec_host(self._h, _np_ptr(x2), xc, _np_ptr(y), B, prec,
                                            ctypes.c_void_p(stream or 0)))
         return y.reshape(self.n) if squeeze else y
@@ -642,6 +654,7 @@ class MlfmaPlanSet:
         """y[f] = Z(k_f) x[f] for x [nk, N, B] (or one [N, B] block for every
         wavenumber); returns [nk, N, B] complex."""
         import torch
+        _check_device_pair(x, y)
         nk = len(self.ks)
         shared = x.dim() == 2 or (x.dim() == 1)
         x3 = x.reshape(self.n, -1) if shared else x.reshape(nk, self.n, -1)
@@ -652,6 +665,8 @@ class MlfmaPlanSet:
         B = x3.shape[-1]
         if y is None:
             y = torch.empty((nk, self.n, B), dtype=cdt, device=x3.device)
+        if y.dtype != cdt or not y.is_contiguous() or y.numel() != nk * self.n * B:
+            raise ValueError("y must be a contiguous %s tensor with nk*N*B elements" % cdt)
         s = torch.cuda.current_stream(x3.device).cuda_stream if stream is None else stream
         _check(self._lib.mlfma_set_matvec(self._h, ctypes.c_void_p(x3.data_ptr()), 1 if shared else 0, xc,
                                           ctypes.c_void_p(y.data_ptr()), B, prec, ctypes.c_void_p(s)))

@@ -523,3 +523,26 @@ def test_sweep_admission_refusals_are_host_logic():
         with pytest.raises(M.MlfmaError) as e:
             M.MlfmaPlanSet(v, t, ks, 3, device=0, budget_bytes=1 << 30)
         assert e.value.status == 1
+
+
+def test_binding_refuses_host_buffers_for_device_products():
+    """The binding's argument checks before any library call: device
+    products take CUDA tensors for x and y (a host buffer would be accessed by
+    the kernels as device memory), and matvec_host takes a y array of the
+    right dtype, layout and size (the device-to-host copy fills N*B values)."""
+    import types
+    torch = pytest.importorskip("torch")
+    W, v, t, P = host_plan("sphere-r0.5m-ico2")
+    with pytest.raises(ValueError, match="x must be a CUDA tensor"):
+        P.matvec(torch.zeros(P.n, 2))
+    fake_x = types.SimpleNamespace(is_cuda=True, device="cuda:0")
+    with pytest.raises(ValueError, match="y must be a CUDA tensor"):
+        M._check_device_pair(fake_x, torch.zeros(4))
+    M._check_device_pair(fake_x, None)
+    x = np.zeros((P.n, 2), np.float32)
+    for y in (np.zeros((P.n, 2), np.complex128), np.zeros((P.n, 1), np.complex64),
+              np.zeros((2, P.n), np.complex64).T):
+        with pytest.raises(ValueError, match="y must be"):
+            P.matvec_host(x, M.FP32, y=y)
+    with pytest.raises(M.MlfmaError):   # well-formed buffers: refused by the host-only plan itself
+        P.matvec_host(x, M.FP32, y=np.zeros((P.n, 2), np.complex64))
