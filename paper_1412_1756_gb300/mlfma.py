@@ -90,6 +90,16 @@ def _check_device_pair(x, y=None):
         raise ValueError("y must be a CUDA tensor on x's device")
 
 
+def _mesh_arrays(verts, tris):
+    """float64 [nv, 3] and int32 [nt, 3] copies of the mesh (the library reads
+    three values per row)."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    if v.ndim != 2 or v.shape[1] != 3 or t.ndim != 2 or t.shape[1] != 3:
+        raise ValueError("verts must be [nv, 3] and tris [nt, 3]")
+    return v, t
+
+
 def library_path() -> str:
     """Path of the in-tree compiled library."""
     return _build.LIB
@@ -173,8 +183,7 @@ class MlfmaPlan:
             return
         self._owned = True
         self._lib = L
-        v = np.ascontiguousarray(verts, dtype=np.float64)
-        t = np.ascontiguousarray(tris, dtype=np.int32)
+        v, t = _mesh_arrays(verts, tris)
         o = Opts()
         _check(L.mlfma_default_opts(ctypes.byref(o)))
         o.interp_order = int(interp_order)
@@ -608,8 +617,7 @@ class MlfmaPlanSet:
                  precisions=(FP32, FP64), device=None, budget_bytes=0):
         L = load()
         self._lib = L
-        v = np.ascontiguousarray(verts, dtype=np.float64)
-        t = np.ascontiguousarray(tris, dtype=np.int32)
+        v, t = _mesh_arrays(verts, tris)
         kk = np.ascontiguousarray(np.asarray(ks, dtype=np.float64).reshape(-1))
         o = Opts()
         _check(L.mlfma_default_opts(ctypes.byref(o)))

@@ -528,8 +528,9 @@ def test_sweep_admission_refusals_are_host_logic():
 def test_binding_refuses_host_buffers_for_device_products():
     """The binding's argument checks before any library call: device
     products take CUDA tensors for x and y (a host buffer would be accessed by
-    the kernels as device memory), and matvec_host takes a y array of the
-    right dtype, layout and size (the device-to-host copy fills N*B values)."""
+    the kernels as device memory), matvec_host takes a y array of the right
+    dtype, layout and size (the device-to-host copy fills N*B values), and
+    plans and sweep sets take [nv, 3] vertices and [nt, 3] triangles."""
     import types
     torch = pytest.importorskip("torch")
     W, v, t, P = host_plan("sphere-r0.5m-ico2")
@@ -546,3 +547,8 @@ def test_binding_refuses_host_buffers_for_device_products():
             P.matvec_host(x, M.FP32, y=y)
     with pytest.raises(M.MlfmaError):   # well-formed buffers: refused by the host-only plan itself
         P.matvec_host(x, M.FP32, y=np.zeros((P.n, 2), np.complex64))
+    for vv, tt in ((v[:, :2], t), (v, t[:, :2]), (v.reshape(-1), t)):
+        with pytest.raises(ValueError, match="verts must be"):
+            M.MlfmaPlan(vv, tt, W.k, 3, host_only=True)
+        with pytest.raises(ValueError, match="verts must be"):
+            M.MlfmaPlanSet(vv, tt, [W.k], 3, device=0)
