@@ -552,3 +552,27 @@ def test_binding_refuses_host_buffers_for_device_products():
             M.MlfmaPlan(vv, tt, W.k, 3, host_only=True)
         with pytest.raises(ValueError, match="verts must be"):
             M.MlfmaPlanSet(vv, tt, [W.k], 3, device=0)
+
+
+def test_c_abi_null_arguments():
+    """NULL where the header asks for a plan, set or output pointer is
+    MLFMA_EINVAL with a message; destroying NULL is a no-op; the RWG list
+    copies only the arrays it is given (either may be NULL)."""
+    import ctypes
+    W, v, t, P = host_plan("sphere-r0.5m-ico2")
+    L = M.load()
+    vp, tp = v.ctypes.data_as(ctypes.c_void_p), np.ascontiguousarray(t, np.int32)
+    calls = [lambda: L.mlfma_plan_info(P._h, None), lambda: L.mlfma_num_unknowns(P._h, None),
+             lambda: L.mlfma_default_opts(None), lambda: L.mlfma_cm_default_opts(None),
+             lambda: L.mlfma_plan_info(None, None), lambda: L.mlfma_export(None, M.X_GRID, 2, None, 0, None),
+             lambda: L.mlfma_sync(None, None), lambda: L.mlfma_set_info(None, None, None, None, None, None),
+             lambda: L.mlfma_set_plan(None, 0, None),
+             lambda: L.mlfma_plan(vp, len(v), tp.ctypes.data_as(ctypes.c_void_p), len(t), W.k, 3, 3.0, None, None)]
+    for c in calls:
+        assert c() == 1 and L.mlfma_last_error()
+    L.mlfma_destroy(None)
+    L.mlfma_set_destroy(None)
+    ev = np.full((P.n, 2), -1, np.int32)
+    assert L.mlfma_rwg_edges(P._h, ev.ctypes.data_as(ctypes.c_void_p), None) == 0
+    assert (ev >= 0).all() and (ev[:, 0] < ev[:, 1]).all()
+    assert L.mlfma_rwg_edges(P._h, None, None) == 0
