@@ -5,7 +5,9 @@ columns), must equal the figures written out by hand below (every operand
 read once, every result written once, 8 bytes per complex FP32 value; a
 translation costs 16 real flops per pair, sample and column: one complex
 multiply-add for each of the two tangential components).  The whole-job rate
-of N replicas is N x columns x steps over the slowest rank's time."""
+of N replicas is N x columns x steps over the slowest rank's time.  The
+clock sampler reads nvidia-smi's CSV rows into the median SM clock, the
+maximum clock and the throttle reasons that were active."""
 import bench
 import workloads
 from paper_1412_1756_gb300 import mlfma as M
@@ -37,3 +39,22 @@ def test_algorithmic_counts_of_the_cube_at_64_columns():
 def test_replica_rate_and_single_process_max():
     assert bench.replica_rate(64, 20, 0.5, 4) == 4 * 64 * 20 / 0.5
     assert bench.reduce_max(3.25, None, "cpu") == 3.25
+
+
+def test_clock_sampler_summary(tmp_path):
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "garbled line",
+            "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    c = bench.ClockSampler(0)
+    c.proc, c.path = object(), str(path)
+    out = c.summary()
+    assert out == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"]}
+    path.write_text("0, 1200, 2070, 700.0, 0x8, Active, Not Active, Active, Not Active\n")
+    c.path = str(path)
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.proc = None
+    assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
