@@ -80,7 +80,7 @@ typedef struct {
                            even, 4..12; default 10 */
     int max_batch;      /* largest B (real columns; a complex column counts
                            two) a product may use; fields are sized for it;
-                           default 64 */
+                           1..4096, default 64 */
     int precisions;     /* bit mask (1 << mlfma_prec) of arithmetic to set up;
                            default both */
     int host_only;      /* 1: build the host tables only and never touch a
