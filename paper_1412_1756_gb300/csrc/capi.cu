@@ -1281,7 +1281,7 @@ mlfma_status mlfma_plan(const double *verts, int64_t nv, const int32_t *tris, in
     if (!p) return fail(MLFMA_ENOMEM, "host allocation failed");
     if (opts) p->opts = *opts; else mlfma_default_opts(&p->opts);
     if (p->opts.max_batch < 1 || p->opts.max_batch > 4096) return fail(MLFMA_EINVAL, "max_batch must be in 1..4096");
-    if (!(p->opts.eta > 0)) return fail(MLFMA_EINVAL, "eta must be positive");
+    if (!(p->opts.eta > 0) || !std::isfinite(p->opts.eta)) return fail(MLFMA_EINVAL, "eta must be positive and finite");
     std::string err;
     try {
         err = build_plan_host(p->host, verts, nv, tris, nt, k, levels, digits, p->opts.interp_order, p->opts.eta);

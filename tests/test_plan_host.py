@@ -430,13 +430,14 @@ def test_translation_tables_match_scipy_series():
 
 
 @pytest.mark.parametrize("case", ["nan vertex", "inf vertex", "digits 0", "digits nan", "k nan", "k inf", "levels 23",
-                                  "max_batch 0", "interp 0", "interp 2", "interp 40", "negative index", "empty", "zero area"])
+                                  "max_batch 0", "interp 0", "interp 2", "interp 40", "negative index", "empty", "zero area", "eta inf", "eta 0"])
 def test_plan_arguments_rejected(case):
     """mlfma_plan answers each invalid argument with MLFMA_EINVAL (status 1)
     and a message, before any device work: non-finite coordinates or
     wavenumber, digits outside 1..15, levels outside 2..21, max_batch
     outside 1..4096, an odd interpolation order or one outside 4..12, a vertex
-    index out of range, an empty mesh, a triangle of zero area."""
+    index out of range, an empty mesh, a triangle of zero area, a wave
+    impedance that is not positive and finite."""
     v, t = workloads.icosphere(2, 0.5)
     k, kw, levels, digits = 2 * math.pi, {}, 3, 3.0
     if case in ("nan vertex", "inf vertex"):
@@ -458,6 +459,8 @@ def test_plan_arguments_rejected(case):
         t = np.where(t == 0, -1, t)
     elif case == "empty":
         t = t[:0]
+    elif case in ("eta inf", "eta 0"):
+        kw["eta"] = float("inf") if case == "eta inf" else 0.0
     elif case == "zero area":
         v = np.vstack([v, v[:1]])
         t = np.vstack([t, [[0, len(v) - 1, t[0, 1]]]])
